@@ -1,0 +1,54 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case copies oracle/fdlb_oracle.c, plants one plausible mistake (a dropped
+term, a wrong coefficient, sign or index), builds it into a temporary library
+and runs tests/test_oracle_pins.py against it in a subprocess; the pins must
+fail.  Everything runs on the CPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fdlb_oracle.c")
+
+MUTATIONS = {
+    "j1_theta_dlnT_coeff": ("0.3 * (xi * xi * xi / T + 7.0 * xi / 3.0) * dlnT", "0.3 * (xi * xi * xi / T + xi / 3.0) * dlnT"),
+    "j1_phi_missing_Y": ("j1phi[k] = -Y * bphi * fmb[k];", "j1phi[k] = -bphi * fmb[k];"),
+    "j1_phi_du_coeff": ("0.6 * (xi * xi / T - 1.0) * du +", "0.6 * (xi * xi / T - 1.0 / 3.0) * du +"),
+    "shakhov_phi_poly": ("(1.0 + a * (xi * xi / T - 3.0) * xi * q)", "(1.0 + a * (xi * xi / T - 1.0) * xi * q)"),
+    "weno_weight_power": ("t2 = d2 / (b2 * b2)", "t2 = d2 / b2"),
+    "weno_candidate_sign": ("F3 = f0 / 3.0 + 5.0 * fp1 / 6.0 - fp2 / 6.0", "F3 = f0 / 3.0 + 5.0 * fp1 / 6.0 + fp2 / 6.0"),
+    "weno_mirror_index": ("s[r] = ef[(size_t)(j + 3 - r) * Q + k];", "s[r] = ef[(size_t)(j + 2 - r) * Q + k];"),
+    "cd6_coeff": ("3.0 * q[4] / 4.0", "3.0 * q[4] / 5.0"),
+    "rk3_stage2": ("p2[e] = 0.75 * phi[e] + 0.25 * p1[e] + 0.25 * dt * Lp[e];", "p2[e] = 0.75 * phi[e] + 0.25 * p1[e] + 0.5 * dt * Lp[e];"),
+    "moments_temperature": ("out[2] = e / (1.5 * n);", "out[2] = e / n;"),
+    "equilibrium_order": ("int N = Q - 1;", "int N = Q - 2;"),
+    "chi_sign": ("return 0.5 * (2.0 - eta) / pow(1.0 - eta, 3.0);", "return 0.5 * (2.0 + eta) / pow(1.0 - eta, 3.0);"),
+    "viscosity_coeff": ("(1.0 / Y + 0.8 + 4.0 / 25.0", "(1.0 / Y + 1.2 + 4.0 / 25.0"),
+    "dlnchi_chain_rule": ("eta * (3.0 / (1.0 - eta) - 1.0 / (2.0 - eta)) * dlnrho", "eta * (2.0 / (1.0 - eta) - 1.0 / (2.0 - eta)) * dlnrho"),
+    "ghost_theta": ("for (int k = 0; k < Q; ++k) dt[k] = 2.0 * s[2] * dp[k];", "for (int k = 0; k < Q; ++k) dt[k] = s[2] * dp[k];"),
+    "rh_energy": ("double e1 = 1.5 * rho1 * T1", "double e1 = 2.5 * rho1 * T1"),
+    "prandtl_coeff": ("double den = 1.0 + 1.2 * Y", "double den = 1.0 + 1.0 * Y"),
+    "sound_init_eos": ("T[c] = P0 / (r * (1.0 + 4.0 * eta * oq_chi_set(eta)));", "T[c] = P0 / (r * (1.0 + 2.0 * eta * oq_chi_set(eta)));"),
+    "quadrature_weight": ("w[k] = qf / (hq1 * hq1);", "w[k] = qf / (hq1 * hq1) * (1.0 + 1e-9 * k);"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {name}"
+    mutated = tmp_path / "fdlb_oracle.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(mutated), "-lm"])
+    env = dict(os.environ, ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
