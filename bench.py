@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the FDLB solver: cell-velocity updates per second.
+
+Workload: Sod shock tube, Nx = 2^22 cells, Q = 32 velocities, E_l = 0.1 and
+Kn = 0.05 on the left state, rho_R = rho_L / 8, fixed ghosts, dense Pr.  One
+benchmark step is one full time step of Eq. (rk3) (three fused stage kernels)
+over the whole grid; one update advances phi_k and theta_k of one cell by one
+step.  With --gpus N every rank advances its own copy (replicas; the value sums
+the ranks' updates over the slowest rank's time).
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded window of the same workload (see the "sample" field).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ORACLE_SAMPLE_NX = 8192   # cells of the Sod tube (around the membrane) per oracle step
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2211_16933_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.startswith("fdlb_") or f == "qlbm_internal.h":
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(precision_name):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on this kernel source."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
+        e = t.get(precision_name)
+        if e and e.get("kernel_hash") == _kernel_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_sample(w, steps, warmup):
+    """Times the FP64 oracle on a window of the workload; returns (updates/s, seconds, sample text)."""
+    import oracle as O
+    Q, nx = w["Q"], w["nx"]
+    p, _ = O.quadrature(Q)
+    dx = w["length"] / nx
+    from paper_2211_16933_gb300 import inputs
+    dt = inputs.cfl_dt(dx, abs(p).max())
+    ns = ORACLE_SAMPLE_NX
+    a = nx // 2 - ns // 2
+    gm = O.make_model(Q, nx, w["length"], dt, w["denseness"], w["kn"], pr_mode=1, bc=O.BC_FIXED)
+    r, u, T = O.init_fields(gm, O.INIT_RIEMANN, w["prm"], a, ns)
+    gl = O.init_fields(gm, O.INIT_RIEMANN, w["prm"], a - 3, 3)
+    gr = O.init_fields(gm, O.INIT_RIEMANN, w["prm"], a + ns, 3)
+    m = O.make_model(Q, ns, ns * dx, dt, w["denseness"], w["kn"] * w["length"] / (ns * dx), pr_mode=1,
+                     bc=O.BC_FIXED)
+    O.set_ghosts(m, np.stack(gl, 1), np.stack(gr, 1))
+    ph, th = O.equilibrium_state(m, r, u, T)
+    for _ in range(warmup):
+        ph, th = O.run(m, ph, th, 1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ph, th = O.run(m, ph, th, 1)
+    el = time.perf_counter() - t0
+    ups = ns * Q * steps / el
+    sample = (f"{steps} oracle RK3 steps (FP64, 1 thread) on {ns} cells around the membrane of the "
+              f"Nx={nx}, Q={Q} Sod tube, same dx and dt")
+    return ups, el, sample
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    ups, el, sample = _oracle_sample(w, steps, min(args.warmup, 1))
+    line = {"impl": "reference", "metric": "cell-velocity updates/s", "value": ups, "unit": "updates/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "nx": w["nx"], "Q": w["Q"]},
+            "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ups, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import inputs
+    from paper_2211_16933_gb300 import qlbm as q
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.build()
+    Q, nx = w["Q"], w["nx"]
+    prec = q.QL_FP32 if args.precision == "fp32" else q.QL_FP64
+    elem = 4 if prec == q.QL_FP32 else 8
+    pmax = float(np.abs(q.ql_velocity_set(Q)[0]).max())
+    dt = inputs.cfl_dt(w["length"] / nx, pmax)
+    s = q.Solver(Q, nx, w["length"], dt, w["denseness"], w["kn"], bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN,
+                 prm=w["prm"], precision=prec, pr_mode=q.QL_PR_DENSE, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-resident throughput: K timed steps, each 3 stage launches
+    for _ in range(args.warmup):
+        s.step(1)
+    barrier()
+    clk = ClockSampler(dev)
+    clk.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        s.step(1)
+        ev[k + 1].record(stream)
+    barrier()
+    clocks = clk.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    s.sync()
+    t = torch.tensor([total_ms], device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    updates = nx * Q * args.steps * ws
+    value = updates / (max_ms * 1e-3)
+
+    # roofline of the stage kernel: algorithmic bytes = 16 words per update per step
+    # (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2, words of phi and theta)
+    bytes_per_step = 16 * elem * nx * Q
+    launch_s = (total_ms * 1e-3) / (3 * args.steps)
+    achieved = bytes_per_step / 3 / launch_s / 1e9
+    peaks = _peaks()
+    if peaks and "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _traffic(args.precision), "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": bytes_per_step / 3, "launches_per_step": 3,
+                "kernel": "fdlb_stage_kernel"}
+
+    # --- end to end through the C ABI with pinned host buffers: upload initial
+    # fields, K x (step + read back domain totals), read back all fields
+    e2e = None
+    if not args.no_e2e:
+        gm_r, gm_u, gm_T = [torch.empty(nx, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+        x = (np.arange(nx) + 0.5) / nx
+        left = x < 0.5
+        gm_r.numpy()[:] = np.where(left, w["prm"][0], w["prm"][3])
+        gm_u.numpy()[:] = np.where(left, w["prm"][1], w["prm"][4])
+        gm_T.numpy()[:] = np.where(left, w["prm"][2], w["prm"][5])
+        outs = [torch.empty(nx, dtype=torch.float64, pin_memory=True) for _ in range(6)]
+        tot = torch.empty(3, dtype=torch.float64, pin_memory=True)
+        ke = max(1, args.steps)
+        barrier()
+        t0 = time.perf_counter()
+        q.ql_load_fields(s.ctx, gm_r.numpy(), gm_u.numpy(), gm_T.numpy())
+        for _ in range(ke):
+            q.ql_step(s.ctx, 1)
+            q.ql_totals(s.ctx, tot.numpy())
+        q.ql_moments(s.ctx, *[o.numpy() for o in outs], tot.numpy())
+        barrier()
+        el = time.perf_counter() - t0
+        t = torch.tensor([el], device="cuda")
+        if ws > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el = float(t.item())
+        e2e = {"value": nx * Q * ke * ws / el, "unit": "updates/s",
+               "h2d_bytes_per_step": 3 * 8 * nx / ke, "d2h_bytes_per_step": 3 * 8 + 6 * 8 * nx / ke,
+               "steps": ke, "pattern": "load fields (pinned) + K x (step, totals) + all fields"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ups, el, sample = _oracle_sample(w, args.cpu_steps, 0)
+        cpu = {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    s.close()
+    if rank == 0:
+        line = {"metric": "cell-velocity updates/s", "value": value, "unit": "updates/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == q.QL_FP32 else "f64", "data": "synthetic",
+                "config": {"workload": w["name"], "nx": nx, "Q": Q, "precision": args.precision,
+                           "sums": "f64 per-cell conserved moments" if prec == q.QL_FP32 else "f64",
+                           "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (3 state buffers of %.2f GiB)" % (
+                               2 * Q * nx * elem / 2 ** 30)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
+                "clocks": clocks, "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--nx", type=int, default=1 << 22)
+    ap.add_argument("--q", type=int, default=32)
+    ap.add_argument("--cpu-steps", type=int, default=6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from paper_2211_16933_gb300 import inputs
+    w = inputs.sod_tube(nx=args.nx, Q=args.q)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

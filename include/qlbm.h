@@ -1,0 +1,224 @@
+/*
+ * qlbm.h - C ABI of a GB300 (sm_103a) solver for the finite-difference
+ * Enskog-Shakhov lattice Boltzmann model of S. Busuioc, "Quadrature-based
+ * Lattice Boltzmann model for non-equilibrium dense gas flows"
+ * (arXiv:2211.16933).
+ *
+ * The model evolves the two reduced distributions phi_k(x, t), theta_k(x, t)
+ * of Sec. II.C on the Q-point full-range Gauss-Hermite velocity set of
+ * Sec. II.D, with Eq. (evolution_lb):
+ *   d_t psi_k + p_k d_x psi_k = -(psi_k - psi_S;k)/tau + J1_k,  psi in {phi, theta},
+ * advanced by the third-order TVD Runge-Kutta scheme of App. A.1 (Eq. rk3),
+ * with WENO-5 advection (App. A.2) and 6th-order central gradients (App. A.3).
+ *
+ * Units are the nondimensional ones of Sec. II.A: m = k_B = T_ref = 1.
+ *
+ * Conventions for every entry point:
+ *   - Returns a ql_status; nothing is thrown across the ABI.  On an error other
+ *     than QL_OK, ql_last_error() describes it.
+ *   - Pointers named "host" are caller-owned host memory; the library copies
+ *     from or into them before returning.  Pointers named "device" are
+ *     caller-owned device memory on the context's device.
+ *   - The context owns its device buffers and frees them in ql_destroy.
+ *   - Work is queued on the stream given at creation; only ql_step returns
+ *     before its work is done.  Calls on one context are not thread-safe.
+ *   - Non-physical states (n <= 0, T <= 0 or a non-finite moment in any
+ *     interior cell) raise a device error word that the next synchronising
+ *     call (ql_sync, ql_moments, ql_get_state, ql_totals) reports as
+ *     QL_ENONPHYSICAL.
+ */
+#ifndef QLBM_H
+#define QLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ql_ctx ql_ctx; /* opaque, library-owned */
+
+typedef enum {
+    QL_OK = 0,
+    QL_EINVAL = 1,        /* invalid argument or unsupported combination */
+    QL_ENOMEM = 2,        /* device or host allocation failed */
+    QL_ECUDA = 3,         /* a CUDA runtime call failed */
+    QL_ENONPHYSICAL = 4,  /* n <= 0, T <= 0 or non-finite moments in a cell */
+    QL_ETIMEOUT = 5,      /* a bounded device wait ran out */
+    QL_EUNSUPPORTED = 6   /* a velocity-set size this build has no kernel for */
+} ql_status;
+
+enum { QL_FP64 = 0, QL_FP32 = 1 };              /* arithmetic of the state and its update */
+enum { QL_BC_PERIODIC = 0, QL_BC_FIXED = 1 };   /* boundary of the 1D domain */
+enum { QL_INIT_SOUND = 0, QL_INIT_RIEMANN = 1, QL_INIT_SHOCK = 2, QL_INIT_FIELDS = 3 };
+enum { QL_PR_CONST = 0, QL_PR_DENSE = 1 };
+
+/* Velocity set, Sec. II.D: the Q roots p_k of the probabilists' Hermite
+ * polynomial He_Q with weights w_k = Q!/He_{Q+1}(p_k)^2 (kind 0 is the only
+ * kind).  This build has kernels for Q in {8, 16, 24, 32}. */
+typedef struct {
+    int32_t Q;
+    int32_t kind;
+} ql_velset;
+
+/* Uniform grid of nx cells of width dx = length/nx, centres x_i = (i+1/2) dx,
+ * and the time step dt (> 0) of Eq. (rk3). */
+typedef struct {
+    int64_t nx;
+    double length;
+    double dt;
+} ql_grid;
+
+/* Boundary: QL_BC_PERIODIC, or QL_BC_FIXED, where three ghost cells on each
+ * side hold the discrete equilibrium of fixed states for the whole run (the
+ * far field of the initial state, or ql_init.ghost for QL_INIT_FIELDS). */
+typedef struct {
+    int32_t kind;
+    int32_t pad_;
+} ql_bc;
+
+/* Initial macroscopic state; the distributions start as its discrete
+ * equilibrium, phi_k = n g_k[u, T] and theta_k = 2 T n g_k of Eq. (feq).
+ *   QL_INIT_SOUND   prm = {rho0, T0, A}: rho = rho0 (1 + A cos(2 pi x/L)),
+ *                   u = 0, T such that the pressure P = rho T (1 + b rho chi)
+ *                   is uniform (Sec. IV.A, delta P = 0).  Needs periodic bc.
+ *   QL_INIT_RIEMANN prm = {rhoL, uL, TL, rhoR, uR, TR}: two states split at
+ *                   x = L/2 (the Sod tube of Eq. shock_init).
+ *   QL_INIT_SHOCK   prm = {rho1, T1, M, width}: standing normal shock, the
+ *                   upstream state moving at u1 = M c_s(rho1, T1) and the
+ *                   downstream state from the Rankine-Hugoniot relations of
+ *                   Eq. (rankine_hugoniot) with the dense equation of state,
+ *                   joined by a tanh of the given width centred at L/2.
+ *   QL_INIT_FIELDS  rho, u, T: host arrays of nx doubles; with QL_BC_FIXED,
+ *                   ghost: host array of 6 (rho, u, T) triples for cells
+ *                   -3, -2, -1, nx, nx+1, nx+2 in that order. */
+typedef struct {
+    int32_t kind;
+    int32_t pad_;
+    double prm[8];
+    const double *rho, *u, *T;
+    const double *ghost;
+} ql_init;
+
+/* Device allocator hooks (for example a PyTorch caching allocator); when alloc
+ * is NULL the library calls cudaMalloc/cudaFree. */
+typedef void *(*ql_alloc_fn)(size_t bytes, void *user);
+typedef void (*ql_free_fn)(void *ptr, void *user);
+
+/* Options.
+ *   precision  QL_FP64: state, update and sums in FP64.
+ *              QL_FP32: state and update in FP32, per-cell conserved-moment
+ *              sums and the domain totals in FP64.
+ *   pr_mode    QL_PR_CONST uses pr_const; QL_PR_DENSE the Prandtl number of
+ *              the dense gas as a function of b rho chi (Sec. II.B).
+ *   enskog     1 adds the simplified-Enskog term J1 of Eq. (j1_expanded);
+ *              0 leaves it out (b rho chi still sets tau and Pr).
+ *   rho_ref    density at which the denseness E_l is given; the local reduced
+ *              density is eta = eta0 rho / rho_ref.
+ *   stream     cudaStream_t for all work, NULL for the legacy default stream. */
+typedef struct {
+    int32_t precision;
+    int32_t pr_mode;
+    int32_t enskog;
+    int32_t device;
+    double pr_const;
+    double rho_ref;
+    void *stream;
+    ql_alloc_fn alloc;
+    ql_free_fn free;
+    void *alloc_user;
+} ql_opts;
+
+/* Creates a solver (Secs. II.B-II.D).
+ *   denseness  E_l = sigma/l > 0 at rho_ref (Sec. II.B), which fixes the
+ *              reduced density eta0 through E_l = 6 sqrt(2) eta0 chi(eta0).
+ *   kn         l0/L > 0, l0 the Enskog mean free path at rho_ref; with E_l it
+ *              fixes sigma = E_l l0 and so tau = sigma g[eta] (Eq. tau_sigma).
+ * Errors: QL_EINVAL (bad sizes, dt <= 0, eta0 out of range, init kind needs
+ * another bc), QL_EUNSUPPORTED (Q), QL_ENOMEM, QL_ECUDA.  On error *out is
+ * NULL. */
+ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, double kn,
+                    const ql_bc *bc, const ql_init *init, const ql_opts *opts, ql_ctx **out);
+
+/* Queues nsteps >= 0 steps of Eq. (rk3): three fused stage kernels per step,
+ * each computing moments, equilibrium, Shakhov targets, J1, WENO-5 fluxes and
+ * the Runge-Kutta combination for every (cell, velocity).  Asynchronous. */
+ql_status ql_step(ql_ctx *ctx, int64_t nsteps);
+
+/* Waits for the context's stream and reports the device error word. */
+ql_status ql_sync(ql_ctx *ctx);
+
+/* Macroscopic fields of Sec. II.D per cell, computed on the device in FP64:
+ * rho, u, T, P = n T (1 + b rho chi) (Sec. II.B), q, Pxx = sum xi^2 phi.
+ * Each output is a host array of nx doubles or NULL; totals (host, 3 doubles
+ * or NULL) gets the domain sums of mass, momentum and energy times dx.
+ * Synchronises. */
+ql_status ql_moments(ql_ctx *ctx, double *rho, double *u, double *T, double *P, double *q,
+                     double *Pxx, double *totals);
+
+/* Domain totals only (host, 3 doubles), FP64.  Synchronises. */
+ql_status ql_totals(ql_ctx *ctx, double *totals);
+
+/* Copies the state to host arrays phi, theta of nx*Q doubles, cell-major
+ * (phi[i*Q + k]), converting FP32 states to double.  Synchronises. */
+ql_status ql_get_state(ql_ctx *ctx, double *phi, double *theta);
+
+/* Replaces the state from host arrays laid out as in ql_get_state (rounded
+ * to FP32 for QL_FP32 contexts).  Ghost cells are refreshed. */
+ql_status ql_set_state(ql_ctx *ctx, const double *phi, const double *theta);
+
+/* Re-initialises the state from host macroscopic fields rho, u, T (nx
+ * doubles each) as the discrete equilibrium, like QL_INIT_FIELDS.  Fixed
+ * ghost cells keep their states. */
+ql_status ql_load_fields(ql_ctx *ctx, const double *rho, const double *u, const double *T);
+
+/* Evaluates the right-hand side L[psi] of Eq. (cast) for the current state
+ * into host arrays Lphi, Ltheta (nx*Q doubles, cell-major).  Synchronises. */
+ql_status ql_rhs(ql_ctx *ctx, double *Lphi, double *Ltheta);
+
+/* Device view of the current state for callers that keep data on the GPU:
+ * *phi points at row k = 0 of phi, rows of *row_stride elements, cell i of
+ * row k at (*phi)[k * row_stride + i]; theta rows follow at row Q.  The
+ * element type is double for QL_FP64 and float for QL_FP32.  Valid until the
+ * next ql_step returns and the stream has run it. */
+ql_status ql_state_device(ql_ctx *ctx, void **phi, int64_t *row_stride);
+
+/* Numbers fixed at creation: out[0] = eta0, out[1] = chi(eta0),
+ * out[2] = sigma, out[3] = dx, out[4] = dt, out[5] = max |p_k|,
+ * out[6..6+Q) = p_k, out[6+Q..6+2Q) = w_k.  out holds 6 + 2Q doubles. */
+ql_status ql_info(const ql_ctx *ctx, double *out);
+
+/* ---- Host-only helpers (no GPU needed), FP64 ---------------------------- */
+
+/* Velocity set of Sec. II.D: p (ascending) and w (summing to 1), each a host
+ * array of Q doubles; 1 <= Q <= 200.  QL_EINVAL if Q is out of range. */
+ql_status ql_velocity_set(int32_t Q, double *p, double *w);
+
+/* Reduced density eta0 with E_l = 6 sqrt(2) eta0 chi_SET(eta0) (Sec. II.B,
+ * Eq. chi), for 0 <= E_l <= E_l(0.49).  QL_EINVAL outside that range. */
+ql_status ql_eta_of_denseness(double denseness, double *eta0);
+
+/* Squared adiabatic sound speed of the dense gas, Eq. (sw_cs) with the
+ * equation of state P = rho T (1 + b rho chi) and c_V = 3/2, at density rho
+ * and temperature T, for eta = eta0 rho / rho_ref. */
+double ql_sound_speed2(double eta0, double rho_ref, double rho, double T);
+
+/* Standing normal shock of Mach number mach > 1 into (rho1, T1), Eq.
+ * (rankine_hugoniot) with the dense equation of state: out (host, 4 doubles)
+ * = {u1, rho2, u2, T2}.  QL_EINVAL if no compressive solution exists. */
+ql_status ql_rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach,
+                              double *out);
+
+/* Frees the context and its device buffers (waits for its stream). */
+ql_status ql_destroy(ql_ctx *ctx);
+
+/* Last error message of ctx, or of the last failed ql_create when ctx is
+ * NULL.  The string lives until the next call on that context. */
+const char *ql_last_error(const ql_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLBM_H */

@@ -1,0 +1,97 @@
+// Launchers shared by the per-precision translation units.  Before including
+// this file a unit defines QL_REAL (float or double), QL_SUFFIX (f32 or f64)
+// and declares `static __constant__ QL_REAL QL_TAB[kTabTotal]`.
+#pragma once
+#include "fdlb_kernels.cuh"
+
+#define QL_CAT2(a, b) a##b
+#define QL_CAT(a, b) QL_CAT2(a, b)
+#define QL_FN(name) QL_CAT(name, QL_SUFFIX)
+
+namespace qlbm {
+
+cudaError_t QL_FN(upload_tables_)(const double *all)
+{
+    static QL_REAL host[kTabTotal];
+    for (int e = 0; e < kTabTotal; ++e) host[e] = QL_REAL(all[e]);
+    return cudaMemcpyToSymbol(QL_TAB, host, sizeof(host));
+}
+
+template <int Q, int STAGE>
+static cudaError_t stage_q(const StageArgs &a, cudaStream_t s)
+{
+    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q>();
+    auto kern = fdlb_stage_kernel<QL_REAL, Q, STAGE>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!configured[dev & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        configured[dev & 63] = true;
+    }
+    const int64_t nt = num_tiles(a.nx);
+    kern<<<dim3(unsigned(nt)), dim3(kThreads), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q>
+static cudaError_t stage_dispatch(int stage, const StageArgs &a, cudaStream_t s)
+{
+    switch (stage) {
+    case 0: return stage_q<Q, 0>(a, s);
+    case 1: return stage_q<Q, 1>(a, s);
+    case 2: return stage_q<Q, 2>(a, s);
+    case 3: return stage_q<Q, 3>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t QL_FN(launch_stage_)(int Q, int stage, const StageArgs &a, cudaStream_t s)
+{
+    switch (Q) {
+    case 8: return stage_dispatch<8>(stage, a, s);
+    case 16: return stage_dispatch<16>(stage, a, s);
+    case 24: return stage_dispatch<24>(stage, a, s);
+    case 32: return stage_dispatch<32>(stage, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t QL_FN(launch_init_)(int Q, const double *rho, const double *u, const double *T, void *psi,
+                                int64_t nx, int64_t stride, const double *tab64, cudaStream_t s)
+{
+    const int64_t n = (nx + 2 * kHalo) * Q;
+    const unsigned blocks = unsigned((n + 255) / 256);
+    QL_REAL *p = static_cast<QL_REAL *>(psi);
+    switch (Q) {
+    case 8: fdlb_init_kernel<QL_REAL, 8><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
+    case 16: fdlb_init_kernel<QL_REAL, 16><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
+    case 24: fdlb_init_kernel<QL_REAL, 24><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
+    case 32: fdlb_init_kernel<QL_REAL, 32><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t QL_FN(launch_periodic_ghosts_)(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s)
+{
+    QL_REAL *p = static_cast<QL_REAL *>(psi);
+    fdlb_periodic_ghost_kernel<QL_REAL><<<2 * Q, 32, 0, s>>>(p, nx, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t QL_FN(launch_moments_)(int Q, const MomentArgs &a, const double *tab64, cudaStream_t s)
+{
+    const unsigned blocks = unsigned(moment_blocks(a.nx));
+    switch (Q) {
+    case 8: fdlb_moments_kernel<QL_REAL, 8><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+    case 16: fdlb_moments_kernel<QL_REAL, 16><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+    case 24: fdlb_moments_kernel<QL_REAL, 24><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+    case 32: fdlb_moments_kernel<QL_REAL, 32><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qlbm

@@ -1,0 +1,522 @@
+// C ABI of the solver (include/qlbm.h): context, buffers, launches, copies.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qlbm.h"
+#include "qlbm_host.h"
+#include "qlbm_internal.h"
+
+using namespace qlbm;
+
+struct ql_ctx {
+    int Q = 0, precision = 0, pr_mode = 0, enskog = 1, periodic = 1, device = 0;
+    int64_t nx = 0, stride = 0;
+    double L = 0, dx = 0, dt = 0, El = 0, kn = 0, pr_const = 2.0 / 3.0, rho_ref = 1.0;
+    double eta0 = 0, chi0 = 1, sigma = 0, tau_pref = 0;
+    double p[kMaxQ] = {}, w[kMaxQ] = {};
+    cudaStream_t stream = nullptr;
+    ql_alloc_fn alloc = nullptr;
+    ql_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    size_t elem = 8;
+    void *buf[3] = {nullptr, nullptr, nullptr};  // psi^n, psi^(1), psi^(2)
+    double *d_fields = nullptr;   // 6 * nx output fields
+    double *d_init = nullptr;     // 3 * (nx + 2 kHalo) initial fields
+    double *d_partial = nullptr;  // moment_blocks(nx) * 3
+    double *d_totals = nullptr;   // 3
+    double *d_tab64 = nullptr;    // kTabTotal
+    unsigned *d_err = nullptr;
+    std::vector<double> ghost_state;  // (rho, u, T) of the 2 kHalo ghost columns, fixed bc
+    std::string err;
+};
+
+static std::string g_create_error;
+static std::mutex g_mutex;
+static bool g_tables_ready[64] = {};
+static double g_tab[kTabTotal];
+static bool g_tab_built = false;
+
+static ql_status fail(ql_ctx *c, ql_status st, const std::string &msg)
+{
+    if (c) c->err = msg; else g_create_error = msg;
+    return st;
+}
+
+static ql_status cuda_fail(ql_ctx *c, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? QL_ENOMEM : QL_ECUDA, m);
+}
+
+#define QL_CUDA(ctx, call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+static void *dev_alloc(ql_ctx *c, size_t bytes)
+{
+    if (c->alloc) return c->alloc(bytes, c->alloc_user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    return p;
+}
+
+static void dev_free(ql_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, c->alloc_user);
+    else cudaFree(p);
+}
+
+static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, void *out)
+{
+    StageArgs a;
+    a.in = in;
+    a.base = base;
+    a.out = out;
+    a.nx = c->nx;
+    a.stride = c->stride;
+    a.inv_dx = 1.0 / c->dx;
+    a.dt = c->dt;
+    a.eta0 = c->eta0;
+    a.inv_rho_ref = 1.0 / c->rho_ref;
+    a.tau_pref = c->tau_pref;
+    a.pr_const = c->pr_const;
+    a.pr_mode = c->pr_mode;
+    a.enskog = c->enskog;
+    a.periodic = c->periodic;
+    a.pad_ = 0;
+    a.err = c->d_err;
+    return c->precision == QL_FP32 ? launch_stage_f32(c->Q, s, a, c->stream)
+                                   : launch_stage_f64(c->Q, s, a, c->stream);
+}
+
+static ql_status check_err_word(ql_ctx *c)
+{
+    unsigned h = 0;
+    QL_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    QL_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & 1u) return fail(c, QL_ENONPHYSICAL, "non-physical state: n <= 0, T <= 0 or non-finite moments");
+    return QL_OK;
+}
+
+static ql_status upload_fields_and_init(ql_ctx *c, const double *rho, const double *u, const double *T)
+{
+    const int64_t ncol = c->nx + 2 * kHalo;
+    std::vector<double> h(3 * ncol);
+    memcpy(h.data(), rho, sizeof(double) * ncol);
+    memcpy(h.data() + ncol, u, sizeof(double) * ncol);
+    memcpy(h.data() + 2 * ncol, T, sizeof(double) * ncol);
+    QL_CUDA(c, cudaMemcpyAsync(c->d_init, h.data(), sizeof(double) * 3 * ncol, cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = c->precision == QL_FP32
+                        ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
+                                          c->stride, c->d_tab64, c->stream)
+                        : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
+                                          c->stride, c->d_tab64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    QL_CUDA(c, cudaStreamSynchronize(c->stream));  // h goes out of scope
+    return QL_OK;
+}
+
+static void destroy_buffers(ql_ctx *c)
+{
+    for (int b = 0; b < 3; ++b) dev_free(c, c->buf[b]);
+    dev_free(c, c->d_fields);
+    dev_free(c, c->d_init);
+    dev_free(c, c->d_partial);
+    dev_free(c, c->d_totals);
+    dev_free(c, c->d_tab64);
+    dev_free(c, c->d_err);
+}
+
+extern "C" {
+
+ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, double kn, const ql_bc *bc,
+                    const ql_init *init, const ql_opts *opts, ql_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!vs || !grid || !bc || !init || !opts || !out) return fail(nullptr, QL_EINVAL, "null argument");
+    bool qok = false;
+    for (int j = 0; j < kNumQ; ++j) qok |= vs->Q == kQList[j];
+    if (vs->kind != 0) return fail(nullptr, QL_EINVAL, "velocity set kind must be 0 (Gauss-Hermite)");
+    if (!qok) return fail(nullptr, QL_EUNSUPPORTED, "Q must be one of 8, 16, 24, 32");
+    if (grid->nx < 8 || grid->nx > (int64_t(1) << 31)) return fail(nullptr, QL_EINVAL, "nx must be in [8, 2^31]");
+    if (!(grid->length > 0) || !(grid->dt > 0)) return fail(nullptr, QL_EINVAL, "length and dt must be > 0");
+    if (!(denseness > 0) || !(kn > 0)) return fail(nullptr, QL_EINVAL, "denseness and kn must be > 0");
+    if (bc->kind != QL_BC_PERIODIC && bc->kind != QL_BC_FIXED) return fail(nullptr, QL_EINVAL, "bad bc kind");
+    if (opts->precision != QL_FP32 && opts->precision != QL_FP64) return fail(nullptr, QL_EINVAL, "bad precision");
+    if (!(opts->rho_ref > 0)) return fail(nullptr, QL_EINVAL, "rho_ref must be > 0");
+    if (opts->pr_mode == QL_PR_CONST && !(opts->pr_const > 0)) return fail(nullptr, QL_EINVAL, "pr_const must be > 0");
+
+    ql_ctx *c = new ql_ctx();
+    c->Q = vs->Q;
+    c->precision = opts->precision;
+    c->pr_mode = opts->pr_mode;
+    c->enskog = opts->enskog ? 1 : 0;
+    c->periodic = bc->kind == QL_BC_PERIODIC;
+    c->device = opts->device;
+    c->nx = grid->nx;
+    c->L = grid->length;
+    c->dx = grid->length / double(grid->nx);
+    c->dt = grid->dt;
+    c->El = denseness;
+    c->kn = kn;
+    c->pr_const = opts->pr_const;
+    c->rho_ref = opts->rho_ref;
+    c->stream = static_cast<cudaStream_t>(opts->stream);
+    c->alloc = opts->alloc;
+    c->free_fn = opts->free;
+    c->alloc_user = opts->alloc_user;
+    c->elem = c->precision == QL_FP32 ? 4 : 8;
+    c->stride = row_stride(c->nx);
+
+    auto bail = [&](ql_status st, const std::string &m) {
+        destroy_buffers(c);
+        delete c;
+        return fail(nullptr, st, m);
+    };
+
+    if (!eta_of_denseness(denseness, &c->eta0)) return bail(QL_EINVAL, "denseness out of range (eta0 >= 0.49)");
+    c->chi0 = chi_set(c->eta0);
+    // sigma = E_l l0 with l0 = Kn L; tau = (5 sqrt(2 pi)/16) Kn L chi0 / (rho^ chi sqrt T) (1 + 0.8 Y + ...)
+    c->sigma = denseness * kn * grid->length;
+    c->tau_pref = 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * kn * grid->length * c->chi0;
+    {
+        std::lock_guard<std::mutex> lk(g_mutex);
+        if (!g_tab_built) {
+            if (!build_tables(g_tab)) return bail(QL_EINVAL, "velocity-set construction failed");
+            g_tab_built = true;
+        }
+    }
+    const TabView tv = tab_view(c->Q);
+    for (int k = 0; k < c->Q; ++k) {
+        c->p[k] = g_tab[tv.p + k];
+        c->w[k] = g_tab[tv.G + k * c->Q];  // w_k h_0 = w_k
+    }
+
+    // initial fields on the host, ghost columns included
+    const int64_t ncol = c->nx + 2 * kHalo;
+    std::vector<double> rho(ncol), u(ncol), T(ncol);
+    if (!initial_fields(init->kind, init->prm, c->nx, c->L, c->periodic, c->eta0, c->rho_ref, init->rho, init->u,
+                        init->T, init->ghost, kHalo, rho.data(), u.data(), T.data()))
+        return bail(QL_EINVAL, "invalid initial state for this init kind / boundary");
+
+    // device set-up
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    {
+        std::lock_guard<std::mutex> lk(g_mutex);
+        if (!g_tables_ready[c->device & 63]) {
+            e = upload_tables_f32(g_tab);
+            if (e == cudaSuccess) e = upload_tables_f64(g_tab);
+            if (e != cudaSuccess) return bail(QL_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+            g_tables_ready[c->device & 63] = true;
+        }
+    }
+    const size_t state_bytes = size_t(2 * c->Q) * size_t(c->stride) * c->elem;
+    for (int b = 0; b < 3; ++b) {
+        c->buf[b] = dev_alloc(c, state_bytes);
+        if (!c->buf[b]) return bail(QL_ENOMEM, "state buffer allocation failed");
+    }
+    c->d_fields = static_cast<double *>(dev_alloc(c, sizeof(double) * 6 * c->nx));
+    c->d_init = static_cast<double *>(dev_alloc(c, sizeof(double) * 3 * ncol));
+    c->d_partial = static_cast<double *>(dev_alloc(c, sizeof(double) * 3 * moment_blocks(c->nx)));
+    c->d_totals = static_cast<double *>(dev_alloc(c, sizeof(double) * 4));
+    c->d_tab64 = static_cast<double *>(dev_alloc(c, sizeof(double) * kTabTotal));
+    c->d_err = static_cast<unsigned *>(dev_alloc(c, 256));
+    if (!c->d_fields || !c->d_init || !c->d_partial || !c->d_totals || !c->d_tab64 || !c->d_err)
+        return bail(QL_ENOMEM, "work buffer allocation failed");
+    e = cudaMemcpyAsync(c->d_tab64, g_tab, sizeof(double) * kTabTotal, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 256, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, state_bytes, c->stream);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("set-up copy: ") + cudaGetErrorString(e));
+    ql_status st = upload_fields_and_init(c, rho.data(), u.data(), T.data());
+    if (st != QL_OK) {
+        std::string m = c->err;
+        return bail(st, m);
+    }
+    // psi^(1), psi^(2) start as copies so their ghost columns hold the fixed states
+    for (int b = 1; b < 3 && e == cudaSuccess; ++b)
+        e = cudaMemcpyAsync(c->buf[b], c->buf[0], state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+    if (!c->periodic) {
+        c->ghost_state.assign(3 * 2 * kHalo, 0.0);
+        for (int g = 0; g < 2 * kHalo; ++g) {
+            const int64_t col = g < kHalo ? g : c->nx + g;
+            c->ghost_state[3 * g] = rho[col];
+            c->ghost_state[3 * g + 1] = u[col];
+            c->ghost_state[3 * g + 2] = T[col];
+        }
+    }
+    *out = c;
+    return QL_OK;
+}
+
+ql_status ql_step(ql_ctx *c, int64_t nsteps)
+{
+    if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = stage(c, 1, c->buf[0], c->buf[0], c->buf[1]);
+        if (e == cudaSuccess) e = stage(c, 2, c->buf[1], c->buf[0], c->buf[2]);
+        if (e == cudaSuccess) e = stage(c, 3, c->buf[2], c->buf[0], c->buf[0]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+    }
+    return QL_OK;
+}
+
+ql_status ql_sync(ql_ctx *c)
+{
+    if (!c) return fail(c, QL_EINVAL, "null context");
+    return check_err_word(c);
+}
+
+static ql_status run_moments(ql_ctx *c, bool fields)
+{
+    MomentArgs a;
+    a.psi = c->buf[0];
+    a.nx = c->nx;
+    a.stride = c->stride;
+    a.eta0 = c->eta0;
+    a.inv_rho_ref = 1.0 / c->rho_ref;
+    a.dx = c->dx;
+    double *f = c->d_fields;
+    a.rho = fields ? f : nullptr;
+    a.u = fields ? f + c->nx : nullptr;
+    a.T = fields ? f + 2 * c->nx : nullptr;
+    a.P = fields ? f + 3 * c->nx : nullptr;
+    a.q = fields ? f + 4 * c->nx : nullptr;
+    a.Pxx = fields ? f + 5 * c->nx : nullptr;
+    a.partial = c->d_partial;
+    a.err = c->d_err;
+    cudaError_t e = c->precision == QL_FP32 ? launch_moments_f32(c->Q, a, c->d_tab64, c->stream)
+                                            : launch_moments_f64(c->Q, a, c->d_tab64, c->stream);
+    if (e == cudaSuccess) e = launch_reduce_totals(c->d_partial, moment_blocks(c->nx), c->d_totals, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
+    return QL_OK;
+}
+
+ql_status ql_moments(ql_ctx *c, double *rho, double *u, double *T, double *P, double *q, double *Pxx,
+                     double *totals)
+{
+    if (!c) return fail(c, QL_EINVAL, "null context");
+    ql_status st = run_moments(c, true);
+    if (st != QL_OK) return st;
+    double *outs[6] = {rho, u, T, P, q, Pxx};
+    for (int j = 0; j < 6; ++j)
+        if (outs[j])
+            QL_CUDA(c, cudaMemcpyAsync(outs[j], c->d_fields + j * c->nx, sizeof(double) * c->nx,
+                                       cudaMemcpyDeviceToHost, c->stream));
+    if (totals)
+        QL_CUDA(c, cudaMemcpyAsync(totals, c->d_totals, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    return check_err_word(c);
+}
+
+ql_status ql_totals(ql_ctx *c, double *totals)
+{
+    if (!c || !totals) return fail(c, QL_EINVAL, "bad arguments to ql_totals");
+    ql_status st = run_moments(c, false);
+    if (st != QL_OK) return st;
+    QL_CUDA(c, cudaMemcpyAsync(totals, c->d_totals, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    return check_err_word(c);
+}
+
+// rows [2Q][nx] of buffer b <-> cell-major host arrays of doubles
+static ql_status download_rows(ql_ctx *c, const void *dev, double *phi, double *theta)
+{
+    const int Q = c->Q;
+    const int64_t nx = c->nx;
+    std::vector<unsigned char> h(size_t(2 * Q) * nx * c->elem);
+    QL_CUDA(c, cudaMemcpy2DAsync(h.data(), nx * c->elem, static_cast<const unsigned char *>(dev) + kHalo * c->elem,
+                                 c->stride * c->elem, nx * c->elem, 2 * Q, cudaMemcpyDeviceToHost, c->stream));
+    QL_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int r = 0; r < 2 * Q; ++r) {
+        double *dst = r < Q ? phi : theta;
+        const int k = r < Q ? r : r - Q;
+        if (!dst) continue;
+        for (int64_t i = 0; i < nx; ++i) {
+            const size_t src = size_t(r) * nx + i;
+            dst[i * Q + k] = c->elem == 4 ? double(reinterpret_cast<const float *>(h.data())[src])
+                                          : reinterpret_cast<const double *>(h.data())[src];
+        }
+    }
+    return QL_OK;
+}
+
+ql_status ql_get_state(ql_ctx *c, double *phi, double *theta)
+{
+    if (!c) return fail(c, QL_EINVAL, "null context");
+    ql_status st = download_rows(c, c->buf[0], phi, theta);
+    if (st != QL_OK) return st;
+    return check_err_word(c);
+}
+
+ql_status ql_set_state(ql_ctx *c, const double *phi, const double *theta)
+{
+    if (!c || !phi || !theta) return fail(c, QL_EINVAL, "bad arguments to ql_set_state");
+    const int Q = c->Q;
+    const int64_t nx = c->nx;
+    std::vector<unsigned char> h(size_t(2 * Q) * nx * c->elem);
+    for (int r = 0; r < 2 * Q; ++r) {
+        const double *srcp = r < Q ? phi : theta;
+        const int k = r < Q ? r : r - Q;
+        for (int64_t i = 0; i < nx; ++i) {
+            const size_t dst = size_t(r) * nx + i;
+            if (c->elem == 4) reinterpret_cast<float *>(h.data())[dst] = float(srcp[i * Q + k]);
+            else reinterpret_cast<double *>(h.data())[dst] = srcp[i * Q + k];
+        }
+    }
+    QL_CUDA(c, cudaMemcpy2DAsync(static_cast<unsigned char *>(c->buf[0]) + kHalo * c->elem, c->stride * c->elem,
+                                 h.data(), nx * c->elem, nx * c->elem, 2 * Q, cudaMemcpyHostToDevice, c->stream));
+    if (c->periodic) {
+        cudaError_t e = c->precision == QL_FP32 ? launch_periodic_ghosts_f32(Q, c->buf[0], nx, c->stride, c->stream)
+                                                : launch_periodic_ghosts_f64(Q, c->buf[0], nx, c->stride, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ghost kernel");
+    }
+    QL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QL_OK;
+}
+
+ql_status ql_load_fields(ql_ctx *c, const double *rho, const double *u, const double *T)
+{
+    if (!c || !rho || !u || !T) return fail(c, QL_EINVAL, "bad arguments to ql_load_fields");
+    const int64_t nx = c->nx, ncol = nx + 2 * kHalo;
+    // interior columns straight from the caller's arrays (DMA when they are pinned)
+    const double *src[3] = {rho, u, T};
+    for (int f = 0; f < 3; ++f)
+        QL_CUDA(c, cudaMemcpyAsync(c->d_init + f * ncol + kHalo, src[f], sizeof(double) * nx, cudaMemcpyHostToDevice,
+                                   c->stream));
+    // ghost columns: periodic images, or the fixed states kept from creation
+    double gh[3][2 * kHalo];
+    for (int g = 0; g < 2 * kHalo; ++g) {
+        for (int f = 0; f < 3; ++f) {
+            if (c->periodic) {
+                const int64_t cell = g < kHalo ? nx - kHalo + g : g - kHalo;
+                gh[f][g] = src[f][cell];
+            } else {
+                gh[f][g] = c->ghost_state[3 * g + f];
+            }
+        }
+    }
+    for (int f = 0; f < 3; ++f) {
+        QL_CUDA(c, cudaMemcpyAsync(c->d_init + f * ncol, gh[f], sizeof(double) * kHalo, cudaMemcpyHostToDevice,
+                                   c->stream));
+        QL_CUDA(c, cudaMemcpyAsync(c->d_init + f * ncol + kHalo + nx, gh[f] + kHalo, sizeof(double) * kHalo,
+                                   cudaMemcpyHostToDevice, c->stream));
+    }
+    cudaError_t e = c->precision == QL_FP32
+                        ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
+                                          c->stride, c->d_tab64, c->stream)
+                        : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
+                                          c->stride, c->d_tab64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    QL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QL_OK;
+}
+
+ql_status ql_rhs(ql_ctx *c, double *Lphi, double *Ltheta)
+{
+    if (!c) return fail(c, QL_EINVAL, "null context");
+    cudaError_t e = stage(c, 0, c->buf[0], c->buf[0], c->buf[1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+    ql_status st = download_rows(c, c->buf[1], Lphi, Ltheta);
+    if (st != QL_OK) return st;
+    return check_err_word(c);
+}
+
+ql_status ql_state_device(ql_ctx *c, void **phi, int64_t *row_stride)
+{
+    if (!c || !phi || !row_stride) return fail(c, QL_EINVAL, "bad arguments to ql_state_device");
+    *phi = static_cast<unsigned char *>(c->buf[0]) + kHalo * c->elem;
+    *row_stride = c->stride;
+    return QL_OK;
+}
+
+ql_status ql_info(const ql_ctx *c, double *out)
+{
+    if (!c || !out) return QL_EINVAL;
+    out[0] = c->eta0;
+    out[1] = c->chi0;
+    out[2] = c->sigma;
+    out[3] = c->dx;
+    out[4] = c->dt;
+    double pm = 0;
+    for (int k = 0; k < c->Q; ++k) pm = fmax(pm, fabs(c->p[k]));
+    out[5] = pm;
+    for (int k = 0; k < c->Q; ++k) {
+        out[6 + k] = c->p[k];
+        out[6 + c->Q + k] = c->w[k];
+    }
+    return QL_OK;
+}
+
+ql_status ql_destroy(ql_ctx *c)
+{
+    if (!c) return QL_OK;
+    cudaStreamSynchronize(c->stream);
+    destroy_buffers(c);
+    delete c;
+    return QL_OK;
+}
+
+const char *ql_last_error(const ql_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+ql_status ql_velocity_set(int32_t Q, double *p, double *w)
+{
+    if (!p || !w || !gh_quadrature(Q, p, w)) return fail(nullptr, QL_EINVAL, "velocity set: Q out of range");
+    return QL_OK;
+}
+
+ql_status ql_eta_of_denseness(double denseness, double *eta0)
+{
+    if (!eta0 || !eta_of_denseness(denseness, eta0)) return fail(nullptr, QL_EINVAL, "denseness out of range");
+    return QL_OK;
+}
+
+double ql_sound_speed2(double eta0, double rho_ref, double rho, double T)
+{
+    return sound_speed2(eta0, rho_ref, rho, T);
+}
+
+ql_status ql_rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach, double *out)
+{
+    if (!out || !rankine_hugoniot(eta0, rho_ref, rho1, T1, mach, out))
+        return fail(nullptr, QL_EINVAL, "no compressive Rankine-Hugoniot solution");
+    return QL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fixed-order sum of the per-block partial totals (one block).
+__global__ void qlbm_reduce_totals_kernel(const double *__restrict__ partial, int64_t nblocks,
+                                          double *__restrict__ totals)
+{
+    __shared__ double red[3][256];
+    double s[3] = {0, 0, 0};
+    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) s[c] += partial[b * 3 + c];
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) totals[threadIdx.x] = red[threadIdx.x][0];
+}
+
+namespace qlbm {
+cudaError_t launch_reduce_totals(const double *partial, int64_t nblocks, double *totals, cudaStream_t s)
+{
+    qlbm_reduce_totals_kernel<<<1, 256, 0, s>>>(partial, nblocks, totals);
+    return cudaGetLastError();
+}
+}  // namespace qlbm

@@ -1,0 +1,281 @@
+// Host-side physics in FP64 (see qlbm_host.h).
+#include "qlbm_host.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "qlbm_internal.h"
+
+namespace qlbm {
+
+static const double kPi = 3.14159265358979323846;
+
+// Orthonormal Hermite values h_l(x) = He_l(x)/sqrt(l!) for l = 0..n, by the
+// normalised three-term recurrence (no factorial, no overflow for n <= 200).
+static void hermite_normalised(int n, double x, double *h)
+{
+    h[0] = 1.0;
+    if (n >= 1) h[1] = x;
+    for (int l = 1; l < n; ++l) h[l + 1] = (x * h[l] - sqrt(double(l)) * h[l - 1]) / sqrt(double(l + 1));
+}
+
+bool gh_quadrature(int Q, double *p, double *w)
+{
+    if (Q < 1 || Q > 200) return false;
+    std::vector<double> prev(1, 0.0), cur, h(Q + 2);
+    // Zeros of He_n interlace those of He_{n-1}; build them for n = 1..Q, each
+    // by Newton's method safeguarded by bisection inside its bracket.
+    for (int n = 2; n <= Q; ++n) {
+        const double B = sqrt(4.0 * n + 2.0);
+        cur.assign(n, 0.0);
+        for (int j = 0; j < n; ++j) {
+            double lo = j == 0 ? -B : prev[j - 1];
+            double hi = j == n - 1 ? B : prev[j];
+            hermite_normalised(n, lo, h.data());
+            double flo = h[n];
+            double x = 0.5 * (lo + hi);
+            for (int it = 0; it < 200; ++it) {
+                hermite_normalised(n, x, h.data());
+                const double f = h[n], df = sqrt(double(n)) * h[n - 1];
+                if (f == 0.0) break;
+                if ((f < 0.0) == (flo < 0.0)) { lo = x; flo = f; } else { hi = x; }
+                double xn = x - f / df;
+                if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+                const double step = fabs(xn - x);
+                x = xn;
+                if (step <= 4e-16 * (fabs(x) + 1.0)) break;
+            }
+            cur[j] = x;
+        }
+        prev.swap(cur);
+    }
+    if (Q == 1) prev.assign(1, 0.0);
+    // Christoffel weights for the probability weight exp(-p^2/2)/sqrt(2 pi):
+    // w_k = 1 / sum_{l<Q} h_l(p_k)^2.
+    for (int k = 0; k < Q; ++k) {
+        hermite_normalised(Q - 1, prev[k], h.data());
+        double s = 0.0;
+        for (int l = 0; l < Q; ++l) s += h[l] * h[l];
+        p[k] = prev[k];
+        w[k] = 1.0 / s;
+    }
+    // exact mirror symmetry of the set
+    for (int k = 0; k < Q / 2; ++k) {
+        const double a = 0.5 * (p[Q - 1 - k] - p[k]);
+        const double b = 0.5 * (w[k] + w[Q - 1 - k]);
+        p[k] = -a;
+        p[Q - 1 - k] = a;
+        w[k] = w[Q - 1 - k] = b;
+    }
+    if (Q % 2) p[Q / 2] = 0.0;
+    double sum = 0.0;
+    for (int k = 0; k < Q; ++k) {
+        if (!isfinite(p[k]) || !(w[k] > 0.0)) return false;
+        sum += w[k];
+    }
+    return fabs(sum - 1.0) < 1e-12;
+}
+
+double chi_set(double eta) { return 0.5 * (2.0 - eta) / ((1.0 - eta) * (1.0 - eta) * (1.0 - eta)); }
+
+static double dchi_deta(double eta)
+{
+    const double o = 1.0 - eta;
+    return (5.0 - 2.0 * eta) / (2.0 * o * o * o * o);
+}
+
+double cs_z(double eta) { return 1.0 + 4.0 * eta * chi_set(eta); }
+double cs_dz(double eta) { return 4.0 * (chi_set(eta) + eta * dchi_deta(eta)); }
+
+double denseness_of_eta(double eta) { return 6.0 * sqrt(2.0) * eta * chi_set(eta); }
+
+bool eta_of_denseness(double El, double *eta)
+{
+    if (!(El >= 0.0) || El > denseness_of_eta(0.49)) return false;
+    if (El == 0.0) { *eta = 0.0; return true; }
+    double lo = 0.0, hi = 0.49, x = El / (6.0 * sqrt(2.0));
+    for (int it = 0; it < 200; ++it) {
+        const double f = denseness_of_eta(x) - El;
+        if (f == 0.0) break;
+        if (f < 0.0) lo = x; else hi = x;
+        const double df = 6.0 * sqrt(2.0) * (chi_set(x) + x * dchi_deta(x));
+        double xn = x - f / df;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        const double step = fabs(xn - x);
+        x = xn;
+        if (step <= 1e-17 + 2e-16 * x) break;
+    }
+    *eta = x;
+    return true;
+}
+
+double sound_speed2(double eta0, double rho_ref, double rho, double T)
+{
+    const double eta = eta0 * rho / rho_ref;
+    const double Z = cs_z(eta);
+    return T * (Z + eta * cs_dz(eta)) + (2.0 / 3.0) * T * Z * Z;
+}
+
+// Energy balance per unit mass flux across a standing shock, for a trial
+// downstream density; mass and momentum balance give u2 and P2.
+static double rh_residual(double eta0, double rho_ref, double rho1, double u1, double T1, double rho2,
+                          double *u2o, double *T2o)
+{
+    const double P1 = rho1 * T1 * cs_z(eta0 * rho1 / rho_ref);
+    const double u2 = rho1 * u1 / rho2;
+    const double P2 = P1 + rho1 * u1 * (u1 - u2);
+    const double T2 = P2 / (rho2 * cs_z(eta0 * rho2 / rho_ref));
+    if (u2o) *u2o = u2;
+    if (T2o) *T2o = T2;
+    return (1.5 * T1 + 0.5 * u1 * u1 + P1 / rho1) - (1.5 * T2 + 0.5 * u2 * u2 + P2 / rho2);
+}
+
+bool rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach, double *out)
+{
+    if (!(mach > 1.0) || !(rho1 > 0.0) || !(T1 > 0.0)) return false;
+    const double u1 = mach * sqrt(sound_speed2(eta0, rho_ref, rho1, T1));
+    double rmax = 4.0 * rho1;
+    if (eta0 > 0.0) rmax = fmin(rmax, 0.49 * rho_ref / eta0);
+    // bracket: the residual changes sign once between rho1 and rmax
+    double a = rho1 * (1.0 + 1e-7);
+    double fa = rh_residual(eta0, rho_ref, rho1, u1, T1, a, nullptr, nullptr);
+    double b = a, fb = fa;
+    bool found = false;
+    for (int j = 1; j <= 400; ++j) {
+        b = rho1 + (rmax - rho1) * j / 400.0;
+        fb = rh_residual(eta0, rho_ref, rho1, u1, T1, b, nullptr, nullptr);
+        if ((fb < 0.0) != (fa < 0.0)) { found = true; break; }
+        a = b;
+        fa = fb;
+    }
+    if (!found) return false;
+    // Illinois variant of regula falsi
+    int side = 0;
+    double c = a;
+    for (int it = 0; it < 200; ++it) {
+        c = (a * fb - b * fa) / (fb - fa);
+        const double fc = rh_residual(eta0, rho_ref, rho1, u1, T1, c, nullptr, nullptr);
+        if (fc == 0.0 || fabs(b - a) < 1e-15 * c) break;
+        if ((fc < 0.0) == (fb < 0.0)) {
+            b = c; fb = fc;
+            if (side == -1) fa *= 0.5;
+            side = -1;
+        } else {
+            a = c; fa = fc;
+            if (side == 1) fb *= 0.5;
+            side = 1;
+        }
+    }
+    double u2, T2;
+    rh_residual(eta0, rho_ref, rho1, u1, T1, c, &u2, &T2);
+    out[0] = u1;
+    out[1] = c;
+    out[2] = u2;
+    out[3] = T2;
+    return true;
+}
+
+bool initial_fields(int kind, const double *prm, int64_t nx, double length, int periodic, double eta0,
+                    double rho_ref, const double *urho, const double *uu, const double *uT,
+                    const double *ughost, int halo, double *rho, double *u, double *T)
+{
+    const double dx = length / double(nx);
+    const int64_t ncol = nx + 2 * halo;
+    double rh[4] = {0, 0, 0, 0};
+    if (kind == 2 && !rankine_hugoniot(eta0, rho_ref, prm[0], prm[1], prm[2], rh)) return false;
+    if (kind == 0 && !periodic) return false;
+    if (kind == 3 && (!urho || !uu || !uT || (!periodic && !ughost))) return false;
+    const double P0 = kind == 0 ? prm[0] * prm[1] * cs_z(eta0 * prm[0] / rho_ref) : 0.0;
+    for (int64_t c = 0; c < ncol; ++c) {
+        const int64_t i = c - halo;
+        if (i < 0 || i >= nx) continue;
+        const double x = (double(i) + 0.5) * dx;
+        double r, v, t;
+        switch (kind) {
+        case 0:
+            r = prm[0] * (1.0 + prm[2] * cos(2.0 * kPi * x / length));
+            v = 0.0;
+            t = P0 / (r * cs_z(eta0 * r / rho_ref));
+            break;
+        case 1: {
+            const bool left = x < 0.5 * length;
+            r = left ? prm[0] : prm[3];
+            v = left ? prm[1] : prm[4];
+            t = left ? prm[2] : prm[5];
+        } break;
+        case 2: {
+            const double s = 0.5 * (1.0 + tanh((x - 0.5 * length) / prm[3]));
+            r = prm[0] + (rh[1] - prm[0]) * s;
+            v = rh[0] + (rh[2] - rh[0]) * s;
+            t = prm[1] + (rh[3] - prm[1]) * s;
+        } break;
+        case 3:
+            r = urho[i];
+            v = uu[i];
+            t = uT[i];
+            break;
+        default:
+            return false;
+        }
+        rho[c] = r;
+        u[c] = v;
+        T[c] = t;
+    }
+    // ghost columns
+    for (int g = 0; g < halo; ++g) {
+        const int64_t cl = g, cr = halo + nx + g;  // cells g - halo and nx + g
+        if (periodic) {
+            const int64_t sl = halo + ((g - halo) % nx + nx) % nx, sr = halo + (g % nx);
+            rho[cl] = rho[sl]; u[cl] = u[sl]; T[cl] = T[sl];
+            rho[cr] = rho[sr]; u[cr] = u[sr]; T[cr] = T[sr];
+            continue;
+        }
+        double L3[3], R3[3];
+        if (kind == 1) {
+            L3[0] = prm[0]; L3[1] = prm[1]; L3[2] = prm[2];
+            R3[0] = prm[3]; R3[1] = prm[4]; R3[2] = prm[5];
+        } else if (kind == 2) {
+            L3[0] = prm[0]; L3[1] = rh[0]; L3[2] = prm[1];
+            R3[0] = rh[1]; R3[1] = rh[2]; R3[2] = rh[3];
+        } else {
+            // user ghosts for cells -3, -2, -1, nx, nx+1, nx+2; the outermost
+            // padding column repeats its neighbour
+            const int gl = g < halo - 3 ? 0 : g - (halo - 3);
+            const int gr = g < 3 ? g : 2;
+            for (int c = 0; c < 3; ++c) {
+                L3[c] = ughost[3 * gl + c];
+                R3[c] = ughost[3 * (3 + gr) + c];
+            }
+        }
+        rho[cl] = L3[0]; u[cl] = L3[1]; T[cl] = L3[2];
+        rho[cr] = R3[0]; u[cr] = R3[1]; T[cr] = R3[2];
+    }
+    for (int64_t c = 0; c < ncol; ++c)
+        if (!(rho[c] > 0.0) || !(T[c] > 0.0) || !isfinite(u[c])) return false;
+    return true;
+}
+
+bool build_tables(double *all)
+{
+    memset(all, 0, sizeof(double) * kTabTotal);
+    for (int j = 0; j < kNumQ; ++j) {
+        const int Q = kQList[j];
+        const TabView tv = tab_view(Q);
+        double p[kMaxQ], w[kMaxQ], h[kMaxQ + 2];
+        if (!gh_quadrature(Q, p, w)) return false;
+        for (int k = 0; k < Q; ++k) {
+            all[tv.p + k] = p[k];
+            all[tv.p2 + k] = p[k] * p[k];
+            all[tv.p3 + k] = p[k] * p[k] * p[k];
+            hermite_normalised(Q - 1, p[k], h);
+            for (int l = 0; l < Q; ++l) all[tv.G + k * Q + l] = w[k] * h[l];
+        }
+        for (int l = 1; l < Q; ++l) all[tv.ca + l] = 1.0 / sqrt(double(l));
+        for (int l = 2; l < Q; ++l) all[tv.cb + l] = sqrt(double(l - 1) / double(l));
+    }
+    return true;
+}
+
+}  // namespace qlbm

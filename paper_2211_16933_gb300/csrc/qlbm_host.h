@@ -1,0 +1,39 @@
+// Host-side physics of the solver in FP64: velocity set, equation of state,
+// parameter mapping, Rankine-Hugoniot states and initial fields.
+#pragma once
+#include <stdint.h>
+
+namespace qlbm {
+
+// Sec. II.D: roots of He_Q (ascending) and Gauss weights (sum 1).
+// Returns false if Q is out of range (1..200) or a root was not resolved.
+bool gh_quadrature(int Q, double *p, double *w);
+
+// Sec. II.A, Eq. (chi): chi_SET(eta) and the Carnahan-Starling factor
+// Z = P/(n T) = 1 + 4 eta chi.
+double chi_set(double eta);
+double cs_z(double eta);
+double cs_dz(double eta);  // dZ/deta
+
+// Sec. II.B: E_l = 6 sqrt(2) eta chi(eta); inverse on [0, 0.5).
+double denseness_of_eta(double eta);
+bool eta_of_denseness(double El, double *eta);
+
+// Adiabatic sound speed squared of the dense gas, Eq. (sw_cs) with c_V = 3/2:
+// c_s^2 = T (Z + eta Z') + (2/3) T Z^2, eta = eta0 rho / rho_ref.
+double sound_speed2(double eta0, double rho_ref, double rho, double T);
+
+// Eq. (rankine_hugoniot) for a standing shock.  out = {u1, rho2, u2, T2}.
+bool rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach, double *out);
+
+// Initial fields at cells -halo .. nx+halo-1 (arrays of nx + 2 halo).
+// kind/prm as in ql_init; user fields/ghost for kind 3.  Returns false on
+// invalid parameters.
+bool initial_fields(int kind, const double *prm, int64_t nx, double length, int periodic,
+                    double eta0, double rho_ref, const double *urho, const double *uu, const double *uT,
+                    const double *ughost, int halo, double *rho, double *u, double *T);
+
+// All kernel tables (layout of tab_view in qlbm_internal.h).
+bool build_tables(double *all);
+
+}  // namespace qlbm

@@ -1,0 +1,117 @@
+// Internal interface between the C ABI (qlbm_api.cu) and the per-precision
+// kernel translation units (fdlb_f32.cu, fdlb_f64.cu).  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define QL_HD __host__ __device__
+#else
+#define QL_HD
+#endif
+
+namespace qlbm {
+
+// Velocity-set sizes with compiled kernels.
+constexpr int kNumQ = 4;
+constexpr int kQList[kNumQ] = {8, 16, 24, 32};
+constexpr int kMaxQ = 32;
+
+// CTA geometry of the stage kernel.  A CTA stages kSeg consecutive cells of
+// every (component, velocity) row in shared memory: kTile cells it updates
+// plus kHalo cells on each side (the WENO-5 and 6th-order stencils reach 3).
+// Each warp updates 31 cells; its lane 0 computes the flux on the warp's
+// left face.
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kTile = 31 * kWarps;
+constexpr int kHalo = 4;
+constexpr int kSeg = kTile + 2 * kHalo;
+static_assert(kSeg == kThreads, "one staged cell per thread in the moment phase");
+
+// Row layout of a state buffer: 2Q rows (phi rows k = 0..Q-1, then theta
+// rows), each of `stride` elements; cell i (-kHalo <= i < nx + kHalo) of row r
+// sits at r * stride + kHalo + i.  stride covers every staged segment of the
+// last tile and is a multiple of 32 elements.
+inline int64_t num_tiles(int64_t nx) { return (nx + kTile - 1) / kTile; }
+inline int64_t row_stride(int64_t nx)
+{
+    int64_t need = (num_tiles(nx) - 1) * kTile + kSeg;
+    if (need < nx + 2 * kHalo) need = nx + 2 * kHalo;
+    return (need + 31) / 32 * 32;
+}
+
+// Per-Q constant tables, built on the host in FP64 and stored per precision.
+//   p[k], p2[k] = p^2, p3[k] = p^3: velocities, ascending
+//   G[k][l] = w_k He_l(p_k) / sqrt(l!)    (normalised Hermite basis)
+//   ca[l] = 1/sqrt(l), cb[l] = sqrt((l-1)/l)  (l >= 2), for the recurrence of
+//   the normalised equilibrium coefficients c^_l = c_l sqrt(l!):
+//   c^_0 = 1, c^_1 = u, c^_l = ca[l] u c^_{l-1} + cb[l] (T-1) c^_{l-2}.
+QL_HD constexpr int tab_size(int Q) { return Q * Q + 5 * Q; }
+QL_HD constexpr int tab_offset(int Q)
+{
+    // tables of the sizes in kQList, in ascending order
+    return (Q > 8 ? tab_size(8) : 0) + (Q > 16 ? tab_size(16) : 0) + (Q > 24 ? tab_size(24) : 0) +
+           (Q > 32 ? tab_size(32) : 0);
+}
+constexpr int kTabTotal = tab_offset(1 << 30);
+struct TabView {
+    int p, p2, p3, G, ca, cb;
+};
+QL_HD constexpr TabView tab_view(int Q)
+{
+    return TabView{tab_offset(Q), tab_offset(Q) + Q, tab_offset(Q) + 2 * Q, tab_offset(Q) + 3 * Q,
+                   tab_offset(Q) + 3 * Q + Q * Q, tab_offset(Q) + 4 * Q + Q * Q};
+}
+
+struct StageArgs {
+    const void *in;    // stage input psi^(s-1)
+    const void *base;  // psi^n (read by stages 2 and 3)
+    void *out;         // stage output (or L[psi] for stage 0)
+    int64_t nx;
+    int64_t stride;
+    double inv_dx, dt;
+    double eta0, inv_rho_ref, tau_pref, pr_const;
+    int pr_mode, enskog, periodic, pad_;
+    unsigned *err;  // device error word; bit 0: non-physical cell
+};
+
+// Uploads all tables (kTabTotal doubles, laid out by tab_view) to the
+// current device, rounded to the precision of the translation unit.
+cudaError_t upload_tables_f32(const double *all);
+cudaError_t upload_tables_f64(const double *all);
+
+// stage: 0 writes L[psi] into out, 1..3 are the stages of Eq. (rk3).
+cudaError_t launch_stage_f32(int Q, int stage, const StageArgs &a, cudaStream_t s);
+cudaError_t launch_stage_f64(int Q, int stage, const StageArgs &a, cudaStream_t s);
+
+// psi = discrete equilibrium of (rho, u, T) given for cells -kHalo .. nx+kHalo-1
+// (device arrays of nx + 2 kHalo doubles); interior and ghost columns.
+// tab64: the FP64 tables (kTabTotal doubles, device memory).
+cudaError_t launch_init_f32(int Q, const double *rho, const double *u, const double *T, void *psi,
+                            int64_t nx, int64_t stride, const double *tab64, cudaStream_t s);
+cudaError_t launch_init_f64(int Q, const double *rho, const double *u, const double *T, void *psi,
+                            int64_t nx, int64_t stride, const double *tab64, cudaStream_t s);
+
+// Copies the kHalo cells next to each end into the ghost columns of the
+// other end (periodic images), all 2Q rows.
+cudaError_t launch_periodic_ghosts_f32(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s);
+cudaError_t launch_periodic_ghosts_f64(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s);
+
+// Output fields in FP64 per interior cell and per-block partial totals.
+struct MomentArgs {
+    const void *psi;
+    int64_t nx, stride;
+    double eta0, inv_rho_ref, dx;
+    double *rho, *u, *T, *P, *q, *Pxx;  // each nx doubles (device), any may be null
+    double *partial;                    // [nblocks][3] (device)
+    unsigned *err;
+};
+constexpr int kMomThreads = 256;
+inline int64_t moment_blocks(int64_t nx) { return (nx + kMomThreads - 1) / kMomThreads; }
+cudaError_t launch_moments_f32(int Q, const MomentArgs &a, const double *tab64, cudaStream_t s);
+cudaError_t launch_moments_f64(int Q, const MomentArgs &a, const double *tab64, cudaStream_t s);
+// totals[3] = fixed-order sum of partial[nblocks][3]
+cudaError_t launch_reduce_totals(const double *partial, int64_t nblocks, double *totals, cudaStream_t s);
+
+}  // namespace qlbm

@@ -1,0 +1,78 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle legs.
+
+Only workload parameters and random numbers live here: sizes, physical
+parameters, seeds and smooth random fields.  No arithmetic of the method (no
+equation of state, equilibrium, quadrature or time step rule of the solver) is
+computed in this module.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def cfl_dt(dx: float, pmax: float, cfl: float = 0.4) -> float:
+    """Time step dt = cfl * dx / max|p_k|; pmax is supplied by the caller."""
+    return cfl * dx / pmax
+
+
+def sound_wave(nx=256, Q=16):
+    """1D sound wave: periodic, L = 1, E_l = 0.1, Kn = 0.1, constant Pr = 2/3, rho0 = T0 = 1,
+    relative density amplitude 1e-3, delta P = 0, 2000 steps."""
+    return dict(name=f"sound_wave_nx{nx}_Q{Q}", Q=Q, nx=nx, length=1.0, denseness=0.1, kn=0.1,
+                bc="periodic", init="sound", prm=(1.0, 1.0, 1e-3), pr_mode="const", pr_const=2.0 / 3.0,
+                steps=2000)
+
+
+def normal_shock(mach=2.0, denseness=0.1, nx=4096, Q=32):
+    """Standing normal shock: domain of 128 upstream mean free paths (Kn = 1/128), upstream
+    rho = T = 1, tanh initial profile of width 4 mean free paths, fixed far-field ghosts, dense Pr."""
+    return dict(name=f"shock_M{mach}_El{denseness}_nx{nx}_Q{Q}", Q=Q, nx=nx, length=128.0,
+                denseness=denseness, kn=1.0 / 128.0, bc="fixed", init="shock", prm=(1.0, 1.0, mach, 4.0),
+                pr_mode="dense", pr_const=2.0 / 3.0, steps=None)
+
+
+def sod_tube(nx=1 << 22, Q=32):
+    """Sod shock tube for the roofline: L = 1, E_l = 0.1 and Kn = 0.05 on the left state,
+    rho_R = rho_L / 8 (eta_R = eta_L / 8), T = 1, u = 0, fixed ghosts, dense Pr, 1000 steps."""
+    return dict(name=f"sod_nx{nx}_Q{Q}", Q=Q, nx=nx, length=1.0, denseness=0.1, kn=0.05, bc="fixed",
+                init="riemann", prm=(1.0, 0.0, 1.0, 0.125, 0.0, 1.0), pr_mode="dense", pr_const=2.0 / 3.0,
+                steps=1000)
+
+
+def smooth_periodic_fields(nx: int, seed: int, amp=(0.05, 0.1, 0.05), modes: int = 3):
+    """Random smooth periodic (rho, u, T) around (1, 0, 1): a few Fourier modes with
+    seeded amplitudes and phases."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    out = []
+    for j, base in enumerate((1.0, 0.0, 1.0)):
+        f = np.full(nx, base)
+        for m in range(1, modes + 1):
+            f += amp[j] / m * rng.uniform(-1, 1) * np.cos(2 * np.pi * m * x + rng.uniform(0, 2 * np.pi))
+        out.append(f)
+    return out
+
+
+def state_noise(shape, seed: int, scale: float = 1e-2):
+    """Seeded multiplicative noise (1 + scale * N(0,1)) used to take a state off equilibrium."""
+    rng = np.random.default_rng(seed)
+    return 1.0 + scale * rng.standard_normal(shape)
+
+
+def batch_instances(n=4096, seed=20221130):
+    """Uneven batch: half sound waves, half normal shocks; Nx ~ U{256..8192}, Q ~ U{16, 24, 32},
+    E_l ~ U[0.02, 0.3], shock Mach ~ U[1.2, 3]."""
+    rng = np.random.default_rng(seed)
+    inst = []
+    for i in range(n):
+        kind = i % 2
+        nx = int(rng.integers(256, 8193))
+        Q = int(rng.choice([16, 24, 32]))
+        El = float(rng.uniform(0.02, 0.3))
+        mach = float(rng.uniform(1.2, 3.0))
+        if kind == 0:
+            inst.append(dict(kind="sound", nx=nx, Q=Q, denseness=El, kn=0.1, length=1.0, prm=(1.0, 1.0, 1e-3)))
+        else:
+            inst.append(dict(kind="shock", nx=nx, Q=Q, denseness=El, kn=1.0 / 128.0, length=128.0,
+                             prm=(1.0, 1.0, mach, 4.0)))
+    return inst

@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libqlbm.so (include/qlbm.h), with the same entry-point names.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+PyTorch, when present, supplies the device allocator (its caching allocator)
+and the stream.  There is no fallback: if the library has not been built this
+module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqlbm.so")
+
+QL_OK, QL_EINVAL, QL_ENOMEM, QL_ECUDA, QL_ENONPHYSICAL, QL_ETIMEOUT, QL_EUNSUPPORTED = range(7)
+QL_FP64, QL_FP32 = 0, 1
+QL_BC_PERIODIC, QL_BC_FIXED = 0, 1
+QL_INIT_SOUND, QL_INIT_RIEMANN, QL_INIT_SHOCK, QL_INIT_FIELDS = 0, 1, 2, 3
+QL_PR_CONST, QL_PR_DENSE = 0, 1
+SUPPORTED_Q = (8, 16, 24, 32)
+EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_get_state", "ql_set_state",
+            "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",
+            "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error")
+
+
+class QLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"qlbm status {status}: {msg}")
+        self.status = status
+
+
+class ql_velset(C.Structure):
+    _fields_ = [("Q", C.c_int32), ("kind", C.c_int32)]
+
+
+class ql_grid(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("length", C.c_double), ("dt", C.c_double)]
+
+
+class ql_bc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class ql_init(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("prm", C.c_double * 8),
+                ("rho", _DP), ("u", _DP), ("T", _DP), ("ghost", _DP)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class ql_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("pr_mode", C.c_int32), ("enskog", C.c_int32), ("device", C.c_int32),
+                ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libqlbm.so; raises if it is missing (build it with paper_2211_16933_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        V = C.c_void_p
+        L.ql_create.argtypes = [C.POINTER(ql_velset), C.POINTER(ql_grid), C.c_double, C.c_double, C.POINTER(ql_bc),
+                                C.POINTER(ql_init), C.POINTER(ql_opts), C.POINTER(V)]
+        L.ql_step.argtypes = [V, C.c_int64]
+        L.ql_sync.argtypes = [V]
+        L.ql_moments.argtypes = [V] + [_DP] * 7
+        L.ql_totals.argtypes = [V, _DP]
+        L.ql_get_state.argtypes = [V, _DP, _DP]
+        L.ql_set_state.argtypes = [V, _DP, _DP]
+        L.ql_load_fields.argtypes = [V, _DP, _DP, _DP]
+        L.ql_rhs.argtypes = [V, _DP, _DP]
+        L.ql_state_device.argtypes = [V, C.POINTER(V), C.POINTER(C.c_int64)]
+        L.ql_info.argtypes = [V, _DP]
+        L.ql_destroy.argtypes = [V]
+        L.ql_last_error.argtypes = [V]
+        L.ql_last_error.restype = C.c_char_p
+        L.ql_velocity_set.argtypes = [C.c_int32, _DP, _DP]
+        L.ql_eta_of_denseness.argtypes = [C.c_double, _DP]
+        L.ql_sound_speed2.argtypes = [C.c_double] * 4
+        L.ql_sound_speed2.restype = C.c_double
+        L.ql_rankine_hugoniot.argtypes = [C.c_double] * 5 + [_DP]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def _check(st, ctx=None):
+    if st != QL_OK:
+        msg = lib().ql_last_error(ctx)
+        raise QLError(st, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- host-only helpers
+def ql_velocity_set(Q: int):
+    p, w = np.zeros(Q), np.zeros(Q)
+    _check(lib().ql_velocity_set(Q, _ptr(p), _ptr(w)))
+    return p, w
+
+
+def ql_eta_of_denseness(El: float) -> float:
+    out = C.c_double()
+    _check(lib().ql_eta_of_denseness(El, C.byref(out)))
+    return out.value
+
+
+def ql_sound_speed2(eta0, rho_ref, rho, T) -> float:
+    return lib().ql_sound_speed2(eta0, rho_ref, rho, T)
+
+
+def ql_rankine_hugoniot(eta0, rho_ref, rho1, T1, mach):
+    out = np.zeros(4)
+    _check(lib().ql_rankine_hugoniot(eta0, rho_ref, rho1, T1, mach, _ptr(out)))
+    return tuple(out)
+
+
+# ---------------------------------------------------------------- context entry points
+def ql_create(vs, grid, denseness, kn, bc, init, opts):
+    ctx = C.c_void_p()
+    _check(lib().ql_create(C.byref(vs), C.byref(grid), denseness, kn, C.byref(bc), C.byref(init), C.byref(opts),
+                           C.byref(ctx)))
+    return ctx
+
+
+def ql_step(ctx, nsteps: int):
+    _check(lib().ql_step(ctx, nsteps), ctx)
+
+
+def ql_sync(ctx):
+    _check(lib().ql_sync(ctx), ctx)
+
+
+def ql_moments(ctx, rho=None, u=None, T=None, P=None, q=None, Pxx=None, totals=None):
+    _check(lib().ql_moments(ctx, *[_ptr(a) for a in (rho, u, T, P, q, Pxx, totals)]), ctx)
+
+
+def ql_totals(ctx, totals):
+    _check(lib().ql_totals(ctx, _ptr(totals)), ctx)
+
+
+def ql_get_state(ctx, phi, theta):
+    _check(lib().ql_get_state(ctx, _ptr(phi), _ptr(theta)), ctx)
+
+
+def ql_set_state(ctx, phi, theta):
+    _check(lib().ql_set_state(ctx, _ptr(phi), _ptr(theta)), ctx)
+
+
+def ql_load_fields(ctx, rho, u, T):
+    _check(lib().ql_load_fields(ctx, _ptr(rho), _ptr(u), _ptr(T)), ctx)
+
+
+def ql_rhs(ctx, Lphi, Ltheta):
+    _check(lib().ql_rhs(ctx, _ptr(Lphi), _ptr(Ltheta)), ctx)
+
+
+def ql_state_device(ctx):
+    p, s = C.c_void_p(), C.c_int64()
+    _check(lib().ql_state_device(ctx, C.byref(p), C.byref(s)), ctx)
+    return p.value, s.value
+
+
+def ql_info(ctx, Q):
+    out = np.zeros(6 + 2 * Q)
+    _check(lib().ql_info(ctx, _ptr(out)), ctx)
+    return out
+
+
+def ql_destroy(ctx):
+    _check(lib().ql_destroy(ctx))
+
+
+# ---------------------------------------------------------------- convenience object
+class Solver:
+    """One solver context.  Device memory comes from PyTorch's caching allocator and
+    work goes on PyTorch's current stream when torch is importable with CUDA."""
+
+    def __init__(self, Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND,
+                 prm=(1.0, 1.0, 1e-3), rho=None, u=None, T=None, ghost=None, precision=QL_FP64,
+                 pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, device=0, use_torch=True):
+        self.Q, self.nx, self.precision = Q, nx, precision
+        vs = ql_velset(Q, 0)
+        grid = ql_grid(nx, length, dt)
+        b = ql_bc(bc, 0)
+        ini = ql_init()
+        ini.kind = init_kind
+        for j, v in enumerate(prm):
+            ini.prm[j] = v
+        self._keep = []
+        for name, arr in (("rho", rho), ("u", u), ("T", T), ("ghost", ghost)):
+            if arr is not None:
+                a = np.ascontiguousarray(arr, dtype=np.float64)
+                self._keep.append(a)
+                setattr(ini, name, _ptr(a))
+        o = ql_opts()
+        o.precision, o.pr_mode, o.enskog, o.device = precision, pr_mode, enskog, device
+        o.pr_const, o.rho_ref = pr_const, rho_ref
+        self._torch_blocks = {}
+        if use_torch:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.set_device(device)
+                stream = torch.cuda.current_stream(device)
+                o.stream = C.c_void_p(stream.cuda_stream)
+                self._stream = stream
+
+                def _alloc(nbytes, user):
+                    ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+                    self._torch_blocks[ptr] = nbytes
+                    return ptr
+
+                def _free(ptr, user):
+                    if ptr in self._torch_blocks:
+                        del self._torch_blocks[ptr]
+                        torch.cuda.caching_allocator_delete(ptr)
+
+                self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+                o.alloc, o.free = self._alloc_cb, self._free_cb
+        self.ctx = ql_create(vs, grid, denseness, kn, b, ini, o)
+        info = ql_info(self.ctx, Q)
+        self.eta0, self.chi0, self.sigma, self.dx, self.dt, self.pmax = info[:6]
+        self.p, self.w = info[6:6 + Q], info[6 + Q:]
+
+    def step(self, n=1):
+        ql_step(self.ctx, n)
+
+    def sync(self):
+        ql_sync(self.ctx)
+
+    def moments(self):
+        out = {k: np.zeros(self.nx) for k in ("rho", "u", "T", "P", "q", "Pxx")}
+        tot = np.zeros(3)
+        ql_moments(self.ctx, out["rho"], out["u"], out["T"], out["P"], out["q"], out["Pxx"], tot)
+        out["totals"] = tot
+        return out
+
+    def totals(self):
+        t = np.zeros(3)
+        ql_totals(self.ctx, t)
+        return t
+
+    def state(self):
+        phi, th = np.zeros(self.nx * self.Q), np.zeros(self.nx * self.Q)
+        ql_get_state(self.ctx, phi, th)
+        return phi.reshape(self.nx, self.Q), th.reshape(self.nx, self.Q)
+
+    def set_state(self, phi, theta):
+        ql_set_state(self.ctx, np.ascontiguousarray(phi, dtype=np.float64).ravel(),
+                     np.ascontiguousarray(theta, dtype=np.float64).ravel())
+
+    def load_fields(self, rho, u, T):
+        f = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, u, T)]
+        ql_load_fields(self.ctx, *f)
+
+    def rhs(self):
+        a, b = np.zeros(self.nx * self.Q), np.zeros(self.nx * self.Q)
+        ql_rhs(self.ctx, a, b)
+        return a.reshape(self.nx, self.Q), b.reshape(self.nx, self.Q)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            ql_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (normalised by reference scales rho_ref = T_ref = 1, u by sqrt(T_ref),
+P by rho_ref T_ref (1 + b rho chi)_ref, q by rho_ref T_ref^(3/2)):
+  FP64 mode  <= 1e-10 in L-infinity for rho, u, T, P, q and for every psi_k
+             (relative to the largest |psi_k| of that velocity);
+  FP32 mode  <= 1e-5 for the moments, <= 2e-5 for psi_k relative per velocity.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2211_16933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-5}          # moments, by precision (QL_FP64 = 0, QL_FP32 = 1)
+TOL_PSI = {0: 1e-10, 1: 2e-5}
+
+
+def _setup(q, w, precision, dt=None, fields=None, ghost=None, enskog=1):
+    """Oracle model + initial state and a GPU solver for the same workload dict."""
+    Q, nx, L = w["Q"], w["nx"], w["length"]
+    p, _ = O.quadrature(Q)
+    dt = dt or inputs.cfl_dt(L / nx, abs(p).max())
+    bc = O.BC_PERIODIC if w["bc"] == "periodic" else O.BC_FIXED
+    prm = 1 if w["pr_mode"] == "dense" else 0
+    m = O.make_model(Q, nx, L, dt, w["denseness"], w["kn"], pr_mode=prm, pr_const=w["pr_const"], bc=bc,
+                     enskog=enskog)
+    kind = {"sound": O.INIT_SOUND, "riemann": O.INIT_RIEMANN, "shock": O.INIT_SHOCK, "fields": 3}[w["init"]]
+    kw = {}
+    if kind == 3:
+        r, u, T = fields
+        kw = dict(rho=r, u=u, T=T)
+        if bc == O.BC_FIXED:
+            O.set_ghosts(m, ghost[:3], ghost[3:])
+            kw["ghost"] = np.asarray(ghost, dtype=float).ravel()
+    else:
+        r, u, T = O.init_fields(m, kind, w["prm"])
+        if bc == O.BC_FIXED:
+            O.set_ghosts_from_init(m, kind, w["prm"])
+    ph, th = O.equilibrium_state(m, r, u, T)
+    s = q.Solver(Q, nx, L, dt, w["denseness"], w["kn"], bc=bc, init_kind=kind, prm=w["prm"] if kind != 3 else (),
+                 precision=precision, pr_mode=prm, pr_const=w["pr_const"], enskog=enskog, **kw)
+    return m, ph, th, s
+
+
+def _field_errors(m, ph, th, s):
+    f_or = O.fields(m, ph, th)
+    f_gp = s.moments()
+    Y0 = 4 * m.eta0 * O.chi_set(m.eta0)
+    scale = dict(rho=1.0, u=1.0, T=1.0, P=1.0 + Y0, q=1.0)
+    return {k: float(np.abs(f_gp[k] - f_or[k]).max() / scale[k]) for k in scale}
+
+
+def _psi_error(ph, th, s):
+    gp, gt = s.state()
+    e = 0.0
+    for a, b in ((gp, ph), (gt, th)):
+        rowmax = np.abs(b).max(axis=0)
+        e = max(e, float((np.abs(a - b).max(axis=0) / rowmax).max()))
+    return e
+
+
+def _check(m, ph, th, s, precision):
+    errs = _field_errors(m, ph, th, s)
+    assert max(errs.values()) <= TOL[precision], errs
+    e = _psi_error(ph, th, s)
+    assert e <= TOL_PSI[precision], e
+    return errs, e
+
+
+def _smooth_workload(Q, nx, bc="periodic"):
+    return dict(Q=Q, nx=nx, length=1.0, denseness=1.1, kn=0.02, bc=bc, init="fields", prm=(),
+                pr_mode="dense", pr_const=2.0 / 3.0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("Q", [8, 16, 24, 32])
+def test_rhs_matches_oracle(gpu, Q, precision):
+    """L[psi] of Eq. (cast) on an off-equilibrium periodic state spanning 3 tiles + a ragged tail."""
+    nx = 3 * 248 + 17
+    w = _smooth_workload(Q, nx)
+    f = inputs.smooth_periodic_fields(nx, seed=Q)
+    m, ph, th, s = _setup(gpu, w, precision, fields=f)
+    noise = inputs.state_noise(ph.shape, seed=Q + 1, scale=1e-2)
+    ph = ph * noise
+    s.set_state(ph, th)
+    if precision == 1:  # the FP32 solver holds the rounded state
+        ph, th = (a.astype(np.float32).astype(np.float64) for a in s.state())
+    Lp_o, Lt_o = O.rhs(m, ph, th)
+    Lp_g, Lt_g = s.rhs()
+    tol = 1e-11 if precision == 0 else 2e-4
+    for a, b in ((Lp_g, Lp_o), (Lt_g, Lt_o)):
+        scale = np.abs(b).max(axis=0) + 1e-300
+        assert float((np.abs(a - b).max(axis=0) / scale).max()) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("Q", [8, 16, 24, 32])
+@pytest.mark.parametrize("bc", ["periodic", "fixed"])
+def test_steps_match_oracle(gpu, Q, precision, bc):
+    nx = 3 * 248 + 17
+    w = _smooth_workload(Q, nx, bc)
+    f = inputs.smooth_periodic_fields(nx, seed=7 * Q)
+    ghost = None
+    if bc == "fixed":
+        ghost = [(f[0][0], f[1][0], f[2][0])] * 3 + [(f[0][-1], f[1][-1], f[2][-1])] * 3
+    m, ph, th, s = _setup(gpu, w, precision, fields=f, ghost=ghost)
+    ph, th = O.run(m, ph, th, 6)
+    s.step(6)
+    _check(m, ph, th, s, precision)
+
+
+@functools.lru_cache(maxsize=None)
+def _sound_wave_oracle():
+    w = inputs.sound_wave()
+    m, ph, th, _ = _setup_oracle_only(w)
+    return w, m, O.run(m, ph, th, w["steps"])
+
+
+def _setup_oracle_only(w):
+    Q, nx, L = w["Q"], w["nx"], w["length"]
+    p, _ = O.quadrature(Q)
+    dt = inputs.cfl_dt(L / nx, abs(p).max())
+    m = O.make_model(Q, nx, L, dt, w["denseness"], w["kn"], pr_mode=0, pr_const=w["pr_const"])
+    r, u, T = O.init_fields(m, O.INIT_SOUND, w["prm"])
+    ph, th = O.equilibrium_state(m, r, u, T)
+    return m, ph, th, dt
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sound_wave_2000_steps(gpu, precision):
+    """Periodic sound wave, Nx = 256, Q = 16, E_l = 0.1, Kn = 0.1, Pr = 2/3, A = 1e-3, 2000 steps."""
+    w, m, (ph, th) = _sound_wave_oracle()
+    s = gpu.Solver(w["Q"], w["nx"], w["length"], m.dt, w["denseness"], w["kn"], bc=gpu.QL_BC_PERIODIC,
+                   init_kind=gpu.QL_INIT_SOUND, prm=w["prm"], precision=precision, pr_mode=gpu.QL_PR_CONST,
+                   pr_const=w["pr_const"])
+    s.step(w["steps"])
+    errs, e = _check(m, ph, th, s, precision)
+    # the perturbation itself is resolved: errors are small relative to its amplitude 1e-3
+    assert errs["rho"] / 1e-3 <= (1e-7 if precision == 0 else 1e-2)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("mach,El", [(2.0, 0.1), (1.4, 0.05), (1.4, 0.2)])
+def test_normal_shock_steps(gpu, precision, mach, El):
+    """Standing shock, Nx = 4096, Q = 32, fixed Rankine-Hugoniot ghosts: a few steps against the oracle."""
+    w = inputs.normal_shock(mach, El)
+    m, ph, th, s = _setup(gpu, w, precision)
+    n = 3 if (mach, El) == (2.0, 0.1) else 1
+    ph, th = O.run(m, ph, th, n)
+    s.step(n)
+    _check(m, ph, th, s, precision)
+
+
+@pytest.mark.parametrize("nx", [8, 31, 248, 249, 496])
+@pytest.mark.parametrize("bc", ["periodic", "fixed"])
+def test_edge_sizes(gpu, nx, bc):
+    """Minimum size, sizes below/at/above one tile, fixed and periodic ends."""
+    w = _smooth_workload(16, nx, bc)
+    f = inputs.smooth_periodic_fields(nx, seed=nx)
+    ghost = [(1.0, 0.0, 1.0)] * 3 + [(1.0, 0.0, 1.0)] * 3 if bc == "fixed" else None
+    m, ph, th, s = _setup(gpu, w, 0, fields=f, ghost=ghost)
+    ph, th = O.run(m, ph, th, 4)
+    s.step(4)
+    _check(m, ph, th, s, 0)
+
+
+def test_uniform_state_is_stationary(gpu):
+    nx = 300
+    f = [np.full(nx, 1.3), np.full(nx, 0.4), np.full(nx, 0.8)]
+    w = _smooth_workload(24, nx, "fixed")
+    m, ph, th, s = _setup(gpu, w, 0, fields=f, ghost=[(1.3, 0.4, 0.8)] * 6)
+    s.step(10)
+    gp, gt = s.state()
+    np.testing.assert_allclose(gp, ph, rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(gt, th, rtol=1e-12, atol=1e-16)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mass_conservation_periodic(gpu, precision):
+    nx = 777
+    w = _smooth_workload(16, nx)
+    f = inputs.smooth_periodic_fields(nx, seed=3)
+    m, ph, th, s = _setup(gpu, w, precision, fields=f)
+    t0 = s.totals()
+    s.step(100)
+    t1 = s.totals()
+    assert abs(t1[0] - t0[0]) <= (1e-13 if precision == 0 else 2e-6)
+    to = O.totals(m, ph, th)
+    assert abs(t0[0] - to[0]) <= (1e-14 if precision == 0 else 1e-6)
+
+
+def test_nonphysical_state_is_reported(gpu):
+    """A cell with negative density sets the device error word; the next sync reports it."""
+    nx = 64
+    w = _smooth_workload(16, nx)
+    m, ph, th, s = _setup(gpu, w, 0, fields=inputs.smooth_periodic_fields(nx, 1))
+    ph = ph.copy()
+    ph[10] *= -1.0
+    s.set_state(ph, th)
+    s.step(1)
+    with pytest.raises(gpu.QLError) as e:
+        s.sync()
+    assert e.value.status == gpu.QL_ENONPHYSICAL
+
+
+def test_state_roundtrip(gpu):
+    nx = 260
+    w = _smooth_workload(32, nx)
+    m, ph, th, s = _setup(gpu, w, 0, fields=inputs.smooth_periodic_fields(nx, 9))
+    a = ph * inputs.state_noise(ph.shape, 4)
+    s.set_state(a, th)
+    b, c = s.state()
+    np.testing.assert_array_equal(b, a)
+    np.testing.assert_array_equal(c, th)

@@ -1,0 +1,96 @@
+"""CPU tests of the library's host side: it loads without a GPU, exports every
+entry point the header declares, and its host physics (velocity set, E_l -> eta,
+sound speed, Rankine-Hugoniot states) agrees with the oracle and closed forms."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "qlbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ql_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(qlbm_lib):
+    names = _declared()
+    assert len(names) >= 17
+    so = ctypes.CDLL(qlbm_lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    assert set(qlbm_lib.EXPORTED) == set(names)
+
+
+@pytest.mark.parametrize("Q", [8, 16, 24, 32, 48, 64])
+def test_velocity_set_matches_oracle(qlbm_lib, Q):
+    p, w = qlbm_lib.ql_velocity_set(Q)
+    po, wo = O.quadrature(Q)
+    np.testing.assert_allclose(p, po, atol=2e-14 * max(1, abs(po).max()), rtol=0)
+    np.testing.assert_allclose(w, wo, rtol=1e-11)
+    np.testing.assert_array_equal(p, -p[::-1])
+
+
+def test_velocity_set_large_q_and_bad_q(qlbm_lib):
+    p, w = qlbm_lib.ql_velocity_set(200)
+    x, wl = np.polynomial.hermite_e.hermegauss(200)
+    np.testing.assert_allclose(p, x, atol=1e-9)
+    assert w.sum() == pytest.approx(1.0, abs=1e-12)
+    with pytest.raises(qlbm_lib.QLError):
+        qlbm_lib.ql_velocity_set(0)
+
+
+def test_eta_of_denseness_and_sound_speed(qlbm_lib):
+    for El in (0.02, 0.1, 0.3, 1.10576, 4.3998):
+        eta = qlbm_lib.ql_eta_of_denseness(El)
+        assert eta == pytest.approx(O.eta_from_denseness(El), rel=1e-12)
+        for rho, T in ((1.0, 1.0), (1.7, 2.3)):
+            assert qlbm_lib.ql_sound_speed2(eta, 1.0, rho, T) == pytest.approx(
+                O.sound_speed2(eta, 1.0, rho, T), rel=1e-12)
+    with pytest.raises(qlbm_lib.QLError):
+        qlbm_lib.ql_eta_of_denseness(1e6)
+
+
+def test_rankine_hugoniot_matches_oracle(qlbm_lib):
+    for El in (0.02, 0.05, 0.1, 0.2, 0.3):
+        eta = O.eta_from_denseness(El)
+        for M in (1.2, 1.4, 2.0, 3.0):
+            a = qlbm_lib.ql_rankine_hugoniot(eta, 1.0, 1.0, 1.0, M)
+            b = O.rankine_hugoniot(eta, 1.0, 1.0, 1.0, M)
+            np.testing.assert_allclose(a, b, rtol=1e-10)
+    with pytest.raises(qlbm_lib.QLError):
+        qlbm_lib.ql_rankine_hugoniot(0.01, 1.0, 1.0, 1.0, 0.9)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
+    q = qlbm_lib
+    kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-3), use_torch=False)
+    with pytest.raises(q.QLError) as e:
+        q.Solver(12, 64, 1.0, 1e-3, 0.1, 0.1, **kw)
+    assert e.value.status == q.QL_EUNSUPPORTED
+    for bad in (dict(nx=4), dict(dt=-1.0), dict(denseness=0.0), dict(kn=-1.0)):
+        args = dict(Q=16, nx=64, length=1.0, dt=1e-3, denseness=0.1, kn=0.1)
+        args.update(bad)
+        with pytest.raises(q.QLError) as e:
+            q.Solver(**args, **kw)
+        assert e.value.status == q.QL_EINVAL
+    # a sound wave needs a periodic domain
+    with pytest.raises(q.QLError) as e:
+        q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_SOUND,
+                 prm=(1.0, 1.0, 1e-3), use_torch=False)
+    assert e.value.status in (q.QL_EINVAL, q.QL_ECUDA)
+
+
+def test_python_binding_has_no_cpu_path():
+    """The binding only marshals arguments into the CUDA library: it imports no oracle and
+    has no numerical fallback."""
+    src = open(os.path.join(ROOT, "paper_2211_16933_gb300", "qlbm.py")).read()
+    assert "oracle" not in src
+    assert "import torch" in src  # allocator and stream only
