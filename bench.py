@@ -282,6 +282,89 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
 
 
+def _batch_instances(q, inputs, n, seed, nx_div=1):
+    keep, insts, spec = [], [], inputs.batch_instances(n=n, seed=seed)
+    for d in spec:
+        nx = d["nx"] // nx_div
+        p, _ = q.ql_velocity_set(d["Q"])
+        dt = inputs.cfl_dt(d["length"] / nx, abs(p).max())
+        sound = d["kind"] == "sound"
+        insts.append(q.make_instance(d["Q"], nx, d["length"], dt, d["denseness"], d["kn"],
+                                     bc=q.QL_BC_PERIODIC if sound else q.QL_BC_FIXED,
+                                     init_kind=q.QL_INIT_SOUND if sound else q.QL_INIT_SHOCK, prm=d["prm"],
+                                     keep=keep))
+    return insts, keep, spec
+
+
+def run_batch(args):
+    """Batched form: 4096 uneven instances (seed 20221130), FP32 state with FP64 conserved sums,
+    one CUDA-graph launch of K steps; plus time to solution against plain FP64 solves."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import inputs
+    from paper_2211_16933_gb300 import qlbm as q
+    torch.cuda.set_device(0)
+    B.build()
+    insts, keep, spec = _batch_instances(q, inputs, args.batch_n, 20221130)
+    t0 = time.perf_counter()
+    b = q.Batch(insts, precision=q.QL_FP32)
+    setup_s = time.perf_counter() - t0
+    warps, ctas = b.tune(3)
+    info = b.info()
+    upd_per_step = info[1]
+    stream = b._stream
+    b.run(args.warmup)
+    b.sync()
+    clk = ClockSampler(0)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = clk.stop()
+    flags = b.sync()
+    ms = e0.elapsed_time(e1)
+    value = upd_per_step * args.steps / (ms * 1e-3)
+    b.close()
+
+    # time to solution on a subset: batched FP32 vs plain FP64 solves one after another
+    sub_n, sub_steps = args.tts_instances, args.tts_steps
+    sub, keep2, sspec = _batch_instances(q, inputs, sub_n, 20221130)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bs = q.Batch(sub, precision=q.QL_FP32)
+    bs.run(sub_steps)
+    bs.sync()
+    t_batch = time.perf_counter() - t0
+    fields32 = [bs.moments(i) for i in range(sub_n)]
+    bs.close()
+    t_plain, err = 0.0, {k: 0.0 for k in ("rho", "u", "T", "P", "q")}
+    for i, I in enumerate(sub):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = q.Solver(I.vs.Q, I.grid.nx, I.grid.length, I.grid.dt, I.denseness, I.kn, bc=I.bc.kind,
+                     init_kind=I.init.kind, prm=list(I.init.prm)[:4], precision=q.QL_FP64, pr_mode=q.QL_PR_DENSE)
+        s.step(sub_steps)
+        f64 = s.moments()
+        t_plain += time.perf_counter() - t0
+        s.close()
+        for k in err:
+            err[k] = max(err[k], float(np.abs(f64[k] - fields32[i][k]).max()))
+    line = {"metric": "cell-velocity updates/s", "value": value, "unit": "updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch_{args.batch_n}_uneven_sound_and_shock", "instances": args.batch_n,
+                       "updates_per_step": upd_per_step, "tuned_warps_per_cta": warps, "tuned_ctas_per_sm": ctas,
+                       "graph": "one CUDA graph launch of 3 x steps persistent stage kernels",
+                       "sums": "f64 per-cell conserved moments", "setup_s": setup_s},
+            "gpu_launches": 3 * args.steps, "clocks": clocks, "nonphysical_instances": int((flags & 1).sum()),
+            "time_to_solution": {"instances": sub_n, "steps": sub_steps, "batched_fp32_s": t_batch,
+                                 "plain_fp64_sequential_s": t_plain, "speedup": t_plain / t_batch,
+                                 "max_field_error_fp32_vs_fp64": err}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,9 +377,16 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["sod", "batch"], default="sod")
+    ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--tts-instances", type=int, default=64)
+    ap.add_argument("--tts-steps", type=int, default=100)
     args = ap.parse_args()
     from paper_2211_16933_gb300 import inputs
     w = inputs.sod_tube(nx=args.nx, Q=args.q)
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args, w)
     else:

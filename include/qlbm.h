@@ -178,16 +178,75 @@ ql_status ql_load_fields(ql_ctx *ctx, const double *rho, const double *u, const 
 ql_status ql_rhs(ql_ctx *ctx, double *Lphi, double *Ltheta);
 
 /* Device view of the current state for callers that keep data on the GPU:
- * *phi points at row k = 0 of phi, rows of *row_stride elements, cell i of
- * row k at (*phi)[k * row_stride + i]; theta rows follow at row Q.  The
- * element type is double for QL_FP64 and float for QL_FP32.  Valid until the
- * next ql_step returns and the stream has run it. */
-ql_status ql_state_device(ql_ctx *ctx, void **phi, int64_t *row_stride);
+ * the state is Q rows, one per velocity k (ascending p_k), of pairs
+ * (phi_k, theta_k); *psi points at cell 0 of row 0 and cell i of row k is
+ * pair (*psi)[k * row_stride + i].  A pair is two doubles for QL_FP64 and two
+ * floats for QL_FP32.  Valid until the next ql_step returns and the stream has
+ * run it. */
+ql_status ql_state_device(ql_ctx *ctx, void **psi, int64_t *row_stride);
 
 /* Numbers fixed at creation: out[0] = eta0, out[1] = chi(eta0),
  * out[2] = sigma, out[3] = dx, out[4] = dt, out[5] = max |p_k|,
  * out[6..6+Q) = p_k, out[6+Q..6+2Q) = w_k.  out holds 6 + 2Q doubles. */
 ql_status ql_info(const ql_ctx *ctx, double *out);
+
+/* ---- Batched form -------------------------------------------------------- */
+
+/* Many independent domains (for example sound waves and shocks of different
+ * size, velocity set, denseness and Mach number) advanced together: each
+ * Runge-Kutta stage is one persistent kernel launch over a list of (instance,
+ * tile) work items, and ql_batch_run captures a whole run in one CUDA graph. */
+typedef struct ql_batch ql_batch; /* opaque, library-owned */
+
+/* One instance: the arguments of ql_create, with its own gas options. */
+typedef struct {
+    ql_velset vs;
+    ql_grid grid;
+    double denseness;
+    double kn;
+    ql_bc bc;
+    ql_init init;
+    int32_t pr_mode;
+    int32_t enskog;
+    double pr_const;
+    double rho_ref;
+} ql_instance;
+
+/* Creates a batch of n >= 1 instances (host array inst; the initial-field
+ * arrays it points to are read before return).  From opts only precision,
+ * device, stream and the allocator hooks are used; with stream NULL the batch
+ * creates its own stream (a CUDA graph cannot be captured on the legacy
+ * default stream).  Errors as for ql_create, naming the first bad instance. */
+ql_status ql_batch_create(const ql_instance *inst, int64_t n, const ql_opts *opts, ql_batch **out);
+
+/* Picks the CTA shape (warps per CTA, 8 or 4) and the number of persistent
+ * CTAs per SM by timing trial_launches >= 1 launches of the first stage for
+ * each candidate (the first stage leaves the state unchanged).  Outputs may be
+ * NULL.  Synchronises. */
+ql_status ql_batch_tune(ql_batch *b, int32_t trial_launches, int32_t *warps, int32_t *ctas_per_sm);
+
+/* Queues nsteps steps of Eq. (rk3) for every instance as one CUDA graph
+ * launch (3 nsteps persistent stage kernels; the graph is rebuilt only when
+ * nsteps or the tuned shape changes).  Asynchronous. */
+ql_status ql_batch_run(ql_batch *b, int64_t nsteps);
+
+/* Waits for the batch's stream; flags (host, n words, or NULL) receives each
+ * instance's error word.  QL_ENONPHYSICAL if any instance went non-physical. */
+ql_status ql_batch_sync(ql_batch *b, uint32_t *flags);
+
+/* ql_moments for instance i (0 <= i < n); arrays of that instance's nx. */
+ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, double *T, double *P, double *q,
+                           double *Pxx, double *totals);
+
+/* ql_get_state for instance i. */
+ql_status ql_batch_get_state(ql_batch *b, int64_t i, double *phi, double *theta);
+
+/* out (host, 6 doubles) = {n, sum of nx Q (updates per step), warps per CTA,
+ * persistent CTAs, bytes per state arena, SM count}. */
+ql_status ql_batch_info(const ql_batch *b, double *out);
+
+ql_status ql_batch_destroy(ql_batch *b);
+const char *ql_batch_last_error(const ql_batch *b);
 
 /* ---- Host-only helpers (no GPU needed), FP64 ---------------------------- */
 

@@ -20,7 +20,7 @@ cudaError_t QL_FN(upload_tables_)(const double *all)
 template <int Q, int STAGE>
 static cudaError_t stage_q(const StageArgs &a, cudaStream_t s)
 {
-    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q>();
+    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, kWarps>();
     auto kern = fdlb_stage_kernel<QL_REAL, Q, STAGE>;
     static bool configured[64] = {};
     int dev = 0;
@@ -58,12 +58,57 @@ cudaError_t QL_FN(launch_stage_)(int Q, int stage, const StageArgs &a, cudaStrea
     return cudaErrorInvalidValue;
 }
 
+// ---- batched stages
+template <int STAGE, int WARPS>
+static cudaError_t batch_sw(int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
+{
+    constexpr size_t smem = stage_smem_bytes<QL_REAL, kMaxQ, WARPS>();
+    auto kern = fdlb_batch_stage_kernel<QL_REAL, STAGE, WARPS>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!configured[dev & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        configured[dev & 63] = true;
+    }
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, kern, 32 * WARPS, smem);
+    kern<<<dim3(unsigned(grid)), dim3(32 * WARPS), smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <int WARPS>
+static cudaError_t batch_w(int stage, int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
+{
+    switch (stage) {
+    case 1: return batch_sw<1, WARPS>(grid, b, s, query, ctas);
+    case 2: return batch_sw<2, WARPS>(grid, b, s, query, ctas);
+    case 3: return batch_sw<3, WARPS>(grid, b, s, query, ctas);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t QL_FN(launch_batch_stage_)(int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s)
+{
+    if (warps == 8) return batch_w<8>(stage, grid, b, s, false, nullptr);
+    if (warps == 4) return batch_w<4>(stage, grid, b, s, false, nullptr);
+    return cudaErrorInvalidValue;
+}
+
+int QL_FN(batch_ctas_per_sm_)(int stage, int warps)
+{
+    int n = 0;
+    cudaError_t e = warps == 8 ? batch_w<8>(stage, 0, BatchArgs{}, nullptr, true, &n)
+                               : batch_w<4>(stage, 0, BatchArgs{}, nullptr, true, &n);
+    return e == cudaSuccess ? n : 0;
+}
+
 cudaError_t QL_FN(launch_init_)(int Q, const double *rho, const double *u, const double *T, void *psi,
                                 int64_t nx, int64_t stride, const double *tab64, cudaStream_t s)
 {
     const int64_t n = (nx + 2 * kHalo) * Q;
     const unsigned blocks = unsigned((n + 255) / 256);
-    QL_REAL *p = static_cast<QL_REAL *>(psi);
+    P2<QL_REAL> *p = static_cast<P2<QL_REAL> *>(psi);
     switch (Q) {
     case 8: fdlb_init_kernel<QL_REAL, 8><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
     case 16: fdlb_init_kernel<QL_REAL, 16><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
@@ -76,8 +121,8 @@ cudaError_t QL_FN(launch_init_)(int Q, const double *rho, const double *u, const
 
 cudaError_t QL_FN(launch_periodic_ghosts_)(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s)
 {
-    QL_REAL *p = static_cast<QL_REAL *>(psi);
-    fdlb_periodic_ghost_kernel<QL_REAL><<<2 * Q, 32, 0, s>>>(p, nx, stride);
+    P2<QL_REAL> *p = static_cast<P2<QL_REAL> *>(psi);
+    fdlb_periodic_ghost_kernel<QL_REAL><<<Q, 32, 0, s>>>(p, nx, stride);
     return cudaGetLastError();
 }
 

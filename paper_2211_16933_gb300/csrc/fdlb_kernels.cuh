@@ -10,6 +10,12 @@
 //   -> discrete equilibrium n g_k (Eq. feq) -> Shakhov targets (Sec. II.C)
 //   -> J1 (Eq. j1_expanded) -> WENO-5 fluxes (App. A.2)
 //   -> L[psi] (Eq. cast) -> Runge-Kutta combination.
+//
+// The state stores (phi_k, theta_k) of a cell as one pair, and the two
+// components go through the same arithmetic, so every such step is written
+// once on pairs: packed two-lane FP32 instructions in FP32, two scalar
+// instructions in FP64.  Velocities are processed with their mirror images
+// (the Gauss-Hermite set is symmetric, p_{Q-1-k} = -p_k).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,7 +25,39 @@
 namespace qlbm {
 
 // ---------------------------------------------------------------------------
-// Arithmetic helpers
+// Pairs of the working precision
+template <typename Real>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    using T = float2;
+};
+template <>
+struct PairOf<double> {
+    using T = double2;
+};
+template <typename Real>
+using P2 = typename PairOf<Real>::T;
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 sp2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double2 sp2(double a) { return make_double2(a, a); }
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as an exact fused multiply-add
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
 template <typename Real>
 __device__ __forceinline__ Real rsqrt_(Real x);
 template <>
@@ -35,75 +73,74 @@ template <>
 __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 
 template <typename Real>
-__device__ __forceinline__ Real fdiv_(Real a, Real b);
+__device__ __forceinline__ Real rcp_(Real x);
 template <>
-__device__ __forceinline__ float fdiv_<float>(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float rcp_<float>(float x) { return __fdividef(1.0f, x); }
 template <>
-__device__ __forceinline__ double fdiv_<double>(double a, double b) { return a / b; }
+__device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
 
-// 2^-e for x in [2^e, 2^(e+1)): an exact power-of-two rescaling.  x >= 0.
-template <typename Real>
-__device__ __forceinline__ Real pow2_recip_(Real x);
-template <>
-__device__ __forceinline__ float pow2_recip_<float>(float x)
+// 2^-e for x in [2^e, 2^(e+1)): an exact power-of-two rescaling factor, x >= 0.
+__device__ __forceinline__ float pow2_recip_(float x)
 {
-    unsigned e = __float_as_uint(x) & 0x7F800000u;
+    const unsigned e = __float_as_uint(x) & 0x7F800000u;
     return __uint_as_float(0x7F000000u - e);
 }
-template <>
-__device__ __forceinline__ double pow2_recip_<double>(double x)
+__device__ __forceinline__ double pow2_recip_(double x)
 {
-    int e = __double2hiint(x) & 0x7FF00000;
+    const int e = __double2hiint(x) & 0x7FF00000;
     return __hiloint2double(0x7FE00000 - e, 0);
 }
 
 // ---------------------------------------------------------------------------
 // WENO-5 value at the interface i+1/2 for a positive advection velocity
-// (App. A.2), from f_{i-2..i+2}.  Weights are delta_q / beta_q^2 normalised,
-// with no epsilon, evaluated in the product form
+// (App. A.2), from f_{i-2..i+2}, for both components of the pairs.  Weights
+// are delta_q / beta_q^2 normalised, with no epsilon, evaluated in the product
+// form
 //   w_q = delta_q prod_{r != q} beta_r^2 / sum_s delta_s prod_{r != s} beta_r^2,
-// which equals the quotient form wherever all beta_q > 0.  The indicators are
+// equal to the quotient form wherever all beta_q > 0.  The indicators are
 // first rescaled by one exact power of two (the weights depend only on their
-// ratios).  When that denominator vanishes, one or more indicators are zero
-// and the weights are the ideal weights restricted to the vanishing
-// indicators and renormalised, which is every multi-zero row of Table weno_x;
-// single-zero rows come out of the product form directly.  The candidates are
-// written as differences so that constant data give exactly f0.
+// ratios).  Single-zero rows of Table weno_x come out of the product form;
+// multi-zero rows give f0 (see below).  Candidates are differences from f0,
+// so constant data give exactly f0.
 template <typename Real>
-__device__ __forceinline__ Real weno5_face(Real fm2, Real fm1, Real f0, Real fp1, Real fp2)
+__device__ __forceinline__ P2<Real> weno5_face2(P2<Real> fm2, P2<Real> fm1, P2<Real> f0, P2<Real> fp1, P2<Real> fp2)
 {
-    const Real Dm2 = fm1 - fm2, Dm1 = f0 - fm1, D0 = fp1 - f0, D1 = fp2 - fp1;
+    using V = P2<Real>;
+    const V Dm2n = sub2(fm2, fm1);  // -(f_{i-1} - f_{i-2})
+    const V Dm1 = sub2(f0, fm1);
+    const V D0 = sub2(fp1, f0);
+    const V D1 = sub2(fp2, fp1);
     // second differences and one-sided first differences of Eq. (weno5_sigma)
-    const Real d1 = Dm1 - Dm2, d2 = D0 - Dm1, d3 = D1 - D0;
-    const Real e1 = fma(Real(3), Dm1, -Dm2);
-    const Real e2 = Dm1 + D0;
-    const Real e3 = fma(Real(-3), D0, D1);
+    const V d1 = add2(Dm1, Dm2n);
+    const V d2 = sub2(D0, Dm1);
+    const V d3 = sub2(D1, D0);
+    const V e1 = fma2(sp2(Real(3)), Dm1, Dm2n);
+    const V e2 = add2(Dm1, D0);
+    const V e3 = fma2(sp2(Real(-3)), D0, D1);
     // 4 beta_q (a common factor cancels in the weights)
-    const Real k = Real(13.0 / 3.0);
-    Real b1 = fma(k * d1, d1, e1 * e1);
-    Real b2 = fma(k * d2, d2, e2 * e2);
-    Real b3 = fma(k * d3, d3, e3 * e3);
-    // delta_q (F^q - f0), candidate values of Eq. (weno5_flux_x) relative to f0
-    const Real c1 = fma(Real(-1.0 / 30.0), Dm2, Real(1.0 / 12.0) * Dm1);
-    const Real c2 = fma(Real(0.1), Dm1, Real(0.2) * D0);
-    const Real c3 = fma(Real(0.2), D0, Real(-0.05) * D1);
-    const Real sc = pow2_recip_(fmax(b1, fmax(b2, b3)));
-    b1 *= sc;
-    b2 *= sc;
-    b3 *= sc;
-    const Real s1 = b1 * b1, s2 = b2 * b2, s3 = b3 * b3;
-    const Real P1 = s2 * s3, P2 = s1 * s3, P3 = s1 * s2;
-    const Real D = fma(Real(0.1), P1, fma(Real(0.6), P2, Real(0.3) * P3));
-    if (D > Real(0)) {
-        const Real num = fma(P1, c1, fma(P2, c2, P3 * c3));
-        return f0 + fdiv_(num, D);
-    }
-    const Real bmin = fmin(b1, fmin(b2, b3));
-    const Real z1 = b1 <= bmin ? Real(1) : Real(0);
-    const Real z2 = b2 <= bmin ? Real(1) : Real(0);
-    const Real z3 = b3 <= bmin ? Real(1) : Real(0);
-    const Real den = fma(Real(0.1), z1, fma(Real(0.6), z2, Real(0.3) * z3));
-    return f0 + fdiv_(fma(z1, c1, fma(z2, c2, z3 * c3)), den);
+    const V k = sp2(Real(13.0 / 3.0));
+    V b1 = fma2(mul2(k, d1), d1, mul2(e1, e1));
+    V b2 = fma2(mul2(k, d2), d2, mul2(e2, e2));
+    V b3 = fma2(mul2(k, d3), d3, mul2(e3, e3));
+    // delta_q (F^q - f0), candidates of Eq. (weno5_flux_x) relative to f0
+    const V D0x = mul2(sp2(Real(0.2)), D0);
+    const V c1 = fma2(sp2(Real(1.0 / 30.0)), Dm2n, mul2(sp2(Real(1.0 / 12.0)), Dm1));
+    const V c2 = fma2(sp2(Real(0.1)), Dm1, D0x);
+    const V c3 = fma2(sp2(Real(-0.05)), D1, D0x);
+    const V sc = mk2(pow2_recip_(fmax(b1.x, fmax(b2.x, b3.x))), pow2_recip_(fmax(b1.y, fmax(b2.y, b3.y))));
+    b1 = mul2(b1, sc);
+    b2 = mul2(b2, sc);
+    b3 = mul2(b3, sc);
+    const V s1 = mul2(b1, b1), s2 = mul2(b2, b2), s3 = mul2(b3, b3);
+    const V P1 = mul2(s2, s3), P2v = mul2(s1, s3), P3 = mul2(s1, s2);
+    const V D = fma2(sp2(Real(0.1)), P1, fma2(sp2(Real(0.6)), P2v, mul2(sp2(Real(0.3)), P3)));
+    const V num = fma2(P1, c1, fma2(P2v, c2, mul2(P3, c3)));
+    // D = 0 only when two or three indicators vanish.  beta_q = 0 means the three
+    // values of stencil q are equal, so two vanishing indicators make the union of
+    // those stencils constant, the candidates that carry weight in Table weno_x
+    // equal f0 there, and the face value is f0 (num = 0 in that case too).
+    const V rD = mk2(D.x > Real(0) ? rcp_(D.x) : Real(0), D.y > Real(0) ? rcp_(D.y) : Real(0));
+    return fma2(num, rD, f0);
 }
 
 // Sixth-order central difference of App. A.3 (times dx), centred on s.
@@ -114,111 +151,125 @@ __device__ __forceinline__ Real cd6_(const Real *v, int s)
            Real(0.75) * (v[s + 1] - v[s - 1]);
 }
 
-template <typename Real>
-struct SumType {
-    using T = double;  // per-cell conserved-moment sums are always FP64
+// CTA shape: WARPS warps update 31 WARPS cells and stage 4 more on each side.
+template <int WARPS>
+struct TileShape {
+    static constexpr int threads = 32 * WARPS;
+    static constexpr int tile = 31 * WARPS;
+    static constexpr int seg = tile + 2 * kHalo;
 };
 
-// Velocities summed in the working precision before each FP64 accumulation.
-template <typename Real, int Q>
-struct MomentGroup {
-    static constexpr int value = sizeof(Real) == 8 ? Q : 8;
-};
-
-template <typename Real, int Q>
+template <typename Real, int Q, int WARPS>
 constexpr size_t stage_smem_bytes()
 {
-    return sizeof(Real) * (size_t(2 * Q) * kSeg + size_t(Q) * Q + 6 * size_t(kSeg));
+    constexpr int SEG = TileShape<WARPS>::seg;
+    return sizeof(P2<Real>) * size_t(Q) * SEG + sizeof(Real) * (size_t(Q / 2) * Q + 6 * size_t(SEG));
 }
 
+// Resident CTAs per SM the FP32 stage kernels are compiled for (8-warp tiles;
+// the register budget follows from it).
+#ifndef QL_STAGE_MINBLOCKS_F32
+#define QL_STAGE_MINBLOCKS_F32 3
+#endif
+
 // ---------------------------------------------------------------------------
-// One Runge-Kutta stage (STAGE 1..3), or L[psi] itself (STAGE 0).
-template <typename Real, int Q, int STAGE>
-__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 2 : 1)
-    fdlb_stage_kernel(StageArgs a)
+// One Runge-Kutta stage (STAGE 1..3), or L[psi] itself (STAGE 0), on the tile
+// of cells i0 .. i0 + 31 WARPS - 1 of one 1D domain.  All threads of the CTA
+// call it together; it uses dynamic shared memory from `smem`.
+template <typename Real, int Q, int STAGE, int WARPS>
+__device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0, unsigned char *smem_raw)
 {
+    using V = P2<Real>;
     constexpr TabView TV = tab_view(Q);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real *s_psi = reinterpret_cast<Real *>(smem_raw);  // [2Q][kSeg]
-    Real *s_G = s_psi + 2 * Q * kSeg;                   // [Q][Q]
-    Real *s_n = s_G + Q * Q;                            // per staged cell
-    Real *s_u = s_n + kSeg;
-    Real *s_T = s_u + kSeg;
-    Real *s_q = s_T + kSeg;
-    Real *s_lnn = s_q + kSeg;
-    Real *s_lnT = s_lnn + kSeg;
+    constexpr int H = Q / 2;  // velocity k = H + j has p > 0, its mirror H - 1 - j has -p
+    constexpr int THREADS = TileShape<WARPS>::threads;
+    constexpr int SEG = TileShape<WARPS>::seg;
+    static_assert(Q % 2 == 0, "symmetric velocity sets of even size");
+    V *s_psi = reinterpret_cast<V *>(smem_raw);               // [Q][SEG] (phi, theta)
+    Real *s_G = reinterpret_cast<Real *>(s_psi + Q * SEG);   // [H][Q] table rows of p > 0
+    Real *s_n = s_G + H * Q;                                  // per staged cell
+    Real *s_u = s_n + SEG;
+    Real *s_T = s_u + SEG;
+    Real *s_q = s_T + SEG;
+    Real *s_lnn = s_q + SEG;
+    Real *s_lnT = s_lnn + SEG;
 
     const int t = threadIdx.x;
-    const int64_t i0 = int64_t(blockIdx.x) * kTile;  // first cell this CTA updates
     const int64_t stride = a.stride;
-    const Real *__restrict__ in = static_cast<const Real *>(a.in);
+    const V *__restrict__ in = static_cast<const V *>(a.in);
 
-    // 1. Stage cells i0-kHalo .. i0+kTile+kHalo-1 of every row (16-byte vectors).
+    // 1. Stage cells i0-kHalo .. i0+tile+kHalo-1 of every row (16-byte vectors).
     {
-        constexpr int VEC = 16 / sizeof(Real);
-        constexpr int VPR = kSeg / VEC;             // vectors per row
-        constexpr int RPP = kThreads / VPR;         // rows per pass
-        static_assert(kThreads % VPR == 0 && (2 * Q) % RPP == 0, "staging shape");
-        const int rr = t / VPR, vv = t % VPR;
+        constexpr int PPV = 16 / sizeof(V);  // pairs per vector
+        constexpr int VPR = SEG / PPV;       // vectors per row
+        static_assert(SEG % PPV == 0, "staging shape");
 #pragma unroll 4
-        for (int r = rr; r < 2 * Q; r += RPP) {
+        for (int e = t; e < Q * VPR; e += THREADS) {
+            const int r = e / VPR, vv = e - r * VPR;
             const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + r * stride + i0) + vv);
-            reinterpret_cast<uint4 *>(s_psi + r * kSeg)[vv] = v;
+            reinterpret_cast<uint4 *>(s_psi + r * SEG)[vv] = v;
         }
-        for (int e = t; e < Q * Q; e += kThreads) s_G[e] = QL_TAB[TV.G + e];
+        for (int e = t; e < H * Q; e += THREADS) s_G[e] = QL_TAB[TV.G + H * Q + e];
     }
     __syncthreads();
 
-    // 2. Moments of staged cell t (cell i0 - kHalo + t), Sec. II.D, from the raw
-    //    sums S_j = sum p^j phi, R_j = sum p^j theta.
-    {
-        double S0 = 0, S1 = 0, S2 = 0, S3 = 0, R0 = 0, R1 = 0;
-        constexpr int GRP = MomentGroup<Real, Q>::value;
+    // 2. Moments of staged cell c (cell i0 - kHalo + c), Sec. II.D, from raw
+    //    sums over velocity pairs.  Mass, momentum and energy sums go to FP64
+    //    every 8 pairs; the heat-flux sums stay in the working precision.
+    for (int c = t; c < SEG; c += THREADS) {
+        constexpr int GRP = sizeof(Real) == 8 ? H : 8;
+        double M0 = 0, M1 = 0, ME = 0;
+        Real tS2 = 0, tS3 = 0, tR0 = 0, tR1 = 0;
 #pragma unroll
-        for (int g = 0; g < Q; g += GRP) {
-            Real s0 = 0, s1 = 0, s2 = 0, s3 = 0, r0 = 0, r1 = 0;
+        for (int g = 0; g < H; g += GRP) {
+            V s01 = sp2(Real(0)), s11 = sp2(Real(0));  // (S0, R0), (S1, R1) partials
+            Real s2 = 0, s3 = 0;
 #pragma unroll
-            for (int k = g; k < g + GRP; ++k) {
-                const Real ph = s_psi[k * kSeg + t], th = s_psi[(Q + k) * kSeg + t];
-                s0 += ph;
-                s1 = fma(QL_TAB[TV.p + k], ph, s1);
-                s2 = fma(QL_TAB[TV.p2 + k], ph, s2);
-                s3 = fma(QL_TAB[TV.p3 + k], ph, s3);
-                r0 += th;
-                r1 = fma(QL_TAB[TV.p + k], th, r1);
+            for (int j = g; j < g + GRP && j < H; ++j) {
+                const Real p = QL_TAB[TV.p + H + j];
+                const V fa = s_psi[(H + j) * SEG + c], fb = s_psi[(H - 1 - j) * SEG + c];
+                const V sm = add2(fa, fb), df = sub2(fa, fb);
+                s01 = add2(s01, sm);
+                s11 = fma2(sp2(p), df, s11);
+                s2 = fma(QL_TAB[TV.p2 + H + j], sm.x, s2);
+                s3 = fma(QL_TAB[TV.p3 + H + j], df.x, s3);
             }
-            S0 += double(s0);
-            S1 += double(s1);
-            S2 += double(s2);
-            S3 += double(s3);
-            R0 += double(r0);
-            R1 += double(r1);
+            M0 += double(s01.x);
+            M1 += double(s11.x);
+            ME += double(s2 + s01.y);
+            tS2 += s2;
+            tS3 += s3;
+            tR0 += s01.y;
+            tR1 += s11.y;
         }
-        const double n = S0;
-        const double inv_n = 1.0 / n;
-        const double u = S1 * inv_n;
-        // 3 n T = sum xi^2 phi + sum theta,  xi = p - u
-        const double c2 = S2 - u * S1;
-        const double T = (c2 + R0) * inv_n * (1.0 / 3.0);
-        // 2 q = sum xi^3 phi + sum xi theta
-        const double q = 0.5 * (S3 - 3.0 * u * S2 + 2.0 * u * u * S1 + R1 - u * R0);
-        const int64_t i = i0 - kHalo + t;
+        // 1/n to full FP64 precision from a working-precision reciprocal and two Newton steps
+        const double n = M0;
+        double rn = double(rcp_(Real(n)));
+        rn = fma(rn, fma(-n, rn, 1.0), rn);
+        rn = fma(rn, fma(-n, rn, 1.0), rn);
+        const double u = M1 * rn;
+        // 3 n T = sum xi^2 phi + sum theta = (S2 + R0) - u S1
+        const double T = fma(-u, M1, ME) * rn * (1.0 / 3.0);
+        // 2 q = sum xi^3 phi + sum xi theta = S3 + R1 - u (3 S2 + R0) + 2 u^2 S1
+        const Real uf = Real(u);
+        const Real q = Real(0.5) * (tS3 + tR1 - uf * fma(Real(3), tS2, tR0) + Real(2) * uf * uf * Real(M1));
+        const int64_t i = i0 - kHalo + c;
         if (i >= 0 && i < a.nx) {
             if (!(n > 0.0) || !(T > 0.0) || !isfinite(u) || !isfinite(q) || !isfinite(n) || !isfinite(T))
                 atomicOr(a.err, 1u);
         }
-        s_n[t] = Real(n);
-        s_u[t] = Real(u);
-        s_T[t] = Real(T);
-        s_q[t] = Real(q);
-        s_lnn[t] = log_(Real(n));
-        s_lnT[t] = log_(Real(T));
+        s_n[c] = Real(n);
+        s_u[c] = uf;
+        s_T[c] = Real(T);
+        s_q[c] = q;
+        s_lnn[c] = log_(Real(n));
+        s_lnT[c] = log_(Real(T));
     }
     __syncthreads();
 
     // 3. Update.  Lane l of warp w handles staged cell s = 31 w + l + 3: it
-    //    computes the interface value on the right face of s, and (l >= 1)
-    //    updates cell s, whose left face value comes from lane l-1.
+    //    computes the interface values on the right face of s, and (l >= 1)
+    //    updates cell s, whose left-face values come from lane l-1.
     const int lane = t & 31, warp = t >> 5;
     const int s = 31 * warp + lane + 3;
     const int64_t i = i0 - kHalo + s;
@@ -241,7 +292,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 2 : 1)
     const Real inv_tau = rhat * chi * sqT / (Real(a.tau_pref) * muf);
     Real Pr = Real(a.pr_const);
     if (a.pr_mode) {
-        const Real laf = fma(fma(Real(0.36 * (1.0 + 32.0 / (9.0 * 3.14159265358979323846))), Y, Real(1.2)), Y, Real(1));
+        const Real laf =
+            fma(fma(Real(0.36 * (1.0 + 32.0 / (9.0 * 3.14159265358979323846))), Y, Real(1.2)), Y, Real(1));
         Pr = Real(2.0 / 3.0) * muf / laf;
     }
     const Real invT = Real(1) / T;
@@ -251,93 +303,176 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 2 : 1)
     // d ln chi = eta (3/(1-eta) - 1/(2-eta)) d ln rho  (chi_SET depends on eta only)
     const Real dlnchi = eta * (Real(3) / ome - Real(1) / (Real(2) - eta)) * dlnn;
     const Real G = dlnchi + Real(2) * dlnn;
-    // phi target / (n g_k) as a cubic in xi = p_k - u:
-    //   (1/tau)(1 + A xi (xi^2/T - 3)) - Y [xi G + 3/5 (xi^2/T - 1) du + 3/10 (xi^3/T + xi/3) dlnT]
-    // theta target / (2 T n g_k) differs by d0 + d1 xi.
+    // Targets over the equilibrium, cubic in xi = p_k - u:
+    //   phi:   (1/tau)(1 + A xi (xi^2/T - 3)) - Y [xi G + 3/5 (xi^2/T - 1) du + 3/10 (xi^3/T + xi/3) dlnT]
+    //   theta: (1/tau)(1 + A xi (xi^2/T - 1)) - Y [xi G + 3/5 (xi^2/T - 1/3) du + 3/10 (xi^3/T + 7 xi/3) dlnT]
+    // times n g_k and 2 T n g_k; the pairs below hold (phi, theta) coefficients
+    // already multiplied by n and 2 T n.
     const Real a0 = fma(Real(0.6) * Yj, du, inv_tau);
     const Real a1 = -Real(3) * A * inv_tau - Yj * G - Real(0.1) * Yj * dlnT;
     const Real a2 = -Real(0.6) * Yj * du * invT;
     const Real a3 = (A * inv_tau - Real(0.3) * Yj * dlnT) * invT;
-    const Real d0 = -Real(0.4) * Yj * du;
-    const Real d1 = Real(2) * A * inv_tau - Real(0.6) * Yj * dlnT;
+    const Real b0 = fma(Real(0.2) * Yj, du, inv_tau);
+    const Real b1 = -A * inv_tau - Yj * G - Real(0.7) * Yj * dlnT;
     const Real nphi = n, nth = Real(2) * T * n;
+    const V C0 = mk2(a0 * nphi, b0 * nth), C1 = mk2(a1 * nphi, b1 * nth);
+    const V C2 = mk2(a2 * nphi, a2 * nth), C3 = mk2(a3 * nphi, a3 * nth);
 
     // Normalised Hermite coefficients of the equilibrium, Eq. (g_alpha):
-    // c^_0 = 1, c^_1 = u, c^_l = u c^_{l-1}/sqrt(l) + (T-1) c^_{l-2} sqrt((l-1)/l).
-    Real ch[Q];
-    ch[0] = Real(1);
-    ch[1] = u;
-    const Real Tm1 = T - Real(1);
+    // c^_0 = 1, c^_1 = u, c^_l = u c^_{l-1}/sqrt(l) + (T-1) c^_{l-2} sqrt((l-1)/l),
+    // held as pairs (c^_{2m}, c^_{2m+1}).
+    V ch[H];
+    {
+        Real cm2 = Real(1), cm1 = u;
+        ch[0] = mk2(cm2, cm1);
+        const Real Tm1 = T - Real(1);
 #pragma unroll
-    for (int l = 2; l < Q; ++l) ch[l] = fma(QL_TAB[TV.ca + l] * u, ch[l - 1], QL_TAB[TV.cb + l] * Tm1 * ch[l - 2]);
+        for (int m = 1; m < H; ++m) {
+            const Real ce = fma(QL_TAB[TV.ca + 2 * m] * u, cm1, QL_TAB[TV.cb + 2 * m] * Tm1 * cm2);
+            const Real co = fma(QL_TAB[TV.ca + 2 * m + 1] * u, ce, QL_TAB[TV.cb + 2 * m + 1] * Tm1 * cm1);
+            ch[m] = mk2(ce, co);
+            cm2 = ce;
+            cm1 = co;
+        }
+    }
 
-    const Real dt = Real(a.dt);
-    const Real *__restrict__ base = static_cast<const Real *>(a.base);
-    Real *__restrict__ out = static_cast<Real *>(a.out);
+    const V dt2 = sp2(Real(a.dt));
+    const V mtau = sp2(-inv_tau);
+    const V *__restrict__ base = static_cast<const V *>(a.base);
+    V *out = static_cast<V *>(a.out);
     const int64_t col = kHalo + i;
 
 #pragma unroll 1
-    for (int k = 0; k < Q; ++k) {
-        const Real pk = QL_TAB[TV.p + k];
-        const Real *rp = s_psi + k * kSeg;
-        const Real *rt = s_psi + (Q + k) * kSeg;
-        // WENO-5 values at the right face of s (mirrored stencil for p_k < 0)
-        Real hp, ht;
-        if (pk > Real(0)) {
-            hp = weno5_face(rp[s - 2], rp[s - 1], rp[s], rp[s + 1], rp[s + 2]);
-            ht = weno5_face(rt[s - 2], rt[s - 1], rt[s], rt[s + 1], rt[s + 2]);
-        } else {
-            hp = weno5_face(rp[s + 3], rp[s + 2], rp[s + 1], rp[s], rp[s - 1]);
-            ht = weno5_face(rt[s + 3], rt[s + 2], rt[s + 1], rt[s], rt[s - 1]);
+    for (int j = 0; j < H; ++j) {
+        const int kp = H + j, km = H - 1 - j;
+        const int64_t ip = int64_t(kp) * stride + col, im = int64_t(km) * stride + col;
+        // psi^n of this cell, loaded before the arithmetic that hides its latency
+        // (every lane's column lies inside the row: ghost or padding columns at worst)
+        V bp = sp2(Real(0)), bm = sp2(Real(0));
+        if (STAGE >= 2) {
+            bp = base[ip];
+            bm = base[im];
         }
-        const Real hpl = __shfl_up_sync(0xffffffffu, hp, 1);
-        const Real htl = __shfl_up_sync(0xffffffffu, ht, 1);
-        const Real adv_p = pk * inv_dx * (hp - hpl);
-        const Real adv_t = pk * inv_dx * (ht - htl);
+        const Real p = QL_TAB[TV.p + kp];
+        const V *rp = s_psi + kp * SEG;
+        const V *rm = s_psi + km * SEG;
+        // WENO-5 values at the right face of s: upwind stencil for +p, mirrored for -p
+        const V fp0 = rp[s], fm0 = rm[s];
+        const V hp = weno5_face2<Real>(rp[s - 2], rp[s - 1], fp0, rp[s + 1], rp[s + 2]);
+        const V hm = weno5_face2<Real>(rm[s + 3], rm[s + 2], rm[s + 1], fm0, rm[s - 1]);
+        const V hpl = mk2(__shfl_up_sync(0xffffffffu, hp.x, 1), __shfl_up_sync(0xffffffffu, hp.y, 1));
+        const V hml = mk2(__shfl_up_sync(0xffffffffu, hm.x, 1), __shfl_up_sync(0xffffffffu, hm.y, 1));
+        const V advp = mul2(sp2(p * inv_dx), sub2(hp, hpl));
+        const V advm = mul2(sp2(-p * inv_dx), sub2(hm, hml));
 
-        // g_k = sum_l G[k][l] c^_l
-        Real g = Real(0);
-        const Real *Gk = s_G + k * Q;
+        // g at +p and -p: even and odd Hermite parts, h_l(-p) = (-1)^l h_l(p)
+        V eo = sp2(Real(0));
+        const V *Gj = reinterpret_cast<const V *>(s_G + j * Q);
 #pragma unroll
-        for (int l = 0; l < Q; ++l) g = fma(Gk[l], ch[l], g);
+        for (int m = 0; m < H; ++m) eo = fma2(Gj[m], ch[m], eo);
+        const Real gpv = eo.x + eo.y, gmv = eo.x - eo.y;
 
-        const Real xi = pk - u;
-        const Real Pphi = fma(fma(fma(a3, xi, a2), xi, a1), xi, a0);
-        const Real Pth = Pphi + fma(d1, xi, d0);
-        const Real ph0 = rp[s], th0 = rt[s];
-        const Real Lp = fma(nphi * g, Pphi, -fma(ph0, inv_tau, adv_p));
-        const Real Lt = fma(nth * g, Pth, -fma(th0, inv_tau, adv_t));
+        // targets, L[psi] = target - psi / tau - advection, Eq. (cast)
+        const Real xp = p - u, xm = -p - u;
+        const V Pp = fma2(fma2(fma2(C3, sp2(xp), C2), sp2(xp), C1), sp2(xp), C0);
+        const V Pm = fma2(fma2(fma2(C3, sp2(xm), C2), sp2(xm), C1), sp2(xm), C0);
+        const V Lp = sub2(fma2(fp0, mtau, mul2(sp2(gpv), Pp)), advp);
+        const V Lm = sub2(fma2(fm0, mtau, mul2(sp2(gmv), Pm)), advm);
 
         if (owner) {
-            Real op, ot;
-            const int64_t ip = int64_t(k) * stride + col, it = int64_t(Q + k) * stride + col;
+            V op, om;
             if (STAGE == 0) {
                 op = Lp;
-                ot = Lt;
+                om = Lm;
             } else if (STAGE == 1) {
-                op = fma(dt, Lp, ph0);
-                ot = fma(dt, Lt, th0);
-            } else if (STAGE == 2) {
-                op = fma(Real(0.75), base[ip], Real(0.25) * fma(dt, Lp, ph0));
-                ot = fma(Real(0.75), base[it], Real(0.25) * fma(dt, Lt, th0));
+                op = fma2(dt2, Lp, fp0);
+                om = fma2(dt2, Lm, fm0);
             } else {
-                op = fma(Real(1.0 / 3.0), base[ip], Real(2.0 / 3.0) * fma(dt, Lp, ph0));
-                ot = fma(Real(1.0 / 3.0), base[it], Real(2.0 / 3.0) * fma(dt, Lt, th0));
+                // 3/4 psi^n + 1/4 v and 1/3 psi^n + 2/3 v with v = psi + dt L, written as
+                // v + c (psi^n - v) so that the two weights sum to exactly one in any
+                // precision (1/3 and 2/3 rounded to FP32 sum to 1 + 4e-8, a per-step bias)
+                const V c = sp2(STAGE == 2 ? Real(0.75) : Real(1.0 / 3.0));
+                const V vp = fma2(dt2, Lp, fp0), vm = fma2(dt2, Lm, fm0);
+                op = fma2(c, sub2(bp, vp), vp);
+                om = fma2(c, sub2(bm, vm), vm);
             }
             out[ip] = op;
-            out[it] = ot;
+            out[im] = om;
             if (STAGE != 0 && a.periodic) {
                 // periodic images in the ghost columns of the other end
                 if (i < kHalo) {
                     out[ip + a.nx] = op;
-                    out[it + a.nx] = ot;
+                    out[im + a.nx] = om;
                 }
                 if (i >= a.nx - kHalo) {
                     out[ip - a.nx] = op;
-                    out[it - a.nx] = ot;
+                    out[im - a.nx] = om;
                 }
             }
         }
+    }
+}
+
+template <typename Real>
+struct StageOccupancy {
+    static constexpr int value = sizeof(Real) == 4 ? QL_STAGE_MINBLOCKS_F32 : 1;
+};
+
+// One Runge-Kutta stage over a whole domain: CTA b updates tile b.
+template <typename Real, int Q, int STAGE>
+__global__ void __launch_bounds__(kThreads, StageOccupancy<Real>::value) fdlb_stage_kernel(StageArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<Real, Q, STAGE, kWarps>(a, int64_t(blockIdx.x) * kTile, smem_raw);
+}
+
+// Batched form: one persistent launch per Runge-Kutta stage over a work list
+// of (instance, tile) items of many independent domains with their own size,
+// velocity set and gas parameters.  Each CTA walks the list with stride
+// gridDim.x.
+template <int WARPS>
+struct BatchOccupancy {
+    static constexpr int value = WARPS == 8 ? QL_STAGE_MINBLOCKS_F32 : 2 * QL_STAGE_MINBLOCKS_F32 - 1;
+};
+
+template <typename Real, int STAGE, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy<WARPS>::value : 1)
+    fdlb_batch_stage_kernel(BatchArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int64_t w = blockIdx.x; w < b.nwork; w += gridDim.x) {
+        const int2 it = b.work[w];
+        const BatchInstance &I = b.inst[it.x];
+        StageArgs a;
+        const int64_t off = I.off;
+        const P2<Real> *A = static_cast<const P2<Real> *>(b.arena[0]) + off;
+        const P2<Real> *Bb = static_cast<const P2<Real> *>(b.arena[1]) + off;
+        const P2<Real> *C = static_cast<const P2<Real> *>(b.arena[2]) + off;
+        a.in = STAGE == 1 ? A : (STAGE == 2 ? Bb : C);
+        a.base = A;
+        a.out = const_cast<P2<Real> *>(STAGE == 1 ? Bb : (STAGE == 2 ? C : A));
+        a.nx = I.nx;
+        a.stride = I.stride;
+        a.inv_dx = I.inv_dx;
+        a.dt = I.dt;
+        a.eta0 = I.eta0;
+        a.inv_rho_ref = I.inv_rho_ref;
+        a.tau_pref = I.tau_pref;
+        a.pr_const = I.pr_const;
+        a.pr_mode = I.pr_mode;
+        a.enskog = I.enskog;
+        a.periodic = I.periodic;
+        a.pad_ = 0;
+        a.err = b.err + it.x;
+        const int64_t i0 = int64_t(it.y) * TileShape<WARPS>::tile;
+        switch (I.Q) {
+        case 8: stage_tile<Real, 8, STAGE, WARPS>(a, i0, smem_raw); break;
+        case 16: stage_tile<Real, 16, STAGE, WARPS>(a, i0, smem_raw); break;
+        case 24: stage_tile<Real, 24, STAGE, WARPS>(a, i0, smem_raw); break;
+        case 32: stage_tile<Real, 32, STAGE, WARPS>(a, i0, smem_raw); break;
+        default: break;
+        }
+        __syncthreads();  // shared memory is reused by the next item
     }
 }
 
@@ -346,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 2 : 1)
 // interior and the ghost columns.  One thread per (cell, k).
 template <typename Real, int Q>
 __global__ void fdlb_init_kernel(const double *__restrict__ rho, const double *__restrict__ u,
-                                 const double *__restrict__ T, Real *__restrict__ psi, int64_t nx,
+                                 const double *__restrict__ T, P2<Real> *__restrict__ psi, int64_t nx,
                                  int64_t stride, const double *__restrict__ tab)
 {
     constexpr TabView TV = tab_view(Q);
@@ -364,21 +499,20 @@ __global__ void fdlb_init_kernel(const double *__restrict__ rho, const double *_
         cm2 = cm1;
         cm1 = cl;
     }
-    psi[int64_t(k) * stride + c] = Real(n * g);
-    psi[int64_t(Q + k) * stride + c] = Real(2.0 * TT * n * g);
+    psi[int64_t(k) * stride + c] = mk2(Real(n * g), Real(2.0 * TT * n * g));
 }
 
 template <typename Real>
-__global__ void fdlb_periodic_ghost_kernel(Real *__restrict__ psi, int64_t nx, int64_t stride)
+__global__ void fdlb_periodic_ghost_kernel(P2<Real> *__restrict__ psi, int64_t nx, int64_t stride)
 {
-    const int r = blockIdx.x;  // row
-    const int j = threadIdx.x; // 0 .. 2 kHalo - 1
+    const int r = blockIdx.x;   // row
+    const int j = threadIdx.x;  // 0 .. 2 kHalo - 1
     if (j >= 2 * kHalo) return;
-    Real *row = psi + int64_t(r) * stride;
+    P2<Real> *row = psi + int64_t(r) * stride;
     if (j < kHalo) {
         row[kHalo + nx + j] = row[kHalo + j];  // cell nx + j <- cell j
     } else {
-        const int g = j - kHalo;               // cell -kHalo + g <- cell nx - kHalo + g
+        const int g = j - kHalo;  // cell -kHalo + g <- cell nx - kHalo + g
         row[g] = row[nx + g];
     }
 }
@@ -390,14 +524,14 @@ __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a,
 {
     constexpr TabView TV = tab_view(Q);
     __shared__ double red[3][kMomThreads];
-    const Real *__restrict__ psi = static_cast<const Real *>(a.psi);
+    const P2<Real> *__restrict__ psi = static_cast<const P2<Real> *>(a.psi);
     const int64_t i = int64_t(blockIdx.x) * kMomThreads + threadIdx.x;
     double M = 0, Pm = 0, E = 0;
     if (i < a.nx) {
         double S0 = 0, S1 = 0, S2 = 0, S3 = 0, R0 = 0, R1 = 0;
         for (int k = 0; k < Q; ++k) {
-            const double ph = double(psi[int64_t(k) * a.stride + kHalo + i]);
-            const double th = double(psi[int64_t(Q + k) * a.stride + kHalo + i]);
+            const P2<Real> v = psi[int64_t(k) * a.stride + kHalo + i];
+            const double ph = double(v.x), th = double(v.y);
             const double p = tab[TV.p + k];
             S0 += ph;
             S1 += p * ph;

@@ -174,7 +174,7 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     c->alloc = opts->alloc;
     c->free_fn = opts->free;
     c->alloc_user = opts->alloc_user;
-    c->elem = c->precision == QL_FP32 ? 4 : 8;
+    c->elem = c->precision == QL_FP32 ? 8 : 16;  // one (phi, theta) pair
     c->stride = row_stride(c->nx);
 
     auto bail = [&](ql_status st, const std::string &m) {
@@ -220,7 +220,7 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
             g_tables_ready[c->device & 63] = true;
         }
     }
-    const size_t state_bytes = size_t(2 * c->Q) * size_t(c->stride) * c->elem;
+    const size_t state_bytes = size_t(c->Q) * size_t(c->stride) * c->elem;
     for (int b = 0; b < 3; ++b) {
         c->buf[b] = dev_alloc(c, state_bytes);
         if (!c->buf[b]) return bail(QL_ENOMEM, "state buffer allocation failed");
@@ -328,23 +328,28 @@ ql_status ql_totals(ql_ctx *c, double *totals)
     return check_err_word(c);
 }
 
-// rows [2Q][nx] of buffer b <-> cell-major host arrays of doubles
+// rows [Q][nx] of (phi, theta) pairs of buffer b <-> cell-major host arrays of doubles
 static ql_status download_rows(ql_ctx *c, const void *dev, double *phi, double *theta)
 {
     const int Q = c->Q;
     const int64_t nx = c->nx;
-    std::vector<unsigned char> h(size_t(2 * Q) * nx * c->elem);
+    std::vector<unsigned char> h(size_t(Q) * nx * c->elem);
     QL_CUDA(c, cudaMemcpy2DAsync(h.data(), nx * c->elem, static_cast<const unsigned char *>(dev) + kHalo * c->elem,
-                                 c->stride * c->elem, nx * c->elem, 2 * Q, cudaMemcpyDeviceToHost, c->stream));
+                                 c->stride * c->elem, nx * c->elem, Q, cudaMemcpyDeviceToHost, c->stream));
     QL_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int r = 0; r < 2 * Q; ++r) {
-        double *dst = r < Q ? phi : theta;
-        const int k = r < Q ? r : r - Q;
-        if (!dst) continue;
+    for (int k = 0; k < Q; ++k) {
         for (int64_t i = 0; i < nx; ++i) {
-            const size_t src = size_t(r) * nx + i;
-            dst[i * Q + k] = c->elem == 4 ? double(reinterpret_cast<const float *>(h.data())[src])
-                                          : reinterpret_cast<const double *>(h.data())[src];
+            const size_t src = 2 * (size_t(k) * nx + i);
+            double f, t;
+            if (c->precision == QL_FP32) {
+                f = double(reinterpret_cast<const float *>(h.data())[src]);
+                t = double(reinterpret_cast<const float *>(h.data())[src + 1]);
+            } else {
+                f = reinterpret_cast<const double *>(h.data())[src];
+                t = reinterpret_cast<const double *>(h.data())[src + 1];
+            }
+            if (phi) phi[i * Q + k] = f;
+            if (theta) theta[i * Q + k] = t;
         }
     }
     return QL_OK;
@@ -363,18 +368,21 @@ ql_status ql_set_state(ql_ctx *c, const double *phi, const double *theta)
     if (!c || !phi || !theta) return fail(c, QL_EINVAL, "bad arguments to ql_set_state");
     const int Q = c->Q;
     const int64_t nx = c->nx;
-    std::vector<unsigned char> h(size_t(2 * Q) * nx * c->elem);
-    for (int r = 0; r < 2 * Q; ++r) {
-        const double *srcp = r < Q ? phi : theta;
-        const int k = r < Q ? r : r - Q;
+    std::vector<unsigned char> h(size_t(Q) * nx * c->elem);
+    for (int k = 0; k < Q; ++k) {
         for (int64_t i = 0; i < nx; ++i) {
-            const size_t dst = size_t(r) * nx + i;
-            if (c->elem == 4) reinterpret_cast<float *>(h.data())[dst] = float(srcp[i * Q + k]);
-            else reinterpret_cast<double *>(h.data())[dst] = srcp[i * Q + k];
+            const size_t dst = 2 * (size_t(k) * nx + i);
+            if (c->precision == QL_FP32) {
+                reinterpret_cast<float *>(h.data())[dst] = float(phi[i * Q + k]);
+                reinterpret_cast<float *>(h.data())[dst + 1] = float(theta[i * Q + k]);
+            } else {
+                reinterpret_cast<double *>(h.data())[dst] = phi[i * Q + k];
+                reinterpret_cast<double *>(h.data())[dst + 1] = theta[i * Q + k];
+            }
         }
     }
     QL_CUDA(c, cudaMemcpy2DAsync(static_cast<unsigned char *>(c->buf[0]) + kHalo * c->elem, c->stride * c->elem,
-                                 h.data(), nx * c->elem, nx * c->elem, 2 * Q, cudaMemcpyHostToDevice, c->stream));
+                                 h.data(), nx * c->elem, nx * c->elem, Q, cudaMemcpyHostToDevice, c->stream));
     if (c->periodic) {
         cudaError_t e = c->precision == QL_FP32 ? launch_periodic_ghosts_f32(Q, c->buf[0], nx, c->stride, c->stream)
                                                 : launch_periodic_ghosts_f64(Q, c->buf[0], nx, c->stride, c->stream);

@@ -1,0 +1,425 @@
+// C ABI of the batched form (include/qlbm.h, ql_batch_*): many independent 1D
+// domains advanced together by persistent stage kernels over one work list,
+// whole runs captured in a CUDA graph, and a tuner for the CTA shape.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/qlbm.h"
+#include "qlbm_host.h"
+#include "qlbm_internal.h"
+
+using namespace qlbm;
+
+struct ql_batch {
+    int precision = QL_FP32, device = 0;
+    int64_t n = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    ql_alloc_fn alloc = nullptr;
+    ql_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    size_t elem = 8;
+    std::vector<BatchInstance> inst;
+    std::vector<double> updates;  // nx * Q per instance
+    BatchInstance *d_inst = nullptr;
+    int2 *d_work[2] = {nullptr, nullptr};  // work lists for kBatchWarps[0], kBatchWarps[1]
+    int64_t nwork[2] = {0, 0};
+    void *arena[3] = {nullptr, nullptr, nullptr};
+    size_t arena_bytes = 0;
+    unsigned *d_err = nullptr;
+    double *d_tab64 = nullptr, *d_fields = nullptr, *d_partial = nullptr, *d_totals = nullptr, *d_init = nullptr;
+    int64_t max_nx = 0;
+    int warps = 8, grid = 0, sms = 0;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_steps = -1;
+    int graph_warps = 0, graph_grid = 0;
+    std::string err;
+};
+
+static std::string g_batch_error;
+
+static ql_status bfail(ql_batch *b, ql_status st, const std::string &m)
+{
+    if (b) b->err = m; else g_batch_error = m;
+    return st;
+}
+
+static ql_status bcuda(ql_batch *b, cudaError_t e, const char *what)
+{
+    return bfail(b, e == cudaErrorMemoryAllocation ? QL_ENOMEM : QL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QB_CUDA(b, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return bcuda(b, e_, #call); \
+    } while (0)
+
+static void *balloc(ql_batch *b, size_t bytes)
+{
+    if (b->alloc) return b->alloc(bytes, b->alloc_user);
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+
+static void bfree(ql_batch *b, void *p)
+{
+    if (!p) return;
+    if (b->free_fn) b->free_fn(p, b->alloc_user);
+    else cudaFree(p);
+}
+
+static void batch_release(ql_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int j = 0; j < 3; ++j) bfree(b, b->arena[j]);
+    for (int j = 0; j < 2; ++j) bfree(b, b->d_work[j]);
+    bfree(b, b->d_inst);
+    bfree(b, b->d_err);
+    bfree(b, b->d_tab64);
+    bfree(b, b->d_fields);
+    bfree(b, b->d_partial);
+    bfree(b, b->d_totals);
+    bfree(b, b->d_init);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
+{
+    BatchArgs a;
+    a.inst = b->d_inst;
+    const int wi = warps == kBatchWarps[0] ? 0 : 1;
+    a.work = b->d_work[wi];
+    a.nwork = b->nwork[wi];
+    for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
+    a.err = b->d_err;
+    return b->precision == QL_FP32 ? launch_batch_stage_f32(stage, warps, grid, a, b->stream)
+                                   : launch_batch_stage_f64(stage, warps, grid, a, b->stream);
+}
+
+static int ctas_per_sm(ql_batch *b, int warps)
+{
+    int m = 8;
+    for (int s = 1; s <= 3; ++s) {
+        const int c = b->precision == QL_FP32 ? batch_ctas_per_sm_f32(s, warps) : batch_ctas_per_sm_f64(s, warps);
+        m = std::min(m, c);
+    }
+    return m;
+}
+
+extern "C" {
+
+ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts, ql_batch **out)
+{
+    if (out) *out = nullptr;
+    if (!in || n <= 0 || !opts || !out) return bfail(nullptr, QL_EINVAL, "bad arguments to ql_batch_create");
+    if (opts->precision != QL_FP32 && opts->precision != QL_FP64) return bfail(nullptr, QL_EINVAL, "bad precision");
+    ql_batch *b = new ql_batch();
+    b->precision = opts->precision;
+    b->device = opts->device;
+    b->n = n;
+    b->alloc = opts->alloc;
+    b->free_fn = opts->free;
+    b->alloc_user = opts->alloc_user;
+    b->elem = b->precision == QL_FP32 ? 8 : 16;
+    auto bail = [&](ql_status st, const std::string &m) {
+        batch_release(b);
+        delete b;
+        return bfail(nullptr, st, m);
+    };
+
+    // descriptors and host initial fields
+    std::vector<std::vector<double>> fields(n);
+    int64_t off = 0;
+    b->inst.resize(n);
+    b->updates.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const ql_instance &I = in[i];
+        bool qok = false;
+        for (int j = 0; j < kNumQ; ++j) qok |= I.vs.Q == kQList[j];
+        const std::string id = "instance " + std::to_string(i) + ": ";
+        if (!qok || I.vs.kind != 0) return bail(QL_EUNSUPPORTED, id + "Q must be one of 8, 16, 24, 32");
+        if (I.grid.nx < 8 || I.grid.nx > (int64_t(1) << 31) || !(I.grid.length > 0) || !(I.grid.dt > 0))
+            return bail(QL_EINVAL, id + "bad grid");
+        if (!(I.denseness > 0) || !(I.kn > 0) || !(I.rho_ref > 0)) return bail(QL_EINVAL, id + "bad gas parameters");
+        if (I.bc.kind != QL_BC_PERIODIC && I.bc.kind != QL_BC_FIXED) return bail(QL_EINVAL, id + "bad bc");
+        if (I.pr_mode == QL_PR_CONST && !(I.pr_const > 0)) return bail(QL_EINVAL, id + "bad pr_const");
+        double eta0;
+        if (!eta_of_denseness(I.denseness, &eta0)) return bail(QL_EINVAL, id + "denseness out of range");
+        BatchInstance &D = b->inst[i];
+        D.nx = I.grid.nx;
+        D.stride = row_stride(D.nx);
+        D.off = off;
+        off += int64_t(I.vs.Q) * D.stride;
+        D.inv_dx = double(D.nx) / I.grid.length;
+        D.dt = I.grid.dt;
+        D.eta0 = eta0;
+        D.inv_rho_ref = 1.0 / I.rho_ref;
+        D.tau_pref = 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * I.kn * I.grid.length * chi_set(eta0);
+        D.pr_const = I.pr_const;
+        D.Q = I.vs.Q;
+        D.pr_mode = I.pr_mode;
+        D.enskog = I.enskog ? 1 : 0;
+        D.periodic = I.bc.kind == QL_BC_PERIODIC;
+        b->updates[i] = double(D.nx) * D.Q;
+        b->max_nx = std::max(b->max_nx, D.nx);
+        const int64_t ncol = D.nx + 2 * kHalo;
+        fields[i].resize(3 * ncol);
+        if (!initial_fields(I.init.kind, I.init.prm, D.nx, I.grid.length, D.periodic, eta0, I.rho_ref, I.init.rho,
+                            I.init.u, I.init.T, I.init.ghost, kHalo, fields[i].data(), fields[i].data() + ncol,
+                            fields[i].data() + 2 * ncol))
+            return bail(QL_EINVAL, id + "invalid initial state for this init kind / boundary");
+    }
+    // work lists: all tiles of instance 0, then instance 1, ...
+    std::vector<int2> work[2];
+    for (int wi = 0; wi < 2; ++wi) {
+        const int tile = 31 * kBatchWarps[wi];
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t nt = (b->inst[i].nx + tile - 1) / tile;
+            for (int64_t t = 0; t < nt; ++t) work[wi].push_back(make_int2(int(i), int(t)));
+        }
+        b->nwork[wi] = int64_t(work[wi].size());
+    }
+
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (opts->stream) {
+        b->stream = static_cast<cudaStream_t>(opts->stream);
+    } else {
+        // graph capture needs a stream other than the legacy default stream
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(QL_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+        b->own_stream = true;
+    }
+    static double tab[kTabTotal];
+    if (!build_tables(tab)) return bail(QL_EINVAL, "velocity-set construction failed");
+    e = upload_tables_f32(tab);
+    if (e == cudaSuccess) e = upload_tables_f64(tab);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+
+    b->arena_bytes = size_t(off) * b->elem;
+    for (int j = 0; j < 3; ++j) {
+        b->arena[j] = balloc(b, b->arena_bytes);
+        if (!b->arena[j]) return bail(QL_ENOMEM, "arena allocation failed");
+    }
+    b->d_inst = static_cast<BatchInstance *>(balloc(b, sizeof(BatchInstance) * n));
+    for (int wi = 0; wi < 2; ++wi) b->d_work[wi] = static_cast<int2 *>(balloc(b, sizeof(int2) * work[wi].size()));
+    b->d_err = static_cast<unsigned *>(balloc(b, sizeof(unsigned) * n));
+    b->d_tab64 = static_cast<double *>(balloc(b, sizeof(double) * kTabTotal));
+    b->d_fields = static_cast<double *>(balloc(b, sizeof(double) * 6 * b->max_nx));
+    b->d_partial = static_cast<double *>(balloc(b, sizeof(double) * 3 * moment_blocks(b->max_nx)));
+    b->d_totals = static_cast<double *>(balloc(b, sizeof(double) * 4));
+    b->d_init = static_cast<double *>(balloc(b, sizeof(double) * 3 * (b->max_nx + 2 * kHalo)));
+    if (!b->d_inst || !b->d_work[0] || !b->d_work[1] || !b->d_err || !b->d_tab64 || !b->d_fields || !b->d_partial ||
+        !b->d_totals || !b->d_init)
+        return bail(QL_ENOMEM, "work buffer allocation failed");
+    e = cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
+    for (int wi = 0; wi < 2 && e == cudaSuccess; ++wi)
+        e = cudaMemcpyAsync(b->d_work[wi], work[wi].data(), sizeof(int2) * work[wi].size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned) * n, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_tab64, tab, sizeof(double) * kTabTotal, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->arena[0], 0, b->arena_bytes, b->stream);
+    for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
+        const BatchInstance &D = b->inst[i];
+        const int64_t ncol = D.nx + 2 * kHalo;
+        e = cudaMemcpyAsync(b->d_init, fields[i].data(), sizeof(double) * 3 * ncol, cudaMemcpyHostToDevice, b->stream);
+        void *psi = static_cast<unsigned char *>(b->arena[0]) + size_t(D.off) * b->elem;
+        if (e == cudaSuccess)
+            e = b->precision == QL_FP32 ? launch_init_f32(D.Q, b->d_init, b->d_init + ncol, b->d_init + 2 * ncol, psi,
+                                                          D.nx, D.stride, b->d_tab64, b->stream)
+                                        : launch_init_f64(D.Q, b->d_init, b->d_init + ncol, b->d_init + 2 * ncol, psi,
+                                                          D.nx, D.stride, b->d_tab64, b->stream);
+        // d_init is reused by the next instance: wait before overwriting it from the host
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    for (int j = 1; j < 3 && e == cudaSuccess; ++j)
+        e = cudaMemcpyAsync(b->arena[j], b->arena[0], b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+    b->warps = kBatchWarps[0];
+    b->grid = b->sms * std::max(1, ctas_per_sm(b, b->warps));
+    *out = b;
+    return QL_OK;
+}
+
+ql_status ql_batch_tune(ql_batch *b, int32_t trial_launches, int32_t *warps_out, int32_t *ctas_per_sm_out)
+{
+    if (!b || trial_launches < 1) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_tune");
+    cudaEvent_t e0, e1;
+    QB_CUDA(b, cudaEventCreate(&e0));
+    QB_CUDA(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bw = b->warps, bg = b->grid;
+    for (int wi = 0; wi < 2; ++wi) {
+        const int w = kBatchWarps[wi];
+        const int cmax = ctas_per_sm(b, w);
+        for (int c = 1; c <= cmax; ++c) {
+            const int grid = b->sms * c;
+            // stage 1 reads psi^n and writes psi^(1) only, so timing it leaves the state unchanged
+            QB_CUDA(b, launch_stage(b, 1, w, grid));
+            QB_CUDA(b, cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < trial_launches; ++r) QB_CUDA(b, launch_stage(b, 1, w, grid));
+            QB_CUDA(b, cudaEventRecord(e1, b->stream));
+            QB_CUDA(b, cudaEventSynchronize(e1));
+            float ms = 0;
+            QB_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bw = w;
+                bg = grid;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->warps = bw;
+    b->grid = bg;
+    if (warps_out) *warps_out = bw;
+    if (ctas_per_sm_out) *ctas_per_sm_out = bg / std::max(1, b->sms);
+    return QL_OK;
+}
+
+ql_status ql_batch_run(ql_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_run");
+    if (nsteps == 0) return QL_OK;
+    if (!b->graph || b->graph_steps != nsteps || b->graph_warps != b->warps || b->graph_grid != b->grid) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        QB_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s)
+            for (int st = 1; st <= 3 && e == cudaSuccess; ++st) e = launch_stage(b, st, b->warps, b->grid);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bcuda(b, e != cudaSuccess ? e : e2, "graph capture");
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+        b->graph_steps = nsteps;
+        b->graph_warps = b->warps;
+        b->graph_grid = b->grid;
+    }
+    QB_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    return QL_OK;
+}
+
+ql_status ql_batch_sync(ql_batch *b, uint32_t *flags)
+{
+    if (!b) return bfail(b, QL_EINVAL, "null batch");
+    std::vector<unsigned> h(b->n);
+    QB_CUDA(b, cudaMemcpyAsync(h.data(), b->d_err, sizeof(unsigned) * b->n, cudaMemcpyDeviceToHost, b->stream));
+    QB_CUDA(b, cudaStreamSynchronize(b->stream));
+    bool bad = false;
+    for (int64_t i = 0; i < b->n; ++i) {
+        if (flags) flags[i] = h[i];
+        bad |= (h[i] & 1u) != 0;
+    }
+    if (bad) return bfail(b, QL_ENONPHYSICAL, "non-physical state in at least one instance");
+    return QL_OK;
+}
+
+ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, double *T, double *P, double *q,
+                           double *Pxx, double *totals)
+{
+    if (!b || i < 0 || i >= b->n) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_moments");
+    const BatchInstance &D = b->inst[i];
+    MomentArgs a;
+    a.psi = static_cast<unsigned char *>(b->arena[0]) + size_t(D.off) * b->elem;
+    a.nx = D.nx;
+    a.stride = D.stride;
+    a.eta0 = D.eta0;
+    a.inv_rho_ref = D.inv_rho_ref;
+    a.dx = 1.0 / D.inv_dx;
+    double *f = b->d_fields;
+    a.rho = f;
+    a.u = f + D.nx;
+    a.T = f + 2 * D.nx;
+    a.P = f + 3 * D.nx;
+    a.q = f + 4 * D.nx;
+    a.Pxx = f + 5 * D.nx;
+    a.partial = b->d_partial;
+    a.err = b->d_err + i;
+    cudaError_t e = b->precision == QL_FP32 ? launch_moments_f32(D.Q, a, b->d_tab64, b->stream)
+                                            : launch_moments_f64(D.Q, a, b->d_tab64, b->stream);
+    if (e == cudaSuccess) e = launch_reduce_totals(b->d_partial, moment_blocks(D.nx), b->d_totals, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "moments kernel");
+    double *outs[6] = {rho, u, T, P, q, Pxx};
+    for (int j = 0; j < 6; ++j)
+        if (outs[j])
+            QB_CUDA(b, cudaMemcpyAsync(outs[j], f + j * D.nx, sizeof(double) * D.nx, cudaMemcpyDeviceToHost, b->stream));
+    if (totals) QB_CUDA(b, cudaMemcpyAsync(totals, b->d_totals, sizeof(double) * 3, cudaMemcpyDeviceToHost, b->stream));
+    unsigned h = 0;
+    QB_CUDA(b, cudaMemcpyAsync(&h, b->d_err + i, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    QB_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (h & 1u) return bfail(b, QL_ENONPHYSICAL, "non-physical state in instance " + std::to_string(i));
+    return QL_OK;
+}
+
+ql_status ql_batch_get_state(ql_batch *b, int64_t i, double *phi, double *theta)
+{
+    if (!b || i < 0 || i >= b->n) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_get_state");
+    const BatchInstance &D = b->inst[i];
+    const int Q = D.Q;
+    const int64_t nx = D.nx;
+    std::vector<unsigned char> h(size_t(Q) * nx * b->elem);
+    const unsigned char *src = static_cast<const unsigned char *>(b->arena[0]) + size_t(D.off + kHalo) * b->elem;
+    QB_CUDA(b, cudaMemcpy2DAsync(h.data(), nx * b->elem, src, D.stride * b->elem, nx * b->elem, Q,
+                                 cudaMemcpyDeviceToHost, b->stream));
+    QB_CUDA(b, cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < Q; ++k)
+        for (int64_t c = 0; c < nx; ++c) {
+            const size_t s = 2 * (size_t(k) * nx + c);
+            double f, t;
+            if (b->precision == QL_FP32) {
+                f = reinterpret_cast<const float *>(h.data())[s];
+                t = reinterpret_cast<const float *>(h.data())[s + 1];
+            } else {
+                f = reinterpret_cast<const double *>(h.data())[s];
+                t = reinterpret_cast<const double *>(h.data())[s + 1];
+            }
+            if (phi) phi[c * Q + k] = f;
+            if (theta) theta[c * Q + k] = t;
+        }
+    return QL_OK;
+}
+
+ql_status ql_batch_info(const ql_batch *b, double *out)
+{
+    if (!b || !out) return QL_EINVAL;
+    double upd = 0;
+    for (double v : b->updates) upd += v;
+    out[0] = double(b->n);
+    out[1] = upd;
+    out[2] = b->warps;
+    out[3] = b->grid;
+    out[4] = double(b->arena_bytes);
+    out[5] = double(b->sms);
+    return QL_OK;
+}
+
+ql_status ql_batch_destroy(ql_batch *b)
+{
+    if (!b) return QL_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
+    return QL_OK;
+}
+
+const char *ql_batch_last_error(const ql_batch *b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+}  // extern "C"

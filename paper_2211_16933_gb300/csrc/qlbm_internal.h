@@ -29,17 +29,14 @@ constexpr int kHalo = 4;
 constexpr int kSeg = kTile + 2 * kHalo;
 static_assert(kSeg == kThreads, "one staged cell per thread in the moment phase");
 
-// Row layout of a state buffer: 2Q rows (phi rows k = 0..Q-1, then theta
-// rows), each of `stride` elements; cell i (-kHalo <= i < nx + kHalo) of row r
-// sits at r * stride + kHalo + i.  stride covers every staged segment of the
-// last tile and is a multiple of 32 elements.
+// Row layout of a state buffer: Q rows, one per velocity k, each of `stride`
+// pairs (phi_k, theta_k) of the working precision; cell i (-kHalo <= i <
+// nx + kHalo) of row k sits at pair k * stride + kHalo + i.  stride covers
+// every staged segment of the last tile and is a multiple of 32 pairs.
 inline int64_t num_tiles(int64_t nx) { return (nx + kTile - 1) / kTile; }
-inline int64_t row_stride(int64_t nx)
-{
-    int64_t need = (num_tiles(nx) - 1) * kTile + kSeg;
-    if (need < nx + 2 * kHalo) need = nx + 2 * kHalo;
-    return (need + 31) / 32 * 32;
-}
+// Any tile of at most 248 cells staged from any start i0 < nx stays inside the
+// row: (i0 + tile + 2 kHalo) - (-kHalo) <= nx + 256 + kHalo.
+inline int64_t row_stride(int64_t nx) { return (nx + 256 + 2 * kHalo + 31) / 32 * 32; }
 
 // Per-Q constant tables, built on the host in FP64 and stored per precision.
 //   p[k], p2[k] = p^2, p3[k] = p^3: velocities, ascending
@@ -76,6 +73,23 @@ struct StageArgs {
     unsigned *err;  // device error word; bit 0: non-physical cell
 };
 
+// Batched form: instances packed in three arenas (psi^n, psi^(1), psi^(2)),
+// instance rows starting at pair offset `off` in each.
+struct BatchInstance {
+    int64_t nx, stride, off;
+    double inv_dx, dt, eta0, inv_rho_ref, tau_pref, pr_const;
+    int32_t Q, pr_mode, enskog, periodic;
+};
+struct BatchArgs {
+    const BatchInstance *inst;
+    const int2 *work;  // (instance, tile) items
+    int64_t nwork;
+    void *arena[3];
+    unsigned *err;  // one error word per instance
+};
+// Tile shapes the batched kernels are compiled for (warps per CTA).
+constexpr int kBatchWarps[2] = {8, 4};
+
 // Uploads all tables (kTabTotal doubles, laid out by tab_view) to the
 // current device, rounded to the precision of the translation unit.
 cudaError_t upload_tables_f32(const double *all);
@@ -94,7 +108,7 @@ cudaError_t launch_init_f64(int Q, const double *rho, const double *u, const dou
                             int64_t nx, int64_t stride, const double *tab64, cudaStream_t s);
 
 // Copies the kHalo cells next to each end into the ghost columns of the
-// other end (periodic images), all 2Q rows.
+// other end (periodic images), all Q rows.
 cudaError_t launch_periodic_ghosts_f32(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s);
 cudaError_t launch_periodic_ghosts_f64(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s);
 
@@ -109,6 +123,14 @@ struct MomentArgs {
 };
 constexpr int kMomThreads = 256;
 inline int64_t moment_blocks(int64_t nx) { return (nx + kMomThreads - 1) / kMomThreads; }
+// One batched stage over the work list: `grid` persistent CTAs of `warps`
+// warps (8 or 4; the work list must be built for the same tile width).
+cudaError_t launch_batch_stage_f32(int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
+cudaError_t launch_batch_stage_f64(int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
+// Resident CTAs per SM of the batched kernel (occupancy calculator).
+int batch_ctas_per_sm_f32(int stage, int warps);
+int batch_ctas_per_sm_f64(int stage, int warps);
+
 cudaError_t launch_moments_f32(int Q, const MomentArgs &a, const double *tab64, cudaStream_t s);
 cudaError_t launch_moments_f64(int Q, const MomentArgs &a, const double *tab64, cudaStream_t s);
 // totals[3] = fixed-order sum of partial[nblocks][3]

@@ -23,7 +23,9 @@ QL_PR_CONST, QL_PR_DENSE = 0, 1
 SUPPORTED_Q = (8, 16, 24, 32)
 EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_get_state", "ql_set_state",
             "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",
-            "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error")
+            "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error",
+            "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
+            "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error")
 
 
 class QLError(RuntimeError):
@@ -62,6 +64,12 @@ class ql_opts(C.Structure):
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
+class ql_instance(C.Structure):
+    _fields_ = [("vs", ql_velset), ("grid", ql_grid), ("denseness", C.c_double), ("kn", C.c_double),
+                ("bc", ql_bc), ("init", ql_init), ("pr_mode", C.c_int32), ("enskog", C.c_int32),
+                ("pr_const", C.c_double), ("rho_ref", C.c_double)]
+
+
 _lib = None
 
 
@@ -93,6 +101,16 @@ def lib():
         L.ql_sound_speed2.argtypes = [C.c_double] * 4
         L.ql_sound_speed2.restype = C.c_double
         L.ql_rankine_hugoniot.argtypes = [C.c_double] * 5 + [_DP]
+        L.ql_batch_create.argtypes = [C.POINTER(ql_instance), C.c_int64, C.POINTER(ql_opts), C.POINTER(V)]
+        L.ql_batch_tune.argtypes = [V, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.ql_batch_run.argtypes = [V, C.c_int64]
+        L.ql_batch_sync.argtypes = [V, C.POINTER(C.c_uint32)]
+        L.ql_batch_moments.argtypes = [V, C.c_int64] + [_DP] * 7
+        L.ql_batch_get_state.argtypes = [V, C.c_int64, _DP, _DP]
+        L.ql_batch_info.argtypes = [V, _DP]
+        L.ql_batch_destroy.argtypes = [V]
+        L.ql_batch_last_error.argtypes = [V]
+        L.ql_batch_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -187,6 +205,134 @@ def ql_info(ctx, Q):
 
 def ql_destroy(ctx):
     _check(lib().ql_destroy(ctx))
+
+
+# ---------------------------------------------------------------- batched form
+def _bcheck(st, b=None):
+    if st != QL_OK:
+        msg = lib().ql_batch_last_error(b)
+        raise QLError(st, msg.decode() if msg else "")
+
+
+def ql_batch_create(insts, opts):
+    arr = (ql_instance * len(insts))(*insts)
+    b = C.c_void_p()
+    _bcheck(lib().ql_batch_create(arr, len(insts), C.byref(opts), C.byref(b)))
+    return b
+
+
+def ql_batch_tune(b, trial_launches=3):
+    w, c = C.c_int32(), C.c_int32()
+    _bcheck(lib().ql_batch_tune(b, trial_launches, C.byref(w), C.byref(c)), b)
+    return w.value, c.value
+
+
+def ql_batch_run(b, nsteps):
+    _bcheck(lib().ql_batch_run(b, nsteps), b)
+
+
+def ql_batch_sync(b, n):
+    flags = (C.c_uint32 * n)()
+    st = lib().ql_batch_sync(b, flags)
+    return st, np.array(flags[:], dtype=np.uint32)
+
+
+def ql_batch_moments(b, i, rho=None, u=None, T=None, P=None, q=None, Pxx=None, totals=None):
+    _bcheck(lib().ql_batch_moments(b, i, *[_ptr(a) for a in (rho, u, T, P, q, Pxx, totals)]), b)
+
+
+def ql_batch_get_state(b, i, phi, theta):
+    _bcheck(lib().ql_batch_get_state(b, i, _ptr(phi), _ptr(theta)), b)
+
+
+def ql_batch_info(b):
+    out = np.zeros(6)
+    _bcheck(lib().ql_batch_info(b, _ptr(out)), b)
+    return out
+
+
+def ql_batch_destroy(b):
+    _bcheck(lib().ql_batch_destroy(b))
+
+
+def make_instance(Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND, prm=(),
+                  pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, keep=None, rho=None, u=None, T=None,
+                  ghost=None):
+    """One ql_instance; `keep` (a list) holds the numpy arrays its pointers refer to."""
+    I = ql_instance()
+    I.vs = ql_velset(Q, 0)
+    I.grid = ql_grid(nx, length, dt)
+    I.denseness, I.kn = denseness, kn
+    I.bc = ql_bc(bc, 0)
+    I.init.kind = init_kind
+    for j, v in enumerate(prm):
+        I.init.prm[j] = v
+    for name, arr in (("rho", rho), ("u", u), ("T", T), ("ghost", ghost)):
+        if arr is not None:
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            if keep is not None:
+                keep.append(a)
+            setattr(I.init, name, _ptr(a))
+    I.pr_mode, I.enskog, I.pr_const, I.rho_ref = pr_mode, enskog, pr_const, rho_ref
+    return I
+
+
+class Batch:
+    """A batch of instances on one device; stream from PyTorch when available."""
+
+    def __init__(self, instances, precision=QL_FP32, device=0, use_torch=True):
+        o = ql_opts()
+        o.precision, o.device = precision, device
+        self.n = len(instances)
+        self.Qs = [I.vs.Q for I in instances]
+        self.nxs = [I.grid.nx for I in instances]
+        if use_torch:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.set_device(device)
+                self._stream = torch.cuda.Stream(device)
+                o.stream = C.c_void_p(self._stream.cuda_stream)
+        self.b = ql_batch_create(instances, o)
+
+    def tune(self, trial_launches=3):
+        return ql_batch_tune(self.b, trial_launches)
+
+    def run(self, nsteps):
+        ql_batch_run(self.b, nsteps)
+
+    def sync(self):
+        st, flags = ql_batch_sync(self.b, self.n)
+        if st != QL_OK:
+            _bcheck(st, self.b)
+        return flags
+
+    def moments(self, i):
+        nx = self.nxs[i]
+        out = {k: np.zeros(nx) for k in ("rho", "u", "T", "P", "q", "Pxx")}
+        tot = np.zeros(3)
+        ql_batch_moments(self.b, i, out["rho"], out["u"], out["T"], out["P"], out["q"], out["Pxx"], tot)
+        out["totals"] = tot
+        return out
+
+    def state(self, i):
+        nx, Q = self.nxs[i], self.Qs[i]
+        a, c = np.zeros(nx * Q), np.zeros(nx * Q)
+        ql_batch_get_state(self.b, i, a, c)
+        return a.reshape(nx, Q), c.reshape(nx, Q)
+
+    def info(self):
+        return ql_batch_info(self.b)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            ql_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience object

@@ -1,0 +1,110 @@
+"""Batched form: many uneven instances advanced by persistent stage kernels over one
+work list, captured in one CUDA graph.
+
+Each instance must come out bit-identical to the same instance advanced alone by
+ql_step (the per-tile arithmetic is the same device code; tile decomposition does
+not change any cell's arithmetic), whatever tile shape the tuner picks, and a
+sample matches the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2211_16933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(q, n, seed, keep):
+    spec = inputs.batch_instances(n=n, seed=seed)
+    out = []
+    for d in spec:
+        # smaller domains than the benchmark batch so that the test stays short
+        d = dict(d, nx=int(d["nx"] // 8 + 20))
+        p, _ = q.ql_velocity_set(d["Q"])
+        dt = inputs.cfl_dt(d["length"] / d["nx"], abs(p).max())
+        if d["kind"] == "sound":
+            I = q.make_instance(d["Q"], d["nx"], d["length"], dt, d["denseness"], d["kn"], bc=q.QL_BC_PERIODIC,
+                                init_kind=q.QL_INIT_SOUND, prm=d["prm"], keep=keep)
+        else:
+            I = q.make_instance(d["Q"], d["nx"], d["length"], dt, d["denseness"], d["kn"], bc=q.QL_BC_FIXED,
+                                init_kind=q.QL_INIT_SHOCK, prm=d["prm"], keep=keep)
+        out.append((d, dt, I))
+    return out
+
+
+def _single(q, d, dt, precision, steps):
+    bc = q.QL_BC_PERIODIC if d["kind"] == "sound" else q.QL_BC_FIXED
+    kind = q.QL_INIT_SOUND if d["kind"] == "sound" else q.QL_INIT_SHOCK
+    s = q.Solver(d["Q"], d["nx"], d["length"], dt, d["denseness"], d["kn"], bc=bc, init_kind=kind, prm=d["prm"],
+                 precision=precision, pr_mode=q.QL_PR_DENSE)
+    s.step(steps)
+    st = s.state()
+    s.close()
+    return st
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_single_instance_runs_bitwise(gpu, precision):
+    q = gpu
+    keep = []
+    items = _instances(q, 14, 7, keep)
+    b = q.Batch([I for _, _, I in items], precision=precision)
+    b.run(5)
+    flags = b.sync()
+    assert not flags.any()
+    for i in (0, 1, 4, 7, 10, 13):
+        d, dt, _ = items[i]
+        a = b.state(i)
+        r = _single(q, d, dt, precision, 5)
+        np.testing.assert_array_equal(a[0], r[0])
+        np.testing.assert_array_equal(a[1], r[1])
+    b.close()
+
+
+def test_batch_tuning_keeps_results(gpu):
+    q = gpu
+    keep = []
+    items = _instances(q, 10, 3, keep)
+    b1 = q.Batch([I for _, _, I in items], precision=1)
+    w, c = b1.tune(2)
+    assert w in (8, 4) and c >= 1
+    b1.run(4)
+    b1.sync()
+    b2 = q.Batch([I for _, _, I in items], precision=1)
+    b2.run(2)
+    b2.run(2)  # a second graph launch continues the run
+    b2.sync()
+    for i in range(len(items)):
+        x, y = b1.state(i), b2.state(i)
+        np.testing.assert_array_equal(x[0], y[0])
+        np.testing.assert_array_equal(x[1], y[1])
+    info = b1.info()
+    assert info[0] == len(items) and info[2] == w
+    b1.close()
+    b2.close()
+
+
+def test_batch_sample_matches_oracle(gpu):
+    """FP64 batch against the oracle on a sound-wave and a shock instance of the batch."""
+    q = gpu
+    keep = []
+    items = _instances(q, 6, 11, keep)
+    b = q.Batch([I for _, _, I in items], precision=0)
+    b.run(3)
+    b.sync()
+    for i in (0, 1):
+        d, dt, _ = items[i]
+        bc = O.BC_PERIODIC if d["kind"] == "sound" else O.BC_FIXED
+        m = O.make_model(d["Q"], d["nx"], d["length"], dt, d["denseness"], d["kn"], pr_mode=1, bc=bc)
+        kind = O.INIT_SOUND if d["kind"] == "sound" else O.INIT_SHOCK
+        r, u, T = O.init_fields(m, kind, d["prm"])
+        if bc == O.BC_FIXED:
+            O.set_ghosts_from_init(m, kind, d["prm"])
+        ph, th = O.equilibrium_state(m, r, u, T)
+        ph, th = O.run(m, ph, th, 3)
+        fo = O.fields(m, ph, th)
+        fg = b.moments(i)
+        for k in ("rho", "u", "T", "q"):
+            assert float(np.abs(fg[k] - fo[k]).max()) <= 1e-10, (i, k)
+    b.close()
