@@ -1,5 +1,10 @@
 """Builds libqlbm.so (the CUDA library behind include/qlbm.h) in-tree for sm_103a.
 
+Device code is compiled with -fmad=false: every fused multiply-add in the kernels
+is written out explicitly, so the arithmetic does not depend on how the compiler
+contracts a product and a sum in a given context, and the same per-tile code gives
+bit-identical results in the single-domain and the batched kernels.
+
 Translation units compile in parallel with nvcc; objects go to _build/ next to
 this file.  A rebuild happens only when a source or header is newer than the
 library.
@@ -18,7 +23,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqlbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 UNITS = ["qlbm_api.cu", "qlbm_batch.cu", "qlbm_host.cpp", "fdlb_f32.cu", "fdlb_f64.cu"]
 
 

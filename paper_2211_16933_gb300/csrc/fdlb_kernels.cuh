@@ -242,28 +242,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             tR0 += s01.y;
             tR1 += s11.y;
         }
-        // 1/n to full FP64 precision from a working-precision reciprocal and two Newton steps
+        // 1/n from a working-precision reciprocal refined by Newton steps in FP64
+        // (one step gives ~1e-14 after an FP32 seed, two after FP64's own division)
         const double n = M0;
         double rn = double(rcp_(Real(n)));
         rn = fma(rn, fma(-n, rn, 1.0), rn);
-        rn = fma(rn, fma(-n, rn, 1.0), rn);
+        if (sizeof(Real) == 8) rn = fma(rn, fma(-n, rn, 1.0), rn);
         const double u = M1 * rn;
         // 3 n T = sum xi^2 phi + sum theta = (S2 + R0) - u S1
         const double T = fma(-u, M1, ME) * rn * (1.0 / 3.0);
         // 2 q = sum xi^3 phi + sum xi theta = S3 + R1 - u (3 S2 + R0) + 2 u^2 S1
-        const Real uf = Real(u);
-        const Real q = Real(0.5) * (tS3 + tR1 - uf * fma(Real(3), tS2, tR0) + Real(2) * uf * uf * Real(M1));
+        const Real uf = Real(u), Tf = Real(T), nf = Real(n);
+        const Real q = Real(0.5) * (tS3 + tR1 - uf * fma(Real(3), tS2, tR0) + Real(2) * uf * uf * (uf * nf));
         const int64_t i = i0 - kHalo + c;
         if (i >= 0 && i < a.nx) {
-            if (!(n > 0.0) || !(T > 0.0) || !isfinite(u) || !isfinite(q) || !isfinite(n) || !isfinite(T))
+            if (!(nf > Real(0)) || !(Tf > Real(0)) || !isfinite(uf) || !isfinite(q) || !isfinite(nf) || !isfinite(Tf))
                 atomicOr(a.err, 1u);
         }
-        s_n[c] = Real(n);
+        s_n[c] = nf;
         s_u[c] = uf;
-        s_T[c] = Real(T);
+        s_T[c] = Tf;
         s_q[c] = q;
-        s_lnn[c] = log_(Real(n));
-        s_lnT[c] = log_(Real(T));
+        s_lnn[c] = log_(nf);
+        s_lnT[c] = log_(Tf);
     }
     __syncthreads();
 

@@ -42,6 +42,10 @@ static bool g_tables_ready[64] = {};
 static double g_tab[kTabTotal];
 static bool g_tab_built = false;
 
+namespace qlbm {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace qlbm
+
 static ql_status fail(ql_ctx *c, ql_status st, const std::string &msg)
 {
     if (c) c->err = msg; else g_create_error = msg;

@@ -156,7 +156,7 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
         D.stride = row_stride(D.nx);
         D.off = off;
         off += int64_t(I.vs.Q) * D.stride;
-        D.inv_dx = double(D.nx) / I.grid.length;
+        D.inv_dx = 1.0 / (I.grid.length / double(D.nx));  // as ql_create computes it
         D.dt = I.grid.dt;
         D.eta0 = eta0;
         D.inv_rho_ref = 1.0 / I.rho_ref;
