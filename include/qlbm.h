@@ -248,6 +248,43 @@ ql_status ql_batch_info(const ql_batch *b, double *out);
 ql_status ql_batch_destroy(ql_batch *b);
 const char *ql_batch_last_error(const ql_batch *b);
 
+/* ---- Stepping without allocation ----------------------------------------- */
+
+/* Largest scratch ql_step_noalloc uses, in bytes. */
+#define QL_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)
+
+/* Advances a caller-owned state by nsteps steps of Eq. (rk3), like ql_step,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that must not call cudaMalloc, for example
+ * code that runs under a memory budget another framework has already reserved
+ * (where an allocation can fail) or inside a latency-critical loop (where
+ * cudaMalloc can synchronise the whole device).
+ *   psi         device, caller-owned: the state in the layout ql_state_device
+ *               reports (Q rows of row_stride (phi, theta) pairs; psi points at
+ *               cell 0 of row 0 and cell i of row k is pair k * row_stride + i),
+ *               for -4 <= i < nx + 4: the 4 ghost columns on each side hold the
+ *               periodic images or the fixed boundary states (kept).  psi - 4
+ *               pairs must be 16-byte aligned.  Advanced in place.
+ *   row_stride  pairs per row, at least (nx + 264 + 31) / 32 * 32 (the stride
+ *               ql_state_device reports for a context of the same nx).
+ *   The other arguments are those of ql_create; from opts only precision,
+ *   pr_mode, enskog, device, pr_const, rho_ref and stream are used.
+ * The two intermediate stage buffers and the error word live in one fixed
+ * scratch array of QL_NOALLOC_MAX_BYTES that every GPU loading this library
+ * holds until the process exits; a state whose two stage buffers (2 Q
+ * row_stride pairs) do not fit is rejected with QL_EINVAL before any device
+ * work.  Every call shares that array and finds the previous call's contents
+ * there (the error word is cleared on entry), so calls that overlap on the GPU
+ * (other threads, other streams) race and must be serialised by the caller.
+ * The first call on a device also uploads the kernel tables and looks up the
+ * scratch address on that device; make that first call before any stream
+ * capture.  The call returns after the stream has run the steps.  Errors:
+ * QL_EINVAL, QL_EUNSUPPORTED, QL_ECUDA, QL_ENONPHYSICAL; ql_last_error(NULL)
+ * describes them. */
+ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double denseness, double kn,
+                          const ql_bc *bc, const ql_opts *opts, void *psi, int64_t row_stride,
+                          int64_t nsteps);
+
 /* ---- Host-only helpers (no GPU needed), FP64 ---------------------------- */
 
 /* Velocity set of Sec. II.D: p (ascending) and w (summing to 1), each a host

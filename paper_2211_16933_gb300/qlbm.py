@@ -25,7 +25,7 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",
             "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error",
             "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
-            "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error")
+            "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc")
 
 
 class QLError(RuntimeError):
@@ -111,6 +111,8 @@ def lib():
         L.ql_batch_destroy.argtypes = [V]
         L.ql_batch_last_error.argtypes = [V]
         L.ql_batch_last_error.restype = C.c_char_p
+        L.ql_step_noalloc.argtypes = [C.POINTER(ql_velset), C.POINTER(ql_grid), C.c_double, C.c_double,
+                                      C.POINTER(ql_bc), C.POINTER(ql_opts), V, C.c_int64, C.c_int64]
         _lib = L
     return _lib
 
@@ -205,6 +207,12 @@ def ql_info(ctx, Q):
 
 def ql_destroy(ctx):
     _check(lib().ql_destroy(ctx))
+
+
+def ql_step_noalloc(vs, grid, denseness, kn, bc, opts, psi, row_stride, nsteps):
+    """Steps a caller-owned device state (pointer psi) without any allocation."""
+    _check(lib().ql_step_noalloc(C.byref(vs), C.byref(grid), denseness, kn, C.byref(bc), C.byref(opts),
+                                 C.c_void_p(psi), row_stride, nsteps))
 
 
 # ---------------------------------------------------------------- batched form
