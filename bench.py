@@ -271,7 +271,8 @@ def run_ours(args, w):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if prec == q.QL_FP32 else "f64", "data": "synthetic",
                 "config": {"workload": w["name"], "nx": nx, "Q": Q, "precision": args.precision,
-                           "sums": "f64 per-cell conserved moments" if prec == q.QL_FP32 else "f64",
+                           "sums": "per-cell conserved sums: f32 groups of 8 pairs combined in double-f32, u and T in double-f32"
+                           if prec == q.QL_FP32 else "f64",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (3 state buffers of %.2f GiB)" % (
                                2 * Q * nx * elem / 2 ** 30)},
@@ -297,7 +298,7 @@ def _batch_instances(q, inputs, n, seed, nx_div=1):
 
 
 def run_batch(args):
-    """Batched form: 4096 uneven instances (seed 20221130), FP32 state with FP64 conserved sums,
+    """Batched form: 4096 uneven instances (seed 20221130), FP32 state with double-FP32 conserved sums,
     one CUDA-graph launch of K steps; plus time to solution against plain FP64 solves."""
     import torch
     from paper_2211_16933_gb300 import build as B
@@ -357,7 +358,7 @@ def run_batch(args):
             "config": {"workload": f"batch_{args.batch_n}_uneven_sound_and_shock", "instances": args.batch_n,
                        "updates_per_step": upd_per_step, "tuned_warps_per_cta": warps, "tuned_ctas_per_sm": ctas,
                        "graph": "one CUDA graph launch of 3 x steps persistent stage kernels",
-                       "sums": "f64 per-cell conserved moments", "setup_s": setup_s},
+                       "sums": "per-cell conserved sums combined in double-f32", "setup_s": setup_s},
             "gpu_launches": 3 * args.steps, "clocks": clocks, "nonphysical_instances": int((flags & 1).sum()),
             "time_to_solution": {"instances": sub_n, "steps": sub_steps, "batched_fp32_s": t_batch,
                                  "plain_fp64_sequential_s": t_plain, "speedup": t_plain / t_batch,
@@ -365,10 +366,115 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned coarse closure: training pairs from the solver (fine 4096 / coarse 512 cells), training on the
+    GPU with the library's BF16 kernels, held-out errors against the fine solve, and time to solution of
+    coarse + network against the fine solve (batched FP32, and plain FP64 single-domain solves)."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import learned as L
+    from paper_2211_16933_gb300 import qlbm as q
+    torch.cuda.set_device(0)
+    B.build()
+    S = args.fine_steps
+
+    def gen(specs, chunk=4096):
+        parts = [L.generate(specs[c:c + chunk], fine_steps=S) for c in range(0, len(specs), chunk)]
+        return [torch.cat([p[k] for p in parts]) for k in range(4)]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, y, per, _ = gen(L.pair_specs(args.pairs, 0))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, losses = L.train(x, y, per, epochs=args.epochs, batch=args.train_batch, lr=args.lr, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    nsamp = (x.shape[0] // args.train_batch) * args.train_batch * args.epochs
+    # conv FLOPs of one sample over real channels: forward 2 X 5 sum(cin cout); training about 3x forward
+    X = x.shape[1]
+    fwd = sum(2 * X * 5 * ci * co for ci, co in [(7, 64), (64, 64), (64, 64), (64, 64), (64, 5)])
+    train_tflops = 3 * fwd * nsamp / t_train / 1e12
+    del x, y, per
+
+    # held-out pairs, 8 snapshots each: coarse and coarse + network against the fine solve
+    xt, yt, pt, _ = gen(L.pair_specs(args.eval_pairs, 10 ** 6))
+    pred = L.predict(net, xt, pt, args.train_batch)
+    held = {"pairs": args.eval_pairs, "snapshots": 8, "reference": "fine FP32 batched solve",
+            "err_coarse": L.field_errors(yt * 0, yt), "err_coarse_plus_net": L.field_errors(pred, yt)}
+    del xt, yt, pt, pred
+
+    # time to solution on a subset, final snapshot: coarse FP32 batch + network, fine FP32 batch, and plain
+    # FP64 fine solves one after another (the paper's method at full resolution)
+    specs = L.pair_specs(args.tts_pairs, 2 * 10 ** 6)
+    n = len(specs)
+    consts, periodic = L.const_channels(specs, torch.device("cuda", 0))
+    cf = torch.empty(n * 5 * L.NC, dtype=torch.float64, device="cuda")
+    ff = torch.empty(n * 5 * L.NC, dtype=torch.float64, device="cuda")
+    cur = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ci, keep_c = L._instances(specs, L.NC, lambda s_: 8.0 * L._fine_dt(s_))
+    cb = q.Batch(ci, precision=q.QL_FP32)
+    cb._stream.wait_stream(cur)
+    cb.run(S // 8)
+    cb.fields(L.NC, cf)
+    cur.wait_stream(cb._stream)
+    Cc = cf.view(n, 5, L.NC).permute(0, 2, 1).float().contiguous()
+    corr = L.predict(net, torch.cat([Cc, consts[:, None, :].expand(n, L.NC, 2)], dim=2).contiguous(), periodic,
+                     args.train_batch)
+    learned = (Cc + corr).double().cpu()
+    t_learned = time.perf_counter() - t0
+    cb.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fi, keep_f = L._instances(specs, L.NF, L._fine_dt)
+    fb = q.Batch(fi, precision=q.QL_FP32)
+    fb._stream.wait_stream(cur)
+    fb.run(S)
+    fb.fields(L.NC, ff)
+    cur.wait_stream(fb._stream)
+    fine32 = ff.view(n, 5, L.NC).permute(0, 2, 1).cpu()
+    t_fine32 = time.perf_counter() - t0
+    fb.close()
+    t0 = time.perf_counter()
+    fine64 = []
+    for s_ in specs:
+        sound = s_["kind"] == "sound"
+        sv = q.Solver(s_["Q"], L.NF, s_["length"], L._fine_dt(s_), s_["denseness"], s_["kn"],
+                      bc=q.QL_BC_PERIODIC if sound else q.QL_BC_FIXED,
+                      init_kind=q.QL_INIT_SOUND if sound else q.QL_INIT_SHOCK, prm=s_["prm"], precision=q.QL_FP64,
+                      pr_mode=q.QL_PR_DENSE)
+        sv.step(S)
+        f = sv.moments()
+        sv.close()
+        fine64.append(np.stack([f[k].reshape(L.NC, 8).mean(1) for k in L.FIELDS], axis=1))
+    t_fine64 = time.perf_counter() - t0
+    ref = torch.tensor(np.stack(fine64))
+    line = {"metric": "training samples/s", "value": nsamp / t_train, "unit": "samples/s", "n_gpus": 1,
+            "steps": args.epochs, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "learned_closure_conv1d_5x64_k5", "pairs": args.pairs, "snapshots": 8,
+                       "fine_cells": L.NF, "coarse_cells": L.NC, "fine_steps": S, "epochs": args.epochs,
+                       "batch": args.train_batch, "lr": args.lr, "lr_schedule": "cosine to lr/20"},
+            # per training step: pack, 5 convs, mse, 5 wgrads + 5 partial sums, 4 edge terms + 4 transposed
+            # convs, adam, 5 weight casts
+            "gpu_launches": 31 * (nsamp // args.train_batch), "train_conv_tflops": train_tflops, "data_generation_s": t_gen,
+            "train_s": t_train, "loss_per_epoch": losses, "held_out": held,
+            "time_to_solution": {"pairs": n, "coarse_fp32_batch_plus_net_s": t_learned,
+                                 "fine_fp32_batch_s": t_fine32, "plain_fp64_fine_sequential_s": t_fine64,
+                                 "speedup_vs_fp64_fine": t_fine64 / t_learned,
+                                 "speedup_vs_fp32_fine_batch": t_fine32 / t_learned,
+                                 "err_vs_fp64_fine": {"coarse_plus_net": L.field_errors(learned, ref),
+                                                      "fine_fp32_batch": L.field_errors(fine32, ref)}}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
@@ -377,7 +483,14 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sod", "batch"], default="sod")
+    ap.add_argument("--workload", choices=["sod", "batch", "learned"], default="sod")
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--eval-pairs", type=int, default=1000)
+    ap.add_argument("--tts-pairs", type=int, default=16)
+    ap.add_argument("--fine-steps", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--train-batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--tts-instances", type=int, default=64)
     ap.add_argument("--tts-steps", type=int, default=100)
@@ -386,6 +499,9 @@ def main():
     w = inputs.sod_tube(nx=args.nx, Q=args.q)
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)
+        return
+    if args.workload == "learned" and args.impl == "ours":
+        run_learned(args)
         return
     if args.impl == "reference":
         run_reference(args, w)

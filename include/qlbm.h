@@ -108,8 +108,9 @@ typedef void (*ql_free_fn)(void *ptr, void *user);
 
 /* Options.
  *   precision  QL_FP64: state, update and sums in FP64.
- *              QL_FP32: state and update in FP32, per-cell conserved-moment
- *              sums and the domain totals in FP64.
+ *              QL_FP32: state and update in FP32; per-cell conserved-moment
+ *              sums combined, and u and T derived, in double-FP32 (about 48
+ *              significant bits); the domain totals in FP64.
  *   pr_mode    QL_PR_CONST uses pr_const; QL_PR_DENSE the Prandtl number of
  *              the dense gas as a function of b rho chi (Sec. II.B).
  *   enskog     1 adds the simplified-Enskog term J1 of Eq. (j1_expanded);
@@ -238,6 +239,13 @@ ql_status ql_batch_sync(ql_batch *b, uint32_t *flags);
 ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, double *T, double *P, double *q,
                            double *Pxx, double *totals);
 
+/* Fields of every instance on the device, averaged over blocks of nx/ncoarse
+ * cells (ncoarse must divide every instance's nx; ncoarse = nx gives the
+ * fields themselves): out (device, f64, n * 5 * ncoarse) holds, for instance
+ * i, rows rho, u, T, q, Pxx (Sec. II.D) of ncoarse values at offset
+ * i * 5 * ncoarse.  One launch; asynchronous. */
+ql_status ql_batch_fields(ql_batch *b, int32_t ncoarse, double *out);
+
 /* ql_get_state for instance i. */
 ql_status ql_batch_get_state(ql_batch *b, int64_t i, double *phi, double *theta);
 
@@ -247,6 +255,55 @@ ql_status ql_batch_info(const ql_batch *b, double *out);
 
 ql_status ql_batch_destroy(ql_batch *b);
 const char *ql_batch_last_error(const ql_batch *b);
+
+/* ---- Learned coarse-grid closure (not in the paper) ----------------------- */
+
+/* A 1D convolutional network that corrects moment fields computed on a coarse
+ * grid: layers convolutions of kernel size ksize over `positions` cells, width
+ * hidden channels, ReLU between layers, in_channels input features and
+ * out_channels outputs per cell.  BF16 weights and activations with FP32
+ * accumulation on the tensor cores; FP32 master weights trained by Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  Inputs are normalised as
+ * (x - in_shift) / in_scale, outputs are out_scale times the network output.
+ * This build supports ksize 5, width 64, in_channels and out_channels <= 8. */
+typedef struct ql_closure ql_closure; /* opaque, library-owned */
+typedef struct {
+    int32_t in_channels;
+    int32_t out_channels;
+    int32_t width;
+    int32_t layers;
+    int32_t ksize;
+    int32_t positions;
+    int32_t max_batch;
+    int32_t pad_;
+    uint64_t seed; /* seeded He-uniform initial weights, zero biases */
+    float in_shift[8], in_scale[8], out_scale[8];
+} ql_closure_desc;
+
+ql_status ql_closure_create(const ql_closure_desc *desc, const ql_opts *opts, ql_closure **out);
+
+/* Device arrays: x [B][positions][in_channels] f32, y [B][positions][out_channels]
+ * f32 (physical units), periodic [B] int32 (nonzero: periodic padding at the
+ * ends, zero: the end values are replicated).  1 <= B <= max_batch.  Asynchronous on the stream. */
+ql_status ql_closure_forward(ql_closure *c, const float *x, const int32_t *periodic, int64_t B, float *y);
+
+/* Mean squared error between the network and the targets y / out_scale, and its
+ * gradient for every parameter.  loss (host) and grad (host, count floats from
+ * ql_closure_params) may be NULL; either one synchronises. */
+ql_status ql_closure_gradients(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
+                               int64_t B, float *loss, float *grad);
+
+/* One Adam step on the mean squared error of the batch, learning rate lr. */
+ql_status ql_closure_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
+                                int64_t B, float lr, float *loss);
+
+/* Parameter vector (f32, host): for each layer W[cout][ksize][cin] then
+ * bias[cout], channels padded to 16 (padding stays zero).  get and set may be
+ * NULL; count (may be NULL) receives the length.  Synchronises. */
+ql_status ql_closure_params(ql_closure *c, float *get, const float *set, int64_t *count);
+
+ql_status ql_closure_destroy(ql_closure *c);
+const char *ql_closure_last_error(const ql_closure *c);
 
 /* ---- Stepping without allocation ----------------------------------------- */
 
@@ -266,7 +323,8 @@ const char *ql_batch_last_error(const ql_batch *b);
  *               periodic images or the fixed boundary states (kept).  psi - 4
  *               pairs must be 16-byte aligned.  Advanced in place.
  *   row_stride  pairs per row, at least (nx + 264 + 31) / 32 * 32 (the stride
- *               ql_state_device reports for a context of the same nx).
+ *               ql_state_device reports for a context of the same nx); rows
+ *               start 16-byte aligned, so in FP32 it must be even.
  *   The other arguments are those of ql_create; from opts only precision,
  *   pr_mode, enskog, device, pr_const, rho_ref and stream are used.
  * The two intermediate stage buffers and the error word live in one fixed

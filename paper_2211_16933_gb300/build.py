@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "libqlbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
-UNITS = ["qlbm_api.cu", "qlbm_batch.cu", "qlbm_noalloc.cu", "qlbm_host.cpp", "fdlb_f32.cu", "fdlb_f64.cu"]
+UNITS = ["qlbm_api.cu", "qlbm_batch.cu", "qlbm_noalloc.cu", "closure.cu", "qlbm_host.cpp", "fdlb_f32.cu", "fdlb_f64.cu"]
 
 
 def _deps():

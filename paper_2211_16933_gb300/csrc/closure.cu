@@ -1,0 +1,742 @@
+// Learned coarse-grid closure: a 1D convolutional network (5 layers, kernel 5,
+// 64 hidden channels, ReLU) that maps coarse-grid moment fields to a
+// correction of those fields.  Training and inference run in this file's
+// kernels: BF16 weights and activations, FP32 accumulation on the tensor cores
+// (mma.sync m16n8k16), FP32 master weights updated by Adam.
+//
+// Layout: activations are channels-last, act[b][x][c] (bf16), with channel
+// counts padded to multiples of 16; padded channels
+// hold zeros and their weights stay zero.  Weights of layer l are
+// W[co][j][ci] (tap j = 0..4 reads position x + j - 2).  Sample b is padded
+// periodically (periodic[b] != 0) or by replicating its end values.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qlbm.h"
+
+namespace {
+
+constexpr int kTaps = 5;
+constexpr int kTM = 64;  // positions per CTA tile
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ void mma16816(float *d, const uint32_t *a, const uint32_t *b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Padding of a position outside [0, X): periodic image, copy of the nearest end
+// value, or zero (the transposed convolution of the backward pass).
+enum { PAD_ZERO = 0, PAD_PERIODIC = 1, PAD_REPLICATE = 2 };
+__device__ __forceinline__ int wrap_pos(int p, int X, int mode, bool *inside)
+{
+    *inside = true;
+    if (p >= 0 && p < X) return p;
+    if (mode == PAD_PERIODIC) return ((p % X) + X) % X;
+    if (mode == PAD_REPLICATE) return p < 0 ? 0 : X - 1;
+    *inside = false;
+    return 0;
+}
+
+// Epilogues of the convolution kernel.
+enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
+
+// y[b][x][co] = sum_{j, ci} w[co][j][ci] in[b][x + j - 2][ci] (+ bias), then
+//   EPI_RELU_BF16: relu, stored bf16;  EPI_F32: stored f32;
+//   EPI_MASK_BF16: the transposed convolution of the backward pass: input
+//     positions outside the sample are zero; at the two end positions of a
+//     replicate-padded sample edge[b][side][co] is added (edge_grad_kernel);
+//     then times (mask[b][x][co] > 0), stored bf16 (ReLU backward).
+// One CTA: kTM positions of one sample, all COUT channels; 4 warps x 16 positions.
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w,
+                                                   const float *__restrict__ bias, const int *__restrict__ periodic,
+                                                   int X, void *__restrict__ out, const bf16 *__restrict__ mask,
+                                                   const float *__restrict__ edge)
+{
+    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "padded channels");
+    constexpr int WS = CIN + 8;  // smem row stride (bf16), avoids bank conflicts
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16 *win = reinterpret_cast<bf16 *>(smem);  // [kTM + 4][WS]
+    bf16 *ws = win + (kTM + 4) * WS;             // [COUT * 5][WS]
+    const int b = blockIdx.y, x0 = blockIdx.x * kTM, t = threadIdx.x;
+    const bool per = periodic[b] != 0;
+    const int mode = per ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
+    constexpr int VPR = CIN / 8;  // 16-byte vectors per row
+    for (int e = t; e < (kTM + 4) * VPR; e += blockDim.x) {
+        const int r = e / VPR, v = e % VPR;
+        bool inside;
+        const int p = wrap_pos(x0 - 2 + r, X, mode, &inside);
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (inside) val = *reinterpret_cast<const uint4 *>(in + (size_t(b) * X + p) * CIN + v * 8);
+        *reinterpret_cast<uint4 *>(win + r * WS + v * 8) = val;
+    }
+    for (int e = t; e < COUT * kTaps * VPR; e += blockDim.x) {
+        const int r = e / VPR, v = e % VPR;
+        *reinterpret_cast<uint4 *>(ws + r * WS + v * 8) = *reinterpret_cast<const uint4 *>(w + r * CIN + v * 8);
+    }
+    __syncthreads();
+
+    const int lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
+    const int m0 = warp * 16;
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kTaps; ++j) {
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            const int cb = kc * 16 + 2 * tg;
+            const bf16 *ra = win + (m0 + j + g) * WS + cb;
+            uint32_t a[4] = {ld32(ra), ld32(ra + 8 * WS), ld32(ra + 8), ld32(ra + 8 * WS + 8)};
+#pragma unroll
+            for (int n = 0; n < COUT / 8; ++n) {
+                const bf16 *rb = ws + ((n * 8 + g) * kTaps + j) * WS + cb;
+                uint32_t bb[2] = {ld32(rb), ld32(rb + 8)};
+                mma16816(acc[n], a, bb);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < COUT / 8; ++n) {
+        const int co = n * 8 + 2 * tg;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = x0 + m0 + g + 8 * h;
+            if (x >= X) continue;
+            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
+            const size_t o = (size_t(b) * X + x) * COUT + co;
+            if (EPI != EPI_MASK_BF16) {
+                v0 += bias[co];
+                v1 += bias[co + 1];
+            }
+            if (EPI == EPI_RELU_BF16) {
+                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) =
+                    __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+            } else if (EPI == EPI_F32) {
+                *reinterpret_cast<float2 *>(static_cast<float *>(out) + o) = make_float2(v0, v1);
+            } else {
+                if (!per && (x == 0 || x == X - 1)) {
+                    const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + co;
+                    v0 += eg[0];
+                    v1 += eg[1];
+                }
+                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + o);
+                v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+                v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// Weight and bias gradients of one layer:
+//   dW[co][j][ci] = sum_{b,x} dz[b][x][co] in[b][x + j - 2][ci],  db[co] = sum dz[b][x][co].
+// Each CTA accumulates over its share of the (sample, tile) pairs and writes a
+// partial; reduce_partials_kernel sums the partials in a fixed order.
+// 8 warps: warp (mw, nw) holds couts [16 mw, 16 mw + 16) and half of the
+// 5 CIN columns.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ in,
+                                                    const int *__restrict__ periodic, int X, int ntiles,
+                                                    float *__restrict__ partial)
+{
+    constexpr int N = kTaps * CIN;
+    constexpr int MT = (COUT + 15) / 16;  // m tiles (COUT = 8 pads to one)
+    constexpr int NT = N / 8;             // n tiles
+    constexpr int NW = 8 / MT;  // warps along N
+    constexpr int NTW = (NT + NW - 1) / NW;  // n tiles per warp
+    constexpr int PS = kTM + 8;              // smem row stride (positions)
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16 *gt = reinterpret_cast<bf16 *>(smem);  // [16 MT][PS]  dz transposed, rows >= COUT zero
+    bf16 *it0 = gt + 16 * MT * PS;              // [CIN][PS]    input window transposed
+    bf16 *it1 = it0 + CIN * PS;                 // [CIN][PS]    same, shifted by one position
+    float *dbs = reinterpret_cast<float *>(it1 + CIN * PS);  // [16 MT]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
+    const int mw = warp % MT, nw = warp / MT;
+    float acc[NTW][4];
+#pragma unroll
+    for (int n = 0; n < NTW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    float db = 0.f;
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
+        const int b = item / ((X + kTM - 1) / kTM), x0 = (item % ((X + kTM - 1) / kTM)) * kTM;
+        const int mode = periodic[b] != 0 ? PAD_PERIODIC : PAD_REPLICATE;
+        __syncthreads();
+        for (int e = t; e < 16 * MT * kTM; e += blockDim.x) {
+            const int p = e / (16 * MT), co = e % (16 * MT);
+            const int x = x0 + p;
+            bf16 v = __float2bfloat16(0.f);
+            if (co < COUT && x < X) v = dz[(size_t(b) * X + x) * COUT + co];
+            gt[co * PS + p] = v;
+        }
+        for (int e = t; e < (kTM + 5) * CIN; e += blockDim.x) {
+            const int p = e / CIN, ci = e % CIN;
+            bool inside;
+            const int x = wrap_pos(x0 - 2 + p, X, mode, &inside);
+            bf16 v = __float2bfloat16(0.f);
+            if (inside) v = in[(size_t(b) * X + x) * CIN + ci];
+            if (p < kTM + 4) it0[ci * PS + p] = v;
+            if (p >= 1) it1[ci * PS + p - 1] = v;
+        }
+        __syncthreads();
+        // bias gradient: thread t < 16 MT sums row t of dz^T
+        if (t < COUT) {
+            float s = 0.f;
+            for (int p = 0; p < kTM; ++p) s += __bfloat162float(gt[t * PS + p]);
+            db += s;
+        }
+#pragma unroll
+        for (int k0 = 0; k0 < kTM; k0 += 16) {
+            const bf16 *ra = gt + (16 * mw + g) * PS + k0 + 2 * tg;
+            uint32_t a[4] = {ld32(ra), ld32(ra + 8 * PS), ld32(ra + 8), ld32(ra + 8 * PS + 8)};
+#pragma unroll
+            for (int n = 0; n < NTW; ++n) {
+                const int nt = nw * NTW + n;
+                if (nt >= NT) break;
+                const int col = nt * 8 + g;
+                const int j = col / CIN, ci = col % CIN;
+                // B[k][n] = in[x0 + k0 + k + j - 2][ci] = window position k0 + k + j
+                const bf16 *src = (j & 1) ? it1 + ci * PS + k0 + 2 * tg + j - 1 : it0 + ci * PS + k0 + 2 * tg + j;
+                uint32_t bb[2] = {ld32(src), ld32(src + 8)};
+                mma16816(acc[n], a, bb);
+            }
+        }
+    }
+    // partial[cta][co][col] with col = j CIN + ci, then the bias partials
+    float *P = partial + size_t(blockIdx.x) * (COUT * N + COUT);
+#pragma unroll
+    for (int n = 0; n < NTW; ++n) {
+        const int nt = nw * NTW + n;
+        if (nt >= NT) break;
+        const int col = nt * 8 + 2 * tg;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = 16 * mw + g + 8 * h;
+            if (co < COUT) {
+                P[co * N + col] = acc[n][2 * h];
+                P[co * N + col + 1] = acc[n][2 * h + 1];
+            }
+        }
+    }
+    if (t < COUT) P[COUT * N + t] = db;
+    (void)dbs;
+}
+
+// Replicate padding feeds the end values a[0] and a[X-1] of a sample into the
+// taps that reach past its ends, so their gradients get terms the zero-padded
+// transposed convolution lacks:
+//   left  (x = 0):     sum_co (W0 + W1)[co][ci] dz[0][co] + W0[co][ci] dz[1][co]
+//   right (x = X - 1): sum_co (W3 + W4)[co][ci] dz[X-1][co] + W4[co][ci] dz[X-2][co]
+// w is the forward layer's W[co][j][ci]; one block per (sample, side), thread ci.
+__global__ void edge_grad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ w,
+                                 const int *__restrict__ periodic, int X, int cout, int cin, float *__restrict__ edge)
+{
+    const int b = blockIdx.x, side = blockIdx.y, ci = threadIdx.x;
+    if (ci >= cin) return;
+    float s = 0.f;
+    if (periodic[b] == 0) {
+        const bf16 *d0 = dz + (size_t(b) * X + (side ? X - 1 : 0)) * cout;
+        const bf16 *d1 = dz + (size_t(b) * X + (side ? X - 2 : 1)) * cout;
+        const int ja = side ? 3 : 0, jb = side ? 4 : 1, jn = side ? 4 : 0;
+        for (int co = 0; co < cout; ++co) {
+            const float wa = __bfloat162float(w[(co * kTaps + ja) * cin + ci]);
+            const float wb = __bfloat162float(w[(co * kTaps + jb) * cin + ci]);
+            const float wn = __bfloat162float(w[(co * kTaps + jn) * cin + ci]);
+            s = fmaf(wa + wb, __bfloat162float(d0[co]), s);
+            s = fmaf(wn, __bfloat162float(d1[co]), s);
+        }
+    }
+    edge[(size_t(b) * 2 + side) * cin + ci] = s;
+}
+
+// out[i] = sum_c partial[c][i] in a fixed order.
+__global__ void reduce_partials_kernel(const float *__restrict__ partial, int nparts, int len, float *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += partial[size_t(c) * len + i];
+    out[i] = s;
+}
+
+// Input features (f32 [B][X][cin_real]) -> normalised bf16 [B][X][CINP].
+__global__ void pack_input_kernel(const float *__restrict__ x, int64_t n, int cin, int cinp,
+                                  const float *__restrict__ shift, const float *__restrict__ inv_scale,
+                                  bf16 *__restrict__ out)
+{
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * cinp) return;
+    const int64_t pos = e / cinp;
+    const int c = int(e % cinp);
+    float v = 0.f;
+    if (c < cin) v = (x[pos * cin + c] - shift[c]) * inv_scale[c];
+    out[e] = __float2bfloat16(v);
+}
+
+// Mean squared error between prediction (f32 [B][X][COUTP], first cout used) and
+// target / out_scale; writes dL/dpred (bf16, padded channels zero) and
+// per-block partial sums of the squared error.
+__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ y, int64_t npos, int cout,
+                           int coutp, const float *__restrict__ inv_out_scale, float grad_scale,
+                           bf16 *__restrict__ dpred, float *__restrict__ partial)
+{
+    __shared__ float red[256];
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    float se = 0.f;
+    if (e < npos * coutp) {
+        const int64_t pos = e / coutp;
+        const int c = int(e % coutp);
+        float d = 0.f;
+        if (c < cout) {
+            d = pred[e] - y[pos * cout + c] * inv_out_scale[c];
+            se = d * d;
+        }
+        dpred[e] = __float2bfloat16(grad_scale * d);
+    }
+    red[threadIdx.x] = se;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Prediction in physical units: y[pos][c] = pred[pos][c] * out_scale[c], c < cout.
+__global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npos, int cout, int coutp,
+                                     const float *__restrict__ out_scale, float *__restrict__ y)
+{
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= npos * cout) return;
+    const int64_t pos = e / cout;
+    const int c = int(e % cout);
+    y[e] = pred[pos * coutp + c] * out_scale[c];
+}
+
+// Adam on FP32 master parameters; refreshes the bf16 weight copies, the
+// tap-flipped transposed copies used by the backward pass, and the f32 biases.
+struct AdamArgs {
+    float *param, *m, *v;
+    const float *grad;
+    int64_t n;
+    float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+};
+__global__ void adam_kernel(AdamArgs a)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float g = a.grad[i];
+    const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+    const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+    a.m[i] = m;
+    a.v[i] = v;
+    a.param[i] -= a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+}
+
+// bf16 copies of one layer's weights: w[co][j][ci] and wt[ci][4 - j][co].
+__global__ void cast_weights_kernel(const float *__restrict__ wf, int cout, int cin, bf16 *__restrict__ w,
+                                    bf16 *__restrict__ wt)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cout * kTaps * cin) return;
+    const int co = e / (kTaps * cin), j = (e / cin) % kTaps, ci = e % cin;
+    const bf16 v = __float2bfloat16(wf[e]);
+    w[e] = v;
+    wt[(ci * kTaps + (kTaps - 1 - j)) * cout + co] = v;
+}
+
+// ---------------------------------------------------------------------------
+struct Layer {
+    int cin, cout;    // padded
+    int cin_real, cout_real;
+    int64_t woff, boff;  // offsets of W [cout][5][cin] and bias [cout] in the f32 parameter vector
+};
+
+template <int CIN, int COUT, int EPI>
+cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const int *per, int B, int X, void *out,
+                        const bf16 *mask, const float *edge, cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(bf16) * ((kTM + 4) * (CIN + 8) + COUT * kTaps * (CIN + 8));
+    auto k = conv_kernel<CIN, COUT, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k<<<dim3((X + kTM - 1) / kTM, B), 128, smem, s>>>(in, w, bias, per, X, out, mask, edge);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_any(int cin, int cout, int epi, const bf16 *in, const bf16 *w, const float *bias, const int *per,
+                     int B, int X, void *out, const bf16 *mask, const float *edge, cudaStream_t s)
+{
+#define QC(CI, CO, EP)                                                                 \
+    if (cin == CI && cout == CO && epi == EP)                                          \
+        return conv_launch<CI, CO, EP>(in, w, bias, per, B, X, out, mask, edge, s);
+    QC(16, 64, EPI_RELU_BF16)
+    QC(64, 64, EPI_RELU_BF16)
+    QC(64, 16, EPI_F32)
+    QC(16, 64, EPI_MASK_BF16)
+    QC(64, 64, EPI_MASK_BF16)
+#undef QC
+    return cudaErrorInvalidValue;
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad_launch(const bf16 *dz, const bf16 *in, const int *per, int B, int X, int grid, float *partial,
+                         cudaStream_t s)
+{
+    constexpr int MT = (COUT + 15) / 16;
+    constexpr int PS = kTM + 8;
+    constexpr size_t smem = sizeof(bf16) * (16 * MT * PS + 2 * CIN * PS) + sizeof(float) * 16 * MT;
+    auto k = wgrad_kernel<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    const int ntiles = B * ((X + kTM - 1) / kTM);
+    k<<<grid, 256, smem, s>>>(dz, in, per, X, ntiles, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_any(int cin, int cout, const bf16 *dz, const bf16 *in, const int *per, int B, int X, int grid,
+                      float *partial, cudaStream_t s)
+{
+    if (cin == 16 && cout == 64) return wgrad_launch<16, 64>(dz, in, per, B, X, grid, partial, s);
+    if (cin == 64 && cout == 64) return wgrad_launch<64, 64>(dz, in, per, B, X, grid, partial, s);
+    if (cin == 64 && cout == 16) return wgrad_launch<64, 16>(dz, in, per, B, X, grid, partial, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct ql_closure {
+    ql_closure_desc d;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ql_alloc_fn alloc = nullptr;
+    ql_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<Layer> layers;
+    int64_t nparam = 0;
+    float *param = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    bf16 *w16 = nullptr, *wt16 = nullptr;  // per layer at woff
+    std::vector<bf16 *> act;  // act[0] input (bf16), act[l] output of layer l (l < L)
+    float *pred = nullptr;    // last layer output f32 [B][X][16]
+    std::vector<bf16 *> dz;   // dz[l]: gradient wrt pre-activation of layer l (1-based), stored bf16
+    float *partial = nullptr;
+    float *loss_partial = nullptr;
+    float *edge = nullptr;  // [max_batch][2][64] end-position gradient terms of replicate padding
+    float *norm = nullptr;  // in_shift[8], in_inv_scale[8], out_scale[8], inv_out_scale[8]
+    int wgrid = 0;
+    int64_t step = 0;
+    std::string err;
+};
+
+static std::string g_closure_error;
+
+static ql_status cfail(ql_closure *c, ql_status st, const std::string &m)
+{
+    if (c) c->err = m; else g_closure_error = m;
+    return st;
+}
+
+static void *calloc_dev(ql_closure *c, size_t bytes)
+{
+    if (c->alloc) return c->alloc(bytes, c->alloc_user);
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+
+static void cfree_dev(ql_closure *c, void *p)
+{
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, c->alloc_user);
+    else cudaFree(p);
+}
+
+static void closure_release(ql_closure *c)
+{
+    for (void *p : {(void *)c->param, (void *)c->grad, (void *)c->m, (void *)c->v, (void *)c->w16, (void *)c->wt16,
+                    (void *)c->pred, (void *)c->partial, (void *)c->loss_partial, (void *)c->edge,
+                    (void *)c->norm})
+        cfree_dev(c, p);
+    for (bf16 *p : c->act) cfree_dev(c, p);
+    for (bf16 *p : c->dz) cfree_dev(c, p);
+}
+
+#define QC_CUDA(c, call)                                                                               \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return cfail(c, QL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static ql_status refresh_weights(ql_closure *c)
+{
+    for (const Layer &L : c->layers) {
+        const int n = L.cout * kTaps * L.cin;
+        cast_weights_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->param + L.woff, L.cout, L.cin, c->w16 + L.woff,
+                                                                    c->wt16 + L.woff);
+    }
+    QC_CUDA(c, cudaGetLastError());
+    return QL_OK;
+}
+
+// splitmix64, for seeded He-uniform initial weights
+static uint64_t splitmix(uint64_t &s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Forward pass of B samples already packed in act[0]; leaves pred.
+static ql_status forward(ql_closure *c, const int *per, int B)
+{
+    const int X = c->d.positions, nl = int(c->layers.size());
+    for (int l = 0; l < nl; ++l) {
+        const Layer &L = c->layers[l];
+        const bool last = l == nl - 1;
+        void *out = last ? static_cast<void *>(c->pred) : static_cast<void *>(c->act[l + 1]);
+        QC_CUDA(c, conv_any(L.cin, L.cout, last ? EPI_F32 : EPI_RELU_BF16, c->act[l], c->w16 + L.woff,
+                            c->param + L.boff, per, B, X, out, nullptr, nullptr, c->stream));
+    }
+    return QL_OK;
+}
+
+static ql_status pack(ql_closure *c, const float *x, int B)
+{
+    const int64_t npos = int64_t(B) * c->d.positions;
+    const int cinp = c->layers[0].cin;
+    pack_input_kernel<<<unsigned((npos * cinp + 255) / 256), 256, 0, c->stream>>>(
+        x, npos, c->d.in_channels, cinp, c->norm, c->norm + 8, c->act[0]);
+    QC_CUDA(c, cudaGetLastError());
+    return QL_OK;
+}
+
+// Loss, gradients of all parameters into c->grad; loss (host) if not null.
+static ql_status backward(ql_closure *c, const float *y, const int *per, int B, float *loss)
+{
+    const int X = c->d.positions, nl = int(c->layers.size());
+    const int64_t npos = int64_t(B) * X;
+    const int coutp = c->layers[nl - 1].cout;
+    const int64_t nel = npos * coutp;
+    const unsigned nb = unsigned((nel + 255) / 256);
+    const float gscale = 2.f / float(npos * c->d.out_channels);
+    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, npos, c->d.out_channels, coutp, c->norm + 24, gscale,
+                                          c->dz[nl - 1], c->loss_partial);
+    QC_CUDA(c, cudaGetLastError());
+    for (int l = nl - 1; l >= 0; --l) {
+        const Layer &L = c->layers[l];
+        const int len = L.cout * kTaps * L.cin + L.cout;
+        QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->wgrid, c->partial, c->stream));
+        // partial layout per CTA: [cout][5 cin] then [cout]; W and b are contiguous in the parameter vector
+        reduce_partials_kernel<<<(len + 255) / 256, 256, 0, c->stream>>>(c->partial, c->wgrid, len, c->grad + L.woff);
+        QC_CUDA(c, cudaGetLastError());
+        if (l > 0) {
+            // dz[l-1] = (W^T * dz[l] + end terms of replicate padding) masked by act[l] > 0
+            // (act[l] is the output of layer l-1)
+            edge_grad_kernel<<<dim3(B, 2), L.cin, 0, c->stream>>>(c->dz[l], c->w16 + L.woff, per, X, L.cout, L.cin,
+                                                                 c->edge);
+            QC_CUDA(c, cudaGetLastError());
+            QC_CUDA(c, conv_any(L.cout, L.cin, EPI_MASK_BF16, c->dz[l], c->wt16 + L.woff, nullptr, per, B, X,
+                                c->dz[l - 1], c->act[l], c->edge, c->stream));
+        }
+    }
+    if (loss) {
+        std::vector<float> h(nb);
+        QC_CUDA(c, cudaMemcpyAsync(h.data(), c->loss_partial, sizeof(float) * nb, cudaMemcpyDeviceToHost, c->stream));
+        QC_CUDA(c, cudaStreamSynchronize(c->stream));
+        double s = 0;
+        for (float v : h) s += v;
+        *loss = float(s / double(npos * c->d.out_channels));
+    }
+    return QL_OK;
+}
+
+extern "C" {
+
+ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_closure **out)
+{
+    if (out) *out = nullptr;
+    if (!d || !opts || !out) return cfail(nullptr, QL_EINVAL, "null argument");
+    if (d->ksize != kTaps || d->layers < 2 || d->width != 64 || d->in_channels < 1 || d->in_channels > 8 ||
+        d->out_channels < 1 || d->out_channels > 8 || d->positions < 16 || d->max_batch < 1)
+        return cfail(nullptr, QL_EUNSUPPORTED,
+                     "supported: ksize 5, width 64, >= 2 layers, 1..8 inputs, 1..8 outputs, >= 16 positions");
+    ql_closure *c = new ql_closure();
+    c->d = *d;
+    c->device = opts->device;
+    c->alloc = opts->alloc;
+    c->free_fn = opts->free;
+    c->alloc_user = opts->alloc_user;
+    c->stream = static_cast<cudaStream_t>(opts->stream);
+    auto bail = [&](ql_status st, const std::string &m) {
+        closure_release(c);
+        delete c;
+        return cfail(nullptr, st, m);
+    };
+    if (cudaSetDevice(c->device) != cudaSuccess) return bail(QL_ECUDA, "cudaSetDevice failed");
+    int64_t off = 0;
+    for (int l = 0; l < d->layers; ++l) {
+        Layer L;
+        L.cin_real = l == 0 ? d->in_channels : 64;
+        L.cout_real = l == d->layers - 1 ? d->out_channels : 64;
+        L.cin = l == 0 ? 16 : 64;
+        L.cout = l == d->layers - 1 ? 16 : 64;
+        L.woff = off;
+        off += int64_t(L.cout) * kTaps * L.cin;
+        L.boff = off;
+        off += L.cout;
+        c->layers.push_back(L);
+    }
+    c->nparam = off;
+    const int X = d->positions, B = d->max_batch;
+    const int64_t npos = int64_t(B) * X;
+    c->param = static_cast<float *>(calloc_dev(c, sizeof(float) * off));
+    c->grad = static_cast<float *>(calloc_dev(c, sizeof(float) * off));
+    c->m = static_cast<float *>(calloc_dev(c, sizeof(float) * off));
+    c->v = static_cast<float *>(calloc_dev(c, sizeof(float) * off));
+    c->w16 = static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * off));
+    c->wt16 = static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * off));
+    c->pred = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * 16));
+    c->norm = static_cast<float *>(calloc_dev(c, sizeof(float) * 32));
+    for (int l = 0; l < d->layers; ++l) {
+        c->act.push_back(static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * npos * c->layers[l].cin)));
+        c->dz.push_back(static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * npos * c->layers[l].cout)));
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->wgrid = sms > 0 ? 2 * sms : 256;
+    c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(c->wgrid) * (64 * kTaps * 64 + 64)));
+    c->loss_partial = static_cast<float *>(calloc_dev(c, sizeof(float) * ((npos * 16 + 255) / 256)));
+    c->edge = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(B) * 2 * 64));
+    bool ok = c->param && c->grad && c->m && c->v && c->w16 && c->wt16 && c->pred && c->norm && c->partial &&
+              c->loss_partial && c->edge;
+    for (int l = 0; l < d->layers; ++l) ok = ok && c->act[l] && c->dz[l];
+    if (!ok) return bail(QL_ENOMEM, "closure allocation failed");
+
+    // seeded He-uniform weights (real channels only), zero biases and padding
+    std::vector<float> h(off, 0.f);
+    uint64_t s = d->seed;
+    for (size_t l = 0; l < c->layers.size(); ++l) {
+        const Layer &L = c->layers[l];
+        const float a = sqrtf(6.f / float(kTaps * L.cin_real)) * (l + 1 == c->layers.size() ? 0.1f : 1.f);
+        for (int co = 0; co < L.cout_real; ++co)
+            for (int j = 0; j < kTaps; ++j)
+                for (int ci = 0; ci < L.cin_real; ++ci) {
+                    const double u = double(splitmix(s) >> 11) * (1.0 / 9007199254740992.0);
+                    h[L.woff + (int64_t(co) * kTaps + j) * L.cin + ci] = float((2.0 * u - 1.0) * a);
+                }
+    }
+    float nrm[32];
+    for (int i = 0; i < 8; ++i) {
+        nrm[i] = d->in_shift[i];
+        nrm[8 + i] = d->in_scale[i] != 0.f ? 1.f / d->in_scale[i] : 1.f;
+        nrm[16 + i] = d->out_scale[i] != 0.f ? d->out_scale[i] : 1.f;
+        nrm[24 + i] = 1.f / nrm[16 + i];
+    }
+    cudaError_t e = cudaMemcpyAsync(c->param, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->m, 0, sizeof(float) * off, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->v, 0, sizeof(float) * off, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->norm, nrm, sizeof(nrm), cudaMemcpyHostToDevice, c->stream);
+    for (int l = 0; l < d->layers && e == cudaSuccess; ++l) {
+        e = cudaMemsetAsync(c->act[l], 0, sizeof(bf16) * npos * c->layers[l].cin, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->dz[l], 0, sizeof(bf16) * npos * c->layers[l].cout, c->stream);
+    }
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("closure set-up: ") + cudaGetErrorString(e));
+    if (refresh_weights(c) != QL_OK) return bail(QL_ECUDA, c->err);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(QL_ECUDA, "closure set-up sync failed");
+    *out = c;
+    return QL_OK;
+}
+
+ql_status ql_closure_forward(ql_closure *c, const float *x, const int32_t *periodic, int64_t B, float *y)
+{
+    if (!c || !x || !periodic || !y || B < 1 || B > c->d.max_batch) return cfail(c, QL_EINVAL, "bad arguments");
+    ql_status st = pack(c, x, int(B));
+    if (st == QL_OK) st = forward(c, periodic, int(B));
+    if (st != QL_OK) return st;
+    const int64_t npos = B * c->d.positions;
+    unpack_output_kernel<<<unsigned((npos * c->d.out_channels + 255) / 256), 256, 0, c->stream>>>(
+        c->pred, npos, c->d.out_channels, c->layers.back().cout, c->norm + 16, y);
+    QC_CUDA(c, cudaGetLastError());
+    return QL_OK;
+}
+
+ql_status ql_closure_gradients(ql_closure *c, const float *x, const float *y, const int32_t *periodic, int64_t B,
+                               float *loss, float *grad_host)
+{
+    if (!c || !x || !y || !periodic || B < 1 || B > c->d.max_batch) return cfail(c, QL_EINVAL, "bad arguments");
+    ql_status st = pack(c, x, int(B));
+    if (st == QL_OK) st = forward(c, periodic, int(B));
+    if (st == QL_OK) st = backward(c, y, periodic, int(B), loss);
+    if (st != QL_OK) return st;
+    if (grad_host) {
+        QC_CUDA(c, cudaMemcpyAsync(grad_host, c->grad, sizeof(float) * c->nparam, cudaMemcpyDeviceToHost, c->stream));
+        QC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return QL_OK;
+}
+
+ql_status ql_closure_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic, int64_t B,
+                                float lr, float *loss)
+{
+    ql_status st = ql_closure_gradients(c, x, y, periodic, B, loss, nullptr);
+    if (st != QL_OK) return st;
+    c->step += 1;
+    AdamArgs a;
+    a.param = c->param;
+    a.m = c->m;
+    a.v = c->v;
+    a.grad = c->grad;
+    a.n = c->nparam;
+    a.lr = lr;
+    a.b1 = 0.9f;
+    a.b2 = 0.999f;
+    a.eps = 1e-8f;
+    a.c1 = float(1.0 / (1.0 - pow(0.9, double(c->step))));
+    a.c2 = float(1.0 / (1.0 - pow(0.999, double(c->step))));
+    adam_kernel<<<unsigned((c->nparam + 255) / 256), 256, 0, c->stream>>>(a);
+    QC_CUDA(c, cudaGetLastError());
+    return refresh_weights(c);
+}
+
+ql_status ql_closure_params(ql_closure *c, float *get_host, const float *set_host, int64_t *count)
+{
+    if (!c) return cfail(c, QL_EINVAL, "null closure");
+    if (count) *count = c->nparam;
+    if (get_host) {
+        QC_CUDA(c, cudaMemcpyAsync(get_host, c->param, sizeof(float) * c->nparam, cudaMemcpyDeviceToHost, c->stream));
+        QC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (set_host) {
+        QC_CUDA(c, cudaMemcpyAsync(c->param, set_host, sizeof(float) * c->nparam, cudaMemcpyHostToDevice, c->stream));
+        ql_status st = refresh_weights(c);
+        if (st != QL_OK) return st;
+        QC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return QL_OK;
+}
+
+ql_status ql_closure_destroy(ql_closure *c)
+{
+    if (!c) return QL_OK;
+    cudaStreamSynchronize(c->stream);
+    closure_release(c);
+    delete c;
+    return QL_OK;
+}
+
+const char *ql_closure_last_error(const ql_closure *c) { return c ? c->err.c_str() : g_closure_error.c_str(); }
+
+}  // extern "C"

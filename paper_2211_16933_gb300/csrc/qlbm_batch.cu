@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -100,6 +101,52 @@ static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
     a.err = b->d_err;
     return b->precision == QL_FP32 ? launch_batch_stage_f32(stage, warps, grid, a, b->stream)
                                    : launch_batch_stage_f64(stage, warps, grid, a, b->stream);
+}
+
+// Fields of every instance averaged over blocks of nx/ncoarse cells:
+// out[(i * 5 + f) * ncoarse + c] for f = rho, u, T, q, Pxx.  One thread per
+// (instance, coarse cell); moments per fine cell in FP64 (Sec. II.D).
+template <typename Real>
+__global__ void batch_fields_kernel(const BatchInstance *__restrict__ inst, const void *__restrict__ arena,
+                                    const double *__restrict__ tab, int ncoarse, double *__restrict__ out)
+{
+    using V = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+    const int i = blockIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncoarse) return;
+    const BatchInstance I = inst[i];
+    const int Q = I.Q;
+    int p_off = 0;
+    switch (Q) {
+    case 8: p_off = tab_view(8).p; break;
+    case 16: p_off = tab_view(16).p; break;
+    case 24: p_off = tab_view(24).p; break;
+    default: p_off = tab_view(32).p; break;
+    }
+    const V *psi = static_cast<const V *>(arena) + I.off;
+    const int64_t f = I.nx / ncoarse;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int64_t j = 0; j < f; ++j) {
+        const int64_t cell = int64_t(c) * f + j;
+        double S0 = 0, S1 = 0, S2 = 0, S3 = 0, R0 = 0, R1 = 0;
+        for (int k = 0; k < Q; ++k) {
+            const V v = psi[int64_t(k) * I.stride + kHalo + cell];
+            const double ph = double(v.x), th = double(v.y), p = tab[p_off + k];
+            S0 += ph;
+            S1 += p * ph;
+            S2 += p * p * ph;
+            S3 += p * p * p * ph;
+            R0 += th;
+            R1 += p * th;
+        }
+        const double n = S0, u = S1 / n, c2 = S2 - u * S1;
+        acc[0] += n;
+        acc[1] += u;
+        acc[2] += (c2 + R0) / (3.0 * n);
+        acc[3] += 0.5 * (S3 - 3.0 * u * S2 + 2.0 * u * u * S1 + R1 - u * R0);
+        acc[4] += c2;
+    }
+    for (int q = 0; q < 5; ++q) out[(int64_t(i) * 5 + q) * ncoarse + c] = acc[q] / double(f);
 }
 
 static int ctas_per_sm(ql_batch *b, int warps)
@@ -366,6 +413,21 @@ ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, doubl
     QB_CUDA(b, cudaMemcpyAsync(&h, b->d_err + i, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
     QB_CUDA(b, cudaStreamSynchronize(b->stream));
     if (h & 1u) return bfail(b, QL_ENONPHYSICAL, "non-physical state in instance " + std::to_string(i));
+    return QL_OK;
+}
+
+ql_status ql_batch_fields(ql_batch *b, int32_t ncoarse, double *out)
+{
+    if (!b || ncoarse < 1 || !out) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_fields");
+    for (int64_t i = 0; i < b->n; ++i)
+        if (b->inst[i].nx % ncoarse != 0)
+            return bfail(b, QL_EINVAL, "ncoarse must divide nx of every instance (instance " + std::to_string(i) + ")");
+    const dim3 grid(unsigned((ncoarse + 127) / 128), unsigned(b->n));
+    if (b->precision == QL_FP32)
+        batch_fields_kernel<float><<<grid, 128, 0, b->stream>>>(b->d_inst, b->arena[0], b->d_tab64, ncoarse, out);
+    else
+        batch_fields_kernel<double><<<grid, 128, 0, b->stream>>>(b->d_inst, b->arena[0], b->d_tab64, ncoarse, out);
+    QB_CUDA(b, cudaGetLastError());
     return QL_OK;
 }
 

@@ -25,7 +25,9 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",
             "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error",
             "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
-            "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc")
+            "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc",
+            "ql_batch_fields", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
+            "ql_closure_train_step", "ql_closure_params", "ql_closure_destroy", "ql_closure_last_error")
 
 
 class QLError(RuntimeError):
@@ -68,6 +70,13 @@ class ql_instance(C.Structure):
     _fields_ = [("vs", ql_velset), ("grid", ql_grid), ("denseness", C.c_double), ("kn", C.c_double),
                 ("bc", ql_bc), ("init", ql_init), ("pr_mode", C.c_int32), ("enskog", C.c_int32),
                 ("pr_const", C.c_double), ("rho_ref", C.c_double)]
+
+
+class ql_closure_desc(C.Structure):
+    _fields_ = [("in_channels", C.c_int32), ("out_channels", C.c_int32), ("width", C.c_int32),
+                ("layers", C.c_int32), ("ksize", C.c_int32), ("positions", C.c_int32), ("max_batch", C.c_int32),
+                ("pad_", C.c_int32), ("seed", C.c_uint64), ("in_shift", C.c_float * 8), ("in_scale", C.c_float * 8),
+                ("out_scale", C.c_float * 8)]
 
 
 _lib = None
@@ -113,6 +122,16 @@ def lib():
         L.ql_batch_last_error.restype = C.c_char_p
         L.ql_step_noalloc.argtypes = [C.POINTER(ql_velset), C.POINTER(ql_grid), C.c_double, C.c_double,
                                       C.POINTER(ql_bc), C.POINTER(ql_opts), V, C.c_int64, C.c_int64]
+        L.ql_batch_fields.argtypes = [V, C.c_int32, V]
+        F = C.POINTER(C.c_float)
+        L.ql_closure_create.argtypes = [C.POINTER(ql_closure_desc), C.POINTER(ql_opts), C.POINTER(V)]
+        L.ql_closure_forward.argtypes = [V, V, V, C.c_int64, V]
+        L.ql_closure_gradients.argtypes = [V, V, V, V, C.c_int64, F, F]
+        L.ql_closure_train_step.argtypes = [V, V, V, V, C.c_int64, C.c_float, F]
+        L.ql_closure_params.argtypes = [V, F, F, C.POINTER(C.c_int64)]
+        L.ql_closure_destroy.argtypes = [V]
+        L.ql_closure_last_error.argtypes = [V]
+        L.ql_closure_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -263,6 +282,10 @@ def ql_batch_destroy(b):
     _bcheck(lib().ql_batch_destroy(b))
 
 
+def ql_batch_fields(b, ncoarse, out_ptr):
+    _bcheck(lib().ql_batch_fields(b, ncoarse, C.c_void_p(out_ptr)), b)
+
+
 def make_instance(Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND, prm=(),
                   pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, keep=None, rho=None, u=None, T=None,
                   ghost=None):
@@ -331,10 +354,88 @@ class Batch:
     def info(self):
         return ql_batch_info(self.b)
 
+    def fields(self, ncoarse, out):
+        """out: a device tensor of n * 5 * ncoarse float64 (its data pointer is passed)."""
+        ql_batch_fields(self.b, ncoarse, out.data_ptr())
+
     def close(self):
         if getattr(self, "b", None) is not None:
             ql_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- learned closure
+def _ccheck(st, c=None):
+    if st != QL_OK:
+        msg = lib().ql_closure_last_error(c)
+        raise QLError(st, msg.decode() if msg else "")
+
+
+class Closure:
+    """The learned coarse-grid closure network; device tensors are passed by data pointer."""
+
+    def __init__(self, in_channels, out_channels, positions, max_batch, seed=0, in_shift=None, in_scale=None,
+                 out_scale=None, layers=5, width=64, device=0):
+        import torch
+        d = ql_closure_desc()
+        d.in_channels, d.out_channels, d.width, d.layers, d.ksize = in_channels, out_channels, width, layers, 5
+        d.positions, d.max_batch, d.seed = positions, max_batch, seed
+        for i in range(8):
+            d.in_shift[i] = float(in_shift[i]) if in_shift is not None and i < len(in_shift) else 0.0
+            d.in_scale[i] = float(in_scale[i]) if in_scale is not None and i < len(in_scale) else 1.0
+            d.out_scale[i] = float(out_scale[i]) if out_scale is not None and i < len(out_scale) else 1.0
+        o = ql_opts()
+        o.device = device
+        self._stream = torch.cuda.current_stream(device)
+        o.stream = C.c_void_p(self._stream.cuda_stream)
+        self.c = C.c_void_p()
+        _ccheck(lib().ql_closure_create(C.byref(d), C.byref(o), C.byref(self.c)))
+        self.in_channels, self.out_channels, self.positions = in_channels, out_channels, positions
+
+    def forward(self, x, periodic, y):
+        _ccheck(lib().ql_closure_forward(self.c, C.c_void_p(x.data_ptr()), C.c_void_p(periodic.data_ptr()),
+                                         x.shape[0], C.c_void_p(y.data_ptr())), self.c)
+
+    def gradients(self, x, y, periodic):
+        n = self.nparams()
+        g = np.zeros(n, dtype=np.float32)
+        loss = C.c_float()
+        _ccheck(lib().ql_closure_gradients(self.c, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                           C.c_void_p(periodic.data_ptr()), x.shape[0], C.byref(loss),
+                                           g.ctypes.data_as(C.POINTER(C.c_float))), self.c)
+        return loss.value, g
+
+    def train_step(self, x, y, periodic, lr, want_loss=False):
+        loss = C.c_float()
+        _ccheck(lib().ql_closure_train_step(self.c, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                            C.c_void_p(periodic.data_ptr()), x.shape[0], lr,
+                                            C.byref(loss) if want_loss else None), self.c)
+        return loss.value if want_loss else None
+
+    def nparams(self):
+        n = C.c_int64()
+        _ccheck(lib().ql_closure_params(self.c, None, None, C.byref(n)), self.c)
+        return n.value
+
+    def get_params(self):
+        p = np.zeros(self.nparams(), dtype=np.float32)
+        _ccheck(lib().ql_closure_params(self.c, p.ctypes.data_as(C.POINTER(C.c_float)), None, None), self.c)
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _ccheck(lib().ql_closure_params(self.c, None, p.ctypes.data_as(C.POINTER(C.c_float)), None), self.c)
+
+    def close(self):
+        if getattr(self, "c", None) is not None and self.c:
+            lib().ql_closure_destroy(self.c)
+            self.c = None
 
     def __del__(self):
         try:
