@@ -1,5 +1,5 @@
 // FP32 kernels: state, fluxes and update in FP32; per-cell conserved-moment
-// sums and domain totals in FP64.
+// sums combined in double-FP32, domain totals in FP64.
 #include "qlbm_internal.h"
 namespace qlbm {
 static __constant__ float QL_TAB[kTabTotal];

@@ -106,7 +106,7 @@ int QL_FN(batch_ctas_per_sm_)(int stage, int warps)
 cudaError_t QL_FN(launch_init_)(int Q, const double *rho, const double *u, const double *T, void *psi,
                                 int64_t nx, int64_t stride, const double *tab64, cudaStream_t s)
 {
-    const int64_t n = (nx + 2 * kHalo) * Q;
+    const int64_t n = nx + 2 * kHalo;  // one thread per column
     const unsigned blocks = unsigned((n + 255) / 256);
     P2<QL_REAL> *p = static_cast<P2<QL_REAL> *>(psi);
     switch (Q) {

@@ -92,6 +92,54 @@ __device__ __forceinline__ double pow2_recip_(double x)
 }
 
 // ---------------------------------------------------------------------------
+// Double-FP32 arithmetic: a value held as the unevaluated sum h + l of two
+// floats, |l| <= ulp(h)/2 after normalisation, about 48 significant bits.
+// two_sum is Knuth's error-free sum (no ordering needed), fast_two_sum Dekker's
+// (|a| >= |b|), and products are made exact with one fma (Dekker/Knuth
+// error-free transformations; the build never contracts a * b + c by itself).
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const FF s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p);
+    return fast_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+__device__ __forceinline__ FF ff_mul_f(FF a, float b)
+{
+    const float p = a.h * b;
+    return fast_two_sum(p, fmaf(a.l, b, fmaf(a.h, b, -p)));
+}
+// a / b: one quotient digit from an approximate reciprocal, then the exact
+// remainder a - q b gives the correction digit.
+__device__ __forceinline__ FF ff_div(FF a, FF b)
+{
+    const float r = __fdividef(1.0f, b.h);
+    const float q = a.h * r;
+    const float p = q * b.h;
+    const float pe = fmaf(q, b.h, -p);
+    const float rem = ((a.h - p) - pe) + fmaf(-q, b.l, a.l);
+    return fast_two_sum(q, rem * r);
+}
+
+// ---------------------------------------------------------------------------
 // WENO-5 value at the interface i+1/2 for a positive advection velocity
 // (App. A.2), from f_{i-2..i+2}, for both components of the pairs.  Weights
 // are delta_q / beta_q^2 normalised, with no epsilon, evaluated in the product
@@ -143,6 +191,19 @@ __device__ __forceinline__ P2<Real> weno5_face2(P2<Real> fm2, P2<Real> fm1, P2<R
     return fma2(num, rD, f0);
 }
 
+// Asks the TMA unit to bring `bytes` (a multiple of 16, 16-byte aligned
+// address) of global memory into L2; no data reach the SM and nothing waits.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Velocity pairs ahead of the current one whose psi^n rows stages 2 and 3
+// prefetch into L2.
+#ifndef QL_PSIN_PREFETCH_AHEAD
+#define QL_PSIN_PREFETCH_AHEAD 1
+#endif
+
 // Sixth-order central difference of App. A.3 (times dx), centred on s.
 template <typename Real>
 __device__ __forceinline__ Real cd6_(const Real *v, int s)
@@ -165,6 +226,12 @@ constexpr size_t stage_smem_bytes()
     constexpr int SEG = TileShape<WARPS>::seg;
     return sizeof(P2<Real>) * size_t(Q) * SEG + sizeof(Real) * (size_t(Q / 2) * Q + 6 * size_t(SEG));
 }
+
+// 1: the FP32 mode combines its per-cell conserved sums in FP64 instead of
+// double-FP32 (same accuracy, slower on this GPU).
+#ifndef QL_F32_SUMS_FP64
+#define QL_F32_SUMS_FP64 0
+#endif
 
 // Resident CTAs per SM the FP32 stage kernels are compiled for (8-warp tiles;
 // the register budget follows from it).
@@ -214,11 +281,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     __syncthreads();
 
     // 2. Moments of staged cell c (cell i0 - kHalo + c), Sec. II.D, from raw
-    //    sums over velocity pairs.  Mass, momentum and energy sums go to FP64
-    //    every 8 pairs; the heat-flux sums stay in the working precision.
+    //    sums over velocity pairs.  FP64 mode sums in FP64.  FP32 mode sums
+    //    groups of 8 pairs in FP32, combines the groups' mass, momentum and
+    //    energy sums and derives u and T in double-FP32 arithmetic (FP64 runs at
+    //    a small fraction of the FP32 rate on this GPU); the heat-flux sums stay
+    //    in FP32.
     for (int c = t; c < SEG; c += THREADS) {
         constexpr int GRP = sizeof(Real) == 8 ? H : 8;
+        constexpr bool kFF = sizeof(Real) == 4 && !QL_F32_SUMS_FP64;
         double M0 = 0, M1 = 0, ME = 0;
+        FF F0{0.f, 0.f}, F1{0.f, 0.f}, FE{0.f, 0.f};
         Real tS2 = 0, tS3 = 0, tR0 = 0, tR1 = 0;
 #pragma unroll
         for (int g = 0; g < H; g += GRP) {
@@ -234,25 +306,46 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
                 s2 = fma(QL_TAB[TV.p2 + H + j], sm.x, s2);
                 s3 = fma(QL_TAB[TV.p3 + H + j], df.x, s3);
             }
-            M0 += double(s01.x);
-            M1 += double(s11.x);
-            ME += double(s2 + s01.y);
+            if constexpr (kFF) {
+                // error-free accumulation: h takes the rounded sum, l its errors
+                const FF a0 = two_sum(F0.h, float(s01.x)), a1 = two_sum(F1.h, float(s11.x));
+                const FF a2 = two_sum(FE.h, float(s2)), a3 = two_sum(a2.h, float(s01.y));
+                F0 = {a0.h, F0.l + a0.l};
+                F1 = {a1.h, F1.l + a1.l};
+                FE = {a3.h, FE.l + (a2.l + a3.l)};
+            } else {
+                M0 += double(s01.x);
+                M1 += double(s11.x);
+                ME += double(s2 + s01.y);
+            }
             tS2 += s2;
             tS3 += s3;
             tR0 += s01.y;
             tR1 += s11.y;
         }
-        // 1/n from a working-precision reciprocal refined by Newton steps in FP64
-        // (one step gives ~1e-14 after an FP32 seed, two after FP64's own division)
-        const double n = M0;
-        double rn = double(rcp_(Real(n)));
-        rn = fma(rn, fma(-n, rn, 1.0), rn);
-        if (sizeof(Real) == 8) rn = fma(rn, fma(-n, rn, 1.0), rn);
-        const double u = M1 * rn;
         // 3 n T = sum xi^2 phi + sum theta = (S2 + R0) - u S1
-        const double T = fma(-u, M1, ME) * rn * (1.0 / 3.0);
+        Real uf, Tf, nf;
+        if constexpr (kFF) {
+            const FF n = fast_two_sum(F0.h, F0.l), m1 = fast_two_sum(F1.h, F1.l), me = fast_two_sum(FE.h, FE.l);
+            const FF u = ff_div(m1, n);
+            const FF T = ff_div(ff_add(me, ff_neg(ff_mul(u, m1))), ff_mul_f(n, 3.0f));
+            nf = Real(n.h);
+            uf = Real(u.h);
+            Tf = Real(T.h);
+        } else {
+            // 1/n from a working-precision reciprocal refined by Newton steps in FP64
+            // (one step gives ~1e-14 after an FP32 seed, two after FP64's own division)
+            const double n = M0;
+            double rn = double(rcp_(Real(n)));
+            rn = fma(rn, fma(-n, rn, 1.0), rn);
+            if (sizeof(Real) == 8) rn = fma(rn, fma(-n, rn, 1.0), rn);
+            const double u = M1 * rn;
+            const double T = fma(-u, M1, ME) * rn * (1.0 / 3.0);
+            uf = Real(u);
+            Tf = Real(T);
+            nf = Real(n);
+        }
         // 2 q = sum xi^3 phi + sum xi theta = S3 + R1 - u (3 S2 + R0) + 2 u^2 S1
-        const Real uf = Real(u), Tf = Real(T), nf = Real(n);
         const Real q = Real(0.5) * (tS3 + tR1 - uf * fma(Real(3), tS2, tR0) + Real(2) * uf * uf * (uf * nf));
         const int64_t i = i0 - kHalo + c;
         if (i >= 0 && i < a.nx) {
@@ -343,9 +436,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     V *out = static_cast<V *>(a.out);
     const int64_t col = kHalo + i;
 
+    // psi^n rows of the tile's cells (columns kHalo + i0 .. kHalo + i0 + tile - 1,
+    // inside every row, whose stride leaves room for the staged segment): one
+    // thread prefetches the rows of pair j + QL_PSIN_PREFETCH_AHEAD into L2 while
+    // pair j is computed, so the loads of psi^n below hit L2.  The byte offsets
+    // are multiples of 16: stride is a multiple of 32 pairs, kHalo + i0 of 4 pairs
+    // (tile = 31 WARPS with WARPS a multiple of 4) and tile x sizeof(V) of 16.
+    constexpr int AHEAD = QL_PSIN_PREFETCH_AHEAD;
+    constexpr uint32_t kRowBytes = uint32_t(TileShape<WARPS>::tile * sizeof(V));
+    static_assert(kRowBytes % 16 == 0 && (TileShape<WARPS>::tile * sizeof(V)) % 16 == 0, "bulk prefetch size");
+    if (STAGE >= 2 && AHEAD > 0 && t == 0) {
+        for (int j = 0; j < AHEAD && j < H; ++j) {
+            prefetch_l2_bulk(base + int64_t(H + j) * stride + kHalo + i0, kRowBytes);
+            prefetch_l2_bulk(base + int64_t(H - 1 - j) * stride + kHalo + i0, kRowBytes);
+        }
+    }
+
 #pragma unroll 1
     for (int j = 0; j < H; ++j) {
         const int kp = H + j, km = H - 1 - j;
+        if (STAGE >= 2 && AHEAD > 0 && t == 0 && j + AHEAD < H) {
+            prefetch_l2_bulk(base + int64_t(H + j + AHEAD) * stride + kHalo + i0, kRowBytes);
+            prefetch_l2_bulk(base + int64_t(H - 1 - j - AHEAD) * stride + kHalo + i0, kRowBytes);
+        }
         const int64_t ip = int64_t(kp) * stride + col, im = int64_t(km) * stride + col;
         // psi^n of this cell, loaded before the arithmetic that hides its latency
         // (every lane's column lies inside the row: ghost or padding columns at worst)
@@ -479,28 +592,37 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
 
 // ---------------------------------------------------------------------------
 // Discrete equilibrium of given fields (Eq. feq), computed in FP64, for the
-// interior and the ghost columns.  One thread per (cell, k).
+// interior and the ghost columns.  One thread per column: the normalised
+// Hermite coefficients once, then g at +p_k and -p_k from the even and odd
+// parts of the sum.
 template <typename Real, int Q>
 __global__ void fdlb_init_kernel(const double *__restrict__ rho, const double *__restrict__ u,
                                  const double *__restrict__ T, P2<Real> *__restrict__ psi, int64_t nx,
                                  int64_t stride, const double *__restrict__ tab)
 {
     constexpr TabView TV = tab_view(Q);
+    constexpr int H = Q / 2;
     const int64_t ncol = nx + 2 * kHalo;
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= ncol * Q) return;
-    const int k = int(e / ncol);
-    const int64_t c = e % ncol;  // column, cell c - kHalo
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // column, cell c - kHalo
+    if (c >= ncol) return;
     const double uu = u[c], TT = T[c], n = rho[c];
-    double cm2 = 1.0, cm1 = uu;
-    double g = tab[TV.G + k * Q + 0] * cm2 + tab[TV.G + k * Q + 1] * cm1;
-    for (int l = 2; l < Q; ++l) {
-        const double cl = tab[TV.ca + l] * uu * cm1 + tab[TV.cb + l] * (TT - 1.0) * cm2;
-        g += tab[TV.G + k * Q + l] * cl;
-        cm2 = cm1;
-        cm1 = cl;
+    double ch[Q];
+    ch[0] = 1.0;
+    ch[1] = uu;
+#pragma unroll
+    for (int l = 2; l < Q; ++l) ch[l] = tab[TV.ca + l] * uu * ch[l - 1] + tab[TV.cb + l] * (TT - 1.0) * ch[l - 2];
+    for (int j = 0; j < H; ++j) {
+        const double *G = tab + TV.G + (H + j) * Q;
+        double e = 0.0, o = 0.0;
+#pragma unroll
+        for (int l = 0; l < Q; l += 2) {
+            e = fma(G[l], ch[l], e);
+            o = fma(G[l + 1], ch[l + 1], o);
+        }
+        const double gp = n * (e + o), gm = n * (e - o);
+        psi[int64_t(H + j) * stride + c] = mk2(Real(gp), Real(2.0 * TT * gp));
+        psi[int64_t(H - 1 - j) * stride + c] = mk2(Real(gm), Real(2.0 * TT * gm));
     }
-    psi[int64_t(k) * stride + c] = mk2(Real(n * g), Real(2.0 * TT * n * g));
 }
 
 template <typename Real>

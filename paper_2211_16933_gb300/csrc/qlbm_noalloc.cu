@@ -91,7 +91,8 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     const size_t elem = opts->precision == QL_FP32 ? 8 : 16;
     // psi points at cell 0 of row 0; the buffer starts at the first ghost column
     void *rows = static_cast<unsigned char *>(psi) - kHalo * elem;
-    if (reinterpret_cast<uintptr_t>(rows) % 16 != 0) return nfail(QL_EINVAL, "state rows must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(rows) % 16 != 0 || (size_t(row_stride) * elem) % 16 != 0)
+        return nfail(QL_EINVAL, "state rows must be 16-byte aligned (FP32: row_stride must be even)");
     const size_t buf = size_t(vs->Q) * size_t(row_stride) * elem;
     if (kHeaderBytes + 2 * buf > kScratchBytes)
         return nfail(QL_EINVAL, "state of " + std::to_string(buf) + " bytes per stage buffer exceeds the " +

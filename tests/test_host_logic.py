@@ -88,6 +88,22 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
     assert e.value.status in (q.QL_EINVAL, q.QL_ECUDA)
 
 
+def test_noalloc_rejects_bad_layouts_before_touching_the_gpu(qlbm_lib):
+    """Argument checks of ql_step_noalloc run before any device call: a stride below the minimum, an odd FP32
+    stride (rows would start 8-byte aligned) and a misaligned state pointer are rejected."""
+    q = qlbm_lib
+    nx = 512
+    vs, grid, b = q.ql_velset(16, 0), q.ql_grid(nx, 1.0, 1e-4), q.ql_bc(q.QL_BC_PERIODIC, 0)
+    o = q.ql_opts()
+    o.precision, o.pr_mode, o.enskog, o.rho_ref, o.pr_const = q.QL_FP32, q.QL_PR_CONST, 1, 1.0, 2.0 / 3.0
+    good = (nx + 264 + 31) // 32 * 32
+    for psi, stride, words in ((1 << 12, good - 32, "row_stride"), (1 << 12, good + 1, "aligned"),
+                               ((1 << 12) + 8, good, "aligned")):
+        with pytest.raises(q.QLError) as e:
+            q.ql_step_noalloc(vs, grid, 0.1, 0.1, b, o, psi, stride, 1)
+        assert e.value.status == q.QL_EINVAL and words in str(e.value), str(e.value)
+
+
 def test_python_binding_has_no_cpu_path():
     """The binding only marshals arguments into the CUDA library: it imports no oracle and
     has no numerical fallback."""
