@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class Model(C.Structure):
     _fields_ = [
         ("Q", C.c_int), ("nx", C.c_int), ("bc", C.c_int), ("pr_mode", C.c_int),
-        ("enskog", C.c_int), ("pad_", C.c_int),
+        ("enskog", C.c_int), ("chi_mode", C.c_int),
         ("L", C.c_double), ("dx", C.c_double), ("dt", C.c_double),
         ("denseness", C.c_double), ("kn", C.c_double), ("pr_const", C.c_double),
         ("rho_ref", C.c_double),
@@ -84,6 +84,11 @@ def lib():
         L.oq_cd6.restype = C.c_double
         L.oq_cd6.argtypes = [_D, C.c_double]
         L.oq_model_init.argtypes = [C.POINTER(Model)]
+        L.oq_fm_weight.restype = C.c_double
+        L.oq_fm_weight.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.oq_fm_halfwidth.restype = C.c_int
+        L.oq_fm_halfwidth.argtypes = [C.c_double, C.c_double]
+        L.oq_fm_average.argtypes = [C.POINTER(Model), _D, _D]
         L.oq_rhs.argtypes = [C.POINTER(Model), _D, _D, _D, _D]
         L.oq_rk3_step.argtypes = [C.POINTER(Model), _D, _D]
         L.oq_run.argtypes = [C.POINTER(Model), _D, _D, C.c_long]
@@ -214,17 +219,36 @@ def cd6(q, dx) -> float:
 # ---------------------------------------------------------------- whole model
 INIT_SOUND, INIT_RIEMANN, INIT_SHOCK = 0, 1, 2
 BC_PERIODIC, BC_FIXED = 0, 1
+CHI_SET, CHI_RET_FM = 0, 1
 
 
 def make_model(Q, nx, L, dt, denseness, kn, pr_mode=1, pr_const=2.0 / 3.0, rho_ref=1.0,
-               bc=BC_PERIODIC, enskog=1) -> Model:
+               bc=BC_PERIODIC, enskog=1, chi_mode=CHI_SET) -> Model:
     m = Model()
-    m.Q, m.nx, m.bc, m.pr_mode, m.enskog = Q, nx, bc, pr_mode, enskog
+    m.Q, m.nx, m.bc, m.pr_mode, m.enskog, m.chi_mode = Q, nx, bc, pr_mode, enskog, chi_mode
     m.L, m.dt, m.denseness, m.kn, m.pr_const, m.rho_ref = L, dt, denseness, kn, pr_const, rho_ref
     st = lib().oq_model_init(C.byref(m))
     if st:
         raise ValueError(f"oq_model_init failed ({st})")
     return m
+
+
+def fm_weight(d: int, dx: float, sigma: float) -> float:
+    """Weight of the cell at offset d in the Fischer-Methfessel density average (Eq. chi_ret)."""
+    return lib().oq_fm_weight(d, dx, sigma)
+
+
+def fm_halfwidth(dx: float, sigma: float) -> int:
+    return lib().oq_fm_halfwidth(dx, sigma)
+
+
+def fm_average(m: Model, n_ext):
+    """Fischer-Methfessel averages of the densities of the extended cells -3 .. nx+2."""
+    n_ext = _f64(n_ext)
+    assert n_ext.shape == (m.nx + 6,)
+    out = np.zeros_like(n_ext)
+    lib().oq_fm_average(C.byref(m), _p(n_ext), _p(out))
+    return out
 
 
 def velocity_set(m: Model):

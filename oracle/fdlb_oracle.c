@@ -16,6 +16,8 @@
  *   - The reduced distributions are stored cell-major: phi[i*Q + k].
  *   - Passages the paper leaves open are marked READING and listed with the
  *     same label in the project's design notes.
+ *   - chi is chi_SET of the local density (Eq. chi) or, with chi_mode 1, of
+ *     the Fischer-Methfessel average of the density (Eq. chi_ret).
  *
  * Parity status
  *   Every function below is pinned by a -m "not gpu" test against a closed
@@ -44,7 +46,7 @@ typedef struct {
     int bc;       /* 0 periodic, 1 fixed ghost cells (READING c10) */
     int pr_mode;  /* 0 constant Pr, 1 dense Pr(b rho chi), Sec. II.B */
     int enskog;   /* 1: J1 included; 0: J1 omitted (test switch) */
-    int pad_;
+    int chi_mode; /* 0 chi_SET of the local density (Eq. chi); 1 chi_RET-FM (Eq. chi_ret) */
     double L, dx, dt;
     double denseness; /* E_l = sigma / l at the reference density, Sec. II.B */
     double kn;        /* Kn = l0 / L, l0 the Enskog mean free path at rho_ref */
@@ -253,10 +255,9 @@ double oq_mu_ratio(double bn, double chi, double T) { return oq_mu_over_muref(bn
  * b rho = 4 eta, and the ideal-gas pressure uses the density that matches b,
  * P_i = (4 eta / b) T.  This is the "tau = sigma g[eta]" scaling of Eq.
  * (tau_sigma): at fixed eta, tau is proportional to sigma. */
-double oq_tau(const oq_model *m, double n, double T)
+static double oq_tau_chi(const oq_model *m, double n, double chi, double T)
 {
     double eta = m->eta0 * n / m->rho_ref;
-    double chi = oq_chi_set(eta);
     double bn = 4.0 * eta;
     double b = 2.0 * M_PI * pow(m->sigma, 3.0) / 3.0;
     double mu_ref = 5.0 / (16.0 * m->sigma * m->sigma) * sqrt(1.0 / M_PI);
@@ -265,12 +266,74 @@ double oq_tau(const oq_model *m, double n, double T)
     return mu / Pi;
 }
 
+double oq_tau(const oq_model *m, double n, double T)
+{
+    return oq_tau_chi(m, n, oq_chi_set(m->eta0 * n / m->rho_ref), T);
+}
+
 /* Pr used in the Shakhov term (READING c7): constant, or the dense value. */
 double oq_prandtl(const oq_model *m, double n)
 {
     if (m->pr_mode == 0) return m->pr_const;
     double eta = m->eta0 * n / m->rho_ref;
     return oq_prandtl_dense(4.0 * eta * oq_chi_set(eta));
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. II.A, Eq. (chi_ret): Fischer-Methfessel average of the density over a
+ * ball of radius sigma.  For fields that depend on x only, the slice of the
+ * ball at distance s from its centre is a disc of area pi (sigma^2 - s^2), so
+ *   nbar(x) = 3/(4 sigma^3) int_{-sigma}^{sigma} n(x + s) (sigma^2 - s^2) ds.
+ * With the cell values n_j taken as constant over each cell, the cell at
+ * offset d from x_i enters with the weight
+ *   K_d = 3/(4 sigma^3) [F(b) - F(a)],  F(s) = sigma^2 s - s^3/3,
+ *   a = max((d - 1/2) dx, -sigma),  b = min((d + 1/2) dx, sigma)   (0 if a >= b).
+ * READING c19: piecewise-constant cells.  The weights sum to one.
+ * ---------------------------------------------------------------------- */
+double oq_fm_weight(int d, double dx, double sigma)
+{
+    double a = (d - 0.5) * dx, b = (d + 0.5) * dx;
+    if (a < -sigma) a = -sigma;
+    if (b > sigma) b = sigma;
+    if (a >= b) return 0.0;
+    double Fb = sigma * sigma * b - b * b * b / 3.0;
+    double Fa = sigma * sigma * a - a * a * a / 3.0;
+    return 3.0 / (4.0 * sigma * sigma * sigma) * (Fb - Fa);
+}
+
+/* Cells on each side that the ball reaches: the largest d with (d - 1/2) dx < sigma. */
+int oq_fm_halfwidth(double dx, double sigma)
+{
+    int W = 0;
+    while ((W + 0.5) * dx < sigma) ++W;
+    return W;
+}
+
+/* nbar of every cell of the extended array (nx + 2 OQ_NG cells, cell j is
+ * i = j - OQ_NG) from the densities n of the same cells; nbar may alias n.
+ * READING c19: beyond the extended array the density continues periodically
+ * (bc 0) or as that of the outermost ghost cell (bc 1). */
+void oq_fm_average(const oq_model *m, const double *n, double *nbar)
+{
+    int nx = m->nx, ne = nx + 2 * OQ_NG;
+    int W = oq_fm_halfwidth(m->dx, m->sigma);
+    double *out = (double *)malloc(sizeof(double) * ne);
+    for (int j = 0; j < ne; ++j) {
+        double acc = 0.0;
+        for (int d = -W; d <= W; ++d) {
+            int jj = j + d, src;
+            if (m->bc == 0) {
+                int i = jj - OQ_NG;
+                src = ((i % nx) + nx) % nx + OQ_NG;
+            } else {
+                src = jj < 0 ? 0 : (jj >= ne ? ne - 1 : jj);
+            }
+            acc += oq_fm_weight(d, m->dx, m->sigma) * n[src];
+        }
+        out[j] = acc;
+    }
+    memcpy(nbar, out, sizeof(double) * ne);
+    free(out);
 }
 
 /* ------------------------------------------------------------------------
@@ -434,6 +497,7 @@ int oq_rhs(const oq_model *m, const double *phi, const double *theta, double *Lp
            double *Ltheta)
 {
     int Q = m->Q, nx = m->nx, ne = nx + 2 * OQ_NG;
+    double *lnchi = (double *)malloc(sizeof(double) * ne);
     double *ephi = (double *)malloc(sizeof(double) * ne * Q);
     double *eth = (double *)malloc(sizeof(double) * ne * Q);
     double *mom = (double *)malloc(sizeof(double) * ne * 5);
@@ -454,21 +518,33 @@ int oq_rhs(const oq_model *m, const double *phi, const double *theta, double *Lp
         lnT[j] = log(mj[2]);
     }
 
+    /* 2a. chi of every cell, ghosts included: chi_SET of the local density, or
+     * (chi_mode 1) chi_SET of the Fischer-Methfessel average nbar (Eq. chi_ret). */
+    {
+        double *dens = (double *)malloc(sizeof(double) * ne);
+        for (int j = 0; j < ne; ++j) dens[j] = mom[5 * j];
+        if (m->chi_mode == 1) oq_fm_average(m, dens, dens);
+        for (int j = 0; j < ne; ++j) lnchi[j] = log(oq_chi_set(m->eta0 * dens[j] / m->rho_ref));
+        free(dens);
+    }
+
     /* 2.-4. collision terms, written into Lphi/Ltheta */
     for (int i = 0; i < nx; ++i) {
         int j = i + OQ_NG;
         double n = mom[5 * j], u = mom[5 * j + 1], T = mom[5 * j + 2], q = mom[5 * j + 4];
         double eta = m->eta0 * n / m->rho_ref;
-        double chi = oq_chi_set(eta);
+        double chi = exp(lnchi[j]);
         double Y = 4.0 * eta * chi; /* b rho chi */
-        double tau = oq_tau(m, n, T);
-        double Pr = oq_prandtl(m, n);
+        double tau = oq_tau_chi(m, n, chi, T);
+        double Pr = m->pr_mode == 0 ? m->pr_const : oq_prandtl_dense(Y);
         double dlnrho = oq_cd6(lnn + j - 3, m->dx);
         double du = oq_cd6(uu + j - 3, m->dx);
         double dlnT = oq_cd6(lnT + j - 3, m->dx);
-        /* d ln chi / d ln rho = eta d ln chi / d eta, with
-         * d ln chi / d eta = 3/(1-eta) - 1/(2-eta) for chi_SET */
-        double dlnchi = eta * (3.0 / (1.0 - eta) - 1.0 / (2.0 - eta)) * dlnrho;
+        /* chi_SET: d ln chi / d ln rho = eta d ln chi / d eta, with
+         * d ln chi / d eta = 3/(1-eta) - 1/(2-eta) (READING c6); chi_RET-FM: the
+         * 6th-order difference of ln chi(nbar) (App. A.3) */
+        double dlnchi = m->chi_mode == 1 ? oq_cd6(lnchi + j - 3, m->dx)
+                                         : eta * (3.0 / (1.0 - eta) - 1.0 / (2.0 - eta)) * dlnrho;
         double phiS[OQ_QMAX], thS[OQ_QMAX], jp[OQ_QMAX], jt[OQ_QMAX];
         oq_shakhov(Q, m->p, m->w, n, u, T, q, Pr, phiS, thS);
         if (m->enskog)
@@ -504,7 +580,7 @@ int oq_rhs(const oq_model *m, const double *phi, const double *theta, double *Lp
                 Lc[(size_t)i * Q + k] -= pk * (face[i + 1] - face[i]) / m->dx;
         }
     }
-    free(ephi); free(eth); free(mom); free(lnn); free(uu); free(lnT); free(face);
+    free(ephi); free(eth); free(mom); free(lnn); free(uu); free(lnT); free(face); free(lnchi);
     return status;
 }
 

@@ -34,6 +34,14 @@ MUTATIONS = {
     "prandtl_coeff": ("double den = 1.0 + 1.2 * Y", "double den = 1.0 + 1.0 * Y"),
     "sound_init_eos": ("T[c] = P0 / (r * (1.0 + 4.0 * eta * oq_chi_set(eta)));", "T[c] = P0 / (r * (1.0 + 2.0 * eta * oq_chi_set(eta)));"),
     "quadrature_weight": ("w[k] = qf / (hq1 * hq1);", "w[k] = qf / (hq1 * hq1) * (1.0 + 1e-9 * k);"),
+    "fm_slice_area": ("double Fb = sigma * sigma * b - b * b * b / 3.0;", "double Fb = sigma * sigma * b - b * b * b / 2.0;"),
+    "fm_normalisation": ("return 3.0 / (4.0 * sigma * sigma * sigma) * (Fb - Fa);", "return 1.0 / (sigma * sigma * sigma) * (Fb - Fa);"),
+    "fm_halfwidth": ("while ((W + 0.5) * dx < sigma) ++W;", "while ((W + 1.0) * dx < sigma) ++W;"),
+    "fm_fixed_extension": ("src = jj < 0 ? 0 : (jj >= ne ? ne - 1 : jj);", "src = jj < 0 ? 0 : (jj >= ne ? 0 : jj);"),
+    "fm_periodic_wrap": ("src = ((i % nx) + nx) % nx + OQ_NG;", "src = ((i % nx) + nx) % nx;"),
+    "ret_dlnchi": ("double dlnchi = m->chi_mode == 1 ? oq_cd6(lnchi + j - 3, m->dx)", "double dlnchi = m->chi_mode == 1 ? 0.5 * oq_cd6(lnchi + j - 3, m->dx)"),
+    "ret_tau_local_chi": ("double tau = oq_tau_chi(m, n, chi, T);", "double tau = oq_tau(m, n, T);"),
+    "ret_prandtl_local_chi": ("double Pr = m->pr_mode == 0 ? m->pr_const : oq_prandtl_dense(Y);", "double Pr = oq_prandtl(m, n);"),
 }
 
 

@@ -472,3 +472,139 @@ def test_sound_speed_of_dense_gas_from_a_run():
             return a * np.exp(-at * t) + np.exp(-aa * t) * (b * np.cos(om * t) + c * np.sin(om * t))
         popt, _ = curve_fit(model, ts, amps, p0=[0.3, 0.1, 0.7, 0.1, 0.0, k * cs_exact], maxfev=20000)
         assert popt[5] / k == pytest.approx(cs_exact, rel=1e-3), (enskog, popt[5] / k, cs_exact)
+
+
+# ---------------------------------------------------------------------------
+# chi_RET-FM (Eq. chi_ret): the Fischer-Methfessel density average
+
+
+def _ball_fraction_below(t, sigma):
+    """Fraction of a ball of radius sigma lying at x < t: the spherical cap of height h = sigma + t has
+    volume pi h^2 (3 sigma - h) / 3 (textbook cap formula)."""
+    h = min(max(sigma + t, 0.0), 2 * sigma)
+    return math.pi * h * h * (3 * sigma - h) / 3.0 / (4.0 / 3.0 * math.pi * sigma ** 3)
+
+
+@pytest.mark.parametrize("ratio", [0.3, 0.5, 1.0, 2.0, 2.6, 7.3])
+def test_fm_weights_are_ball_volume_fractions(ratio):
+    """K_d is the fraction of the ball's volume inside cell d: differences of spherical-cap volumes."""
+    dx, sigma = 0.37, 0.37 * ratio
+    W = O.fm_halfwidth(dx, sigma)
+    assert (W - 0.5) * dx < sigma <= (W + 0.5) * dx or (W == 0 and sigma <= 0.5 * dx)
+    tot = 0.0
+    for d in range(-W - 2, W + 3):
+        ref = _ball_fraction_below((d + 0.5) * dx, sigma) - _ball_fraction_below((d - 0.5) * dx, sigma)
+        k = O.fm_weight(d, dx, sigma)
+        assert k == pytest.approx(ref, abs=1e-14)
+        if abs(d) > W:
+            assert k == 0.0
+        tot += k
+    assert tot == pytest.approx(1.0, abs=1e-14)
+
+
+def test_fm_average_of_a_fourier_mode_and_reduction_to_the_local_density():
+    """Periodic: the average of c + A sin(k x) is c + A sin(k x) sum_d K_d cos(k d dx) (symmetric
+    kernel); for sigma <= dx/2 the ball stays inside the cell and nbar = n."""
+    nx, L = 40, 1.0
+    for kn, expect_identity in ((0.05, False), (0.005, True)):
+        m = O.make_model(16, nx, L, 1e-3, 1.1, kn, bc=O.BC_PERIODIC)
+        dx, sigma = L / nx, 1.1 * kn * L
+        W = O.fm_halfwidth(dx, sigma)
+        x = (np.arange(-3, nx + 3) + 0.5) * dx
+        k = 2 * np.pi * 3 / L
+        n = 1.0 + 0.2 * np.sin(k * x)
+        nbar = O.fm_average(m, n)
+        gain = sum(O.fm_weight(d, dx, sigma) * math.cos(k * d * dx) for d in range(-W, W + 1))
+        np.testing.assert_allclose(nbar, 1.0 + 0.2 * gain * np.sin(k * x), rtol=0, atol=1e-14)
+        if expect_identity:
+            assert W == 0 and gain == pytest.approx(1.0, abs=1e-15)
+        else:
+            assert W >= 2 and gain < 0.99
+
+
+def test_fm_average_fixed_boundaries_continue_the_ghost_density():
+    """Fixed ghosts: beyond the ghost cells the density is that of the outermost ghost cell, so a
+    state uniform near each end averages to that end's density."""
+    nx = 30
+    m = O.make_model(16, nx, 1.0, 1e-3, 1.1, 0.1, bc=O.BC_FIXED)
+    dx, sigma = 1.0 / nx, 1.1 * 0.1
+    W = O.fm_halfwidth(dx, sigma)
+    assert W == 3
+    n = np.where(np.arange(-3, nx + 3) < nx // 2, 1.0, 0.25)
+    nbar = O.fm_average(m, n)
+    i = np.arange(-3, nx + 3)
+    far = np.abs(i + 0.5 - nx // 2) > W + 0.5
+    np.testing.assert_allclose(nbar[far], n[far], rtol=0, atol=1e-15)
+    # next to the jump the average mixes both states with the cap weights
+    j = nx // 2 + 3  # cell nx//2 (first of the right state) in the extended array
+    ref = sum(O.fm_weight(d, dx, sigma) * (1.0 if d < 0 else 0.25) for d in range(-W, W + 1))
+    assert nbar[j] == pytest.approx(ref, abs=1e-15)
+
+
+def test_ret_fm_uniform_equilibrium_is_a_fixed_point():
+    for bc in (O.BC_PERIODIC, O.BC_FIXED):
+        m = O.make_model(16, 12, 1.0, 2e-3, 1.1, 0.1, bc=bc, chi_mode=O.CHI_RET_FM)
+        state = (1.2, 0.3, 0.9)
+        O.set_ghosts(m, [state] * 3, [state] * 3)
+        ph, th = O.equilibrium_state(m, np.full(12, state[0]), np.full(12, state[1]), np.full(12, state[2]))
+        Lp, Lt = O.rhs(m, ph, th)
+        assert np.abs(Lp).max() < 1e-12 and np.abs(Lt).max() < 1e-12
+
+
+def test_ret_fm_collision_terms_from_pinned_parts():
+    """RHS(RET-FM) - RHS(SET) is the difference of the collision terms alone (the advection is the
+    same); rebuild it cell by cell from the pinned pieces with chi = chi_SET(nbar) in b rho chi, tau,
+    Pr and J1, and d ln chi the 6th-order difference of ln chi(nbar)."""
+    nx, L, El, kn = 36, 1.0, 1.1, 0.08
+    mr = O.make_model(16, nx, L, 1e-3, El, kn, chi_mode=O.CHI_RET_FM)
+    ms = O.make_model(16, nx, L, 1e-3, El, kn, chi_mode=O.CHI_SET)
+    ph, th = _random_periodic_state(ms, 21)
+    Lr_p, Lr_t = O.rhs(mr, ph, th)
+    Ls_p, Ls_t = O.rhs(ms, ph, th)
+    p, w = O.velocity_set(ms)
+    dx, sigma, eta0 = L / nx, El * kn * L, ms.eta0
+    ext = np.arange(-3, nx + 3) % nx
+    mom = np.array([O.moments(p, ph[i], th[i]) for i in range(nx)])
+    n_ext = mom[ext, 0]
+    nbar = O.fm_average(mr, n_ext)
+    lnchi_ret = np.log([O.chi_set(eta0 * v) for v in nbar])
+    lnn, uu, lnT = np.log(mom[ext, 0]), mom[ext, 1], np.log(mom[ext, 2])
+    b = 2 * math.pi * sigma ** 3 / 3
+    mu_ref = 5.0 / (16.0 * sigma * sigma) * math.sqrt(1 / math.pi)
+
+    def coll(i, chi, dlnchi):
+        n, u, T, q = mom[i, 0], mom[i, 1], mom[i, 2], mom[i, 4]
+        eta = eta0 * n
+        Y = 4 * eta * chi
+        tau = mu_ref * O.mu_over_muref(4 * eta, chi, T) / ((4 * eta / b) * T)
+        Pr = O.prandtl_dense(Y)
+        j = i + 3
+        dlnrho, du, dlnT = (O.cd6(a[j - 3:j + 4], dx) for a in (lnn, uu, lnT))
+        phS, thS = O.shakhov(p, w, n, u, T, q, Pr)
+        jp, jt = O.j1(p, w, n, u, T, Y, dlnchi, dlnrho, du, dlnT)
+        return -(ph[i] - phS) / tau + jp, -(th[i] - thS) / tau + jt
+
+    worst = 0.0
+    for i in range(nx):
+        j = i + 3
+        eta = eta0 * mom[i, 0]
+        dlnrho = O.cd6(lnn[j - 3:j + 4], dx)
+        cs_p, cs_t = coll(i, O.chi_set(eta), eta * (3 / (1 - eta) - 1 / (2 - eta)) * dlnrho)
+        cr_p, cr_t = coll(i, math.exp(lnchi_ret[j]), O.cd6(lnchi_ret[j - 3:j + 4], dx))
+        scale = np.abs(Ls_p[i]).max()
+        np.testing.assert_allclose(Lr_p[i] - Ls_p[i], cr_p - cs_p, rtol=0, atol=1e-10 * scale)
+        np.testing.assert_allclose(Lr_t[i] - Ls_t[i], cr_t - cs_t, rtol=0, atol=1e-10 * np.abs(Ls_t[i]).max())
+        worst = max(worst, np.abs(cr_p - cs_p).max() / scale)
+    assert worst > 1e-4  # the two closures do differ on this state
+
+
+def test_ret_fm_conserves_mass_and_is_mirror_symmetric():
+    m = O.make_model(16, 40, 1.0, 1e-3, 1.1, 0.06, chi_mode=O.CHI_RET_FM)
+    ph, th = _random_periodic_state(m, 8)
+    t0 = O.totals(m, ph, th)
+    ph2, th2 = O.run(m, ph, th, 10)
+    assert abs(O.totals(m, ph2, th2)[0] - t0[0]) < 1e-13
+    Lp, Lt = O.rhs(m, ph, th)
+    Lpr, Ltr = O.rhs(m, ph[::-1, ::-1].copy(), th[::-1, ::-1].copy())
+    np.testing.assert_allclose(Lpr, Lp[::-1, ::-1], rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(Ltr, Lt[::-1, ::-1], rtol=1e-9, atol=1e-13)
