@@ -53,6 +53,13 @@ enum { QL_FP64 = 0, QL_FP32 = 1 };              /* arithmetic of the state and i
 enum { QL_BC_PERIODIC = 0, QL_BC_FIXED = 1 };   /* boundary of the 1D domain */
 enum { QL_INIT_SOUND = 0, QL_INIT_RIEMANN = 1, QL_INIT_SHOCK = 2, QL_INIT_FIELDS = 3 };
 enum { QL_PR_CONST = 0, QL_PR_DENSE = 1 };
+/* Contact value of the pair correlation function (Sec. II.A): chi_SET of the
+ * local density (Eq. chi), or chi_RET-FM, chi_SET of the density averaged over
+ * a ball of radius sigma (Eq. chi_ret). */
+enum { QL_CHI_SET = 0, QL_CHI_RET_FM = 1 };
+/* Largest number of cells on each side that the chi_RET-FM ball may reach
+ * (sigma / dx < QL_FM_MAX_HALFWIDTH + 1/2). */
+#define QL_FM_MAX_HALFWIDTH 256
 
 /* Velocity set, Sec. II.D: the Q roots p_k of the probabilists' Hermite
  * polynomial He_Q with weights w_k = Q!/He_{Q+1}(p_k)^2 (kind 0 is the only
@@ -115,6 +122,15 @@ typedef void (*ql_free_fn)(void *ptr, void *user);
  *              the dense gas as a function of b rho chi (Sec. II.B).
  *   enskog     1 adds the simplified-Enskog term J1 of Eq. (j1_expanded);
  *              0 leaves it out (b rho chi still sets tau and Pr).
+ *   chi_mode   QL_CHI_SET or QL_CHI_RET_FM.  With QL_CHI_RET_FM, chi of
+ *              every cell is chi_SET of nbar, the density averaged over the
+ *              ball of radius sigma around the cell centre (for fields that
+ *              depend on x only: nbar = 3/(4 sigma^3) int n(x+s)(sigma^2-s^2)
+ *              ds over |s| < sigma, cells constant over their width); it
+ *              enters b rho chi, tau, Pr and J1, and d ln chi is the 6th-order
+ *              difference of ln chi.  Beyond the domain the density continues
+ *              periodically, or (fixed bc) as that of ghost cell -3 / nx + 2.
+ *              The output pressure keeps chi_SET of the local density.
  *   rho_ref    density at which the denseness E_l is given; the local reduced
  *              density is eta = eta0 rho / rho_ref.
  *   stream     cudaStream_t for all work, NULL for the legacy default stream. */
@@ -123,6 +139,8 @@ typedef struct {
     int32_t pr_mode;
     int32_t enskog;
     int32_t device;
+    int32_t chi_mode;
+    int32_t pad_;
     double pr_const;
     double rho_ref;
     void *stream;
@@ -137,7 +155,8 @@ typedef struct {
  *   kn         l0/L > 0, l0 the Enskog mean free path at rho_ref; with E_l it
  *              fixes sigma = E_l l0 and so tau = sigma g[eta] (Eq. tau_sigma).
  * Errors: QL_EINVAL (bad sizes, dt <= 0, eta0 out of range, init kind needs
- * another bc), QL_EUNSUPPORTED (Q), QL_ENOMEM, QL_ECUDA.  On error *out is
+ * another bc, bad chi_mode), QL_EUNSUPPORTED (Q; a chi_RET-FM ball reaching
+ * more than QL_FM_MAX_HALFWIDTH cells), QL_ENOMEM, QL_ECUDA.  On error *out is
  * NULL. */
 ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, double kn,
                     const ql_bc *bc, const ql_init *init, const ql_opts *opts, ql_ctx **out);
@@ -183,7 +202,9 @@ ql_status ql_rhs(ql_ctx *ctx, double *Lphi, double *Ltheta);
  * (phi_k, theta_k); *psi points at cell 0 of row 0 and cell i of row k is
  * pair (*psi)[k * row_stride + i].  A pair is two doubles for QL_FP64 and two
  * floats for QL_FP32.  Valid until the next ql_step returns and the stream has
- * run it. */
+ * run it.  The view is for reading: with chi_RET-FM the solver keeps the
+ * averaged densities of the state it last wrote, so a state changed through
+ * this pointer must be loaded again with ql_set_state. */
 ql_status ql_state_device(ql_ctx *ctx, void **psi, int64_t *row_stride);
 
 /* Numbers fixed at creation: out[0] = eta0, out[1] = chi(eta0),
@@ -214,8 +235,8 @@ typedef struct {
 } ql_instance;
 
 /* Creates a batch of n >= 1 instances (host array inst; the initial-field
- * arrays it points to are read before return).  From opts only precision,
- * device, stream and the allocator hooks are used; with stream NULL the batch
+ * arrays it points to are read before return).  Instances use chi_SET.  From
+ * opts only precision, device, stream and the allocator hooks are used; with stream NULL the batch
  * creates its own stream (a CUDA graph cannot be captured on the legacy
  * default stream).  Errors as for ql_create, naming the first bad instance. */
 ql_status ql_batch_create(const ql_instance *inst, int64_t n, const ql_opts *opts, ql_batch **out);
@@ -326,7 +347,9 @@ const char *ql_closure_last_error(const ql_closure *c);
  *               ql_state_device reports for a context of the same nx); rows
  *               start 16-byte aligned, so in FP32 it must be even.
  *   The other arguments are those of ql_create; from opts only precision,
- *   pr_mode, enskog, device, pr_const, rho_ref and stream are used.
+ *   pr_mode, enskog, device, pr_const, rho_ref, stream and chi_mode are used,
+ *   and chi_mode must be QL_CHI_SET (QL_EUNSUPPORTED otherwise: chi_RET-FM
+ *   needs per-cell density buffers).
  * The two intermediate stage buffers and the error word live in one fixed
  * scratch array of QL_NOALLOC_MAX_BYTES that every GPU loading this library
  * holds until the process exits; a state whose two stage buffers (2 Q

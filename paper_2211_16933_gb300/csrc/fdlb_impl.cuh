@@ -17,11 +17,11 @@ cudaError_t QL_FN(upload_tables_)(const double *all)
     return cudaMemcpyToSymbol(QL_TAB, host, sizeof(host));
 }
 
-template <int Q, int STAGE>
+template <int Q, int STAGE, bool RET>
 static cudaError_t stage_q(const StageArgs &a, cudaStream_t s)
 {
-    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, kWarps>();
-    auto kern = fdlb_stage_kernel<QL_REAL, Q, STAGE>;
+    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, kWarps, RET>();
+    auto kern = fdlb_stage_kernel<QL_REAL, Q, STAGE, RET>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -35,16 +35,28 @@ static cudaError_t stage_q(const StageArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int Q, bool RET>
+static cudaError_t stage_dispatch_ret(int stage, const StageArgs &a, cudaStream_t s)
+{
+    switch (stage) {
+    case 0: return stage_q<Q, 0, RET>(a, s);
+    case 1: return stage_q<Q, 1, RET>(a, s);
+    case 2: return stage_q<Q, 2, RET>(a, s);
+    case 3: return stage_q<Q, 3, RET>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// chi_RET-FM kernels when the averaged densities are given (a.nbar, and a.nout
+// for stages 1-3), chi_SET kernels otherwise.
 template <int Q>
 static cudaError_t stage_dispatch(int stage, const StageArgs &a, cudaStream_t s)
 {
-    switch (stage) {
-    case 0: return stage_q<Q, 0>(a, s);
-    case 1: return stage_q<Q, 1>(a, s);
-    case 2: return stage_q<Q, 2>(a, s);
-    case 3: return stage_q<Q, 3>(a, s);
+    if (a.nbar != nullptr) {
+        if (stage != 0 && a.nout == nullptr) return cudaErrorInvalidValue;
+        return stage_dispatch_ret<Q, true>(stage, a, s);
     }
-    return cudaErrorInvalidValue;
+    return stage_dispatch_ret<Q, false>(stage, a, s);
 }
 
 cudaError_t QL_FN(launch_stage_)(int Q, int stage, const StageArgs &a, cudaStream_t s)
@@ -126,9 +138,45 @@ cudaError_t QL_FN(launch_periodic_ghosts_)(int Q, void *psi, int64_t nx, int64_t
     return cudaGetLastError();
 }
 
+cudaError_t QL_FN(launch_density_)(int Q, const void *psi, int64_t nx, int64_t stride, void *n, cudaStream_t s)
+{
+    const P2<QL_REAL> *p = static_cast<const P2<QL_REAL> *>(psi);
+    QL_REAL *out = static_cast<QL_REAL *>(n);
+    const unsigned blocks = unsigned((nx + 255) / 256);
+    switch (Q) {
+    case 8: fdlb_density_kernel<QL_REAL, 8><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
+    case 16: fdlb_density_kernel<QL_REAL, 16><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
+    case 24: fdlb_density_kernel<QL_REAL, 24><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
+    case 32: fdlb_density_kernel<QL_REAL, 32><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t QL_FN(launch_fm_)(const FmArgs &a, cudaStream_t s)
+{
+    if (a.W < 0 || a.W > QL_FM_MAX_HALFWIDTH) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(QL_REAL) * (kFmThreads + 4 * size_t(a.W) + 1);
+    const unsigned blocks = unsigned((a.nx + 2 * kHalo + kFmThreads - 1) / kFmThreads);
+    fdlb_fm_kernel<QL_REAL><<<blocks, kFmThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t QL_FN(launch_moments_)(int Q, const MomentArgs &a, const double *tab64, cudaStream_t s)
 {
     const unsigned blocks = unsigned(moment_blocks(a.nx));
+    if constexpr (sizeof(QL_REAL) == 4) {
+        if (!(a.rho || a.u || a.T || a.P || a.q || a.Pxx)) {  // totals only
+            switch (Q) {
+            case 8: fdlb_totals_f32_kernel<8><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+            case 16: fdlb_totals_f32_kernel<16><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+            case 24: fdlb_totals_f32_kernel<24><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+            case 32: fdlb_totals_f32_kernel<32><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+            default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+        }
+    }
     switch (Q) {
     case 8: fdlb_moments_kernel<QL_REAL, 8><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
     case 16: fdlb_moments_kernel<QL_REAL, 16><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;

@@ -73,6 +73,13 @@ template <>
 __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 
 template <typename Real>
+__device__ __forceinline__ Real exp_(Real x);
+template <>
+__device__ __forceinline__ float exp_<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_<double>(double x) { return exp(x); }
+
+template <typename Real>
 __device__ __forceinline__ Real rcp_(Real x);
 template <>
 __device__ __forceinline__ float rcp_<float>(float x) { return __fdividef(1.0f, x); }
@@ -198,6 +205,61 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Shared-memory address of a generic pointer into shared memory.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// mbarrier of a CTA (PTX mbarrier.*): initialised for one arriving thread;
+// the TMA unit signals the bytes of its bulk copies against it.
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bulk copy (TMA, no tensor map) of `bytes` from global to shared memory,
+// completion counted on `bar`; both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (TMA) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Polls of the staging mbarrier before a CTA gives up (each try_wait may
+// itself suspend the thread for a while); a give-up sets bit 1 of the error
+// word and the tile is skipped.
+constexpr uint32_t kMbarPolls = 1u << 22;
+
+// 1: stage the tile's rows with TMA bulk copies; 0: with 16-byte loads.
+#ifndef QL_STAGE_TMA
+#define QL_STAGE_TMA 1
+#endif
+
 // Velocity pairs ahead of the current one whose psi^n rows stages 2 and 3
 // prefetch into L2.
 #ifndef QL_PSIN_PREFETCH_AHEAD
@@ -220,11 +282,13 @@ struct TileShape {
     static constexpr int seg = tile + 2 * kHalo;
 };
 
-template <typename Real, int Q, int WARPS>
+// Shared memory of one stage CTA: the staged rows, the table rows of p > 0,
+// 6 per-cell arrays, and 2 more for chi_RET-FM.
+template <typename Real, int Q, int WARPS, bool RET = false>
 constexpr size_t stage_smem_bytes()
 {
     constexpr int SEG = TileShape<WARPS>::seg;
-    return sizeof(P2<Real>) * size_t(Q) * SEG + sizeof(Real) * (size_t(Q / 2) * Q + 6 * size_t(SEG));
+    return sizeof(P2<Real>) * size_t(Q) * SEG + sizeof(Real) * (size_t(Q / 2) * Q + (RET ? 8 : 6) * size_t(SEG));
 }
 
 // 1: the FP32 mode combines its per-cell conserved sums in FP64 instead of
@@ -232,6 +296,12 @@ constexpr size_t stage_smem_bytes()
 #ifndef QL_F32_SUMS_FP64
 #define QL_F32_SUMS_FP64 0
 #endif
+
+// 16-byte staging loads each thread keeps in flight.
+#ifndef QL_STAGE_LOAD_UNROLL
+#define QL_STAGE_LOAD_UNROLL 4
+#endif
+constexpr int kStageLoadUnroll = QL_STAGE_LOAD_UNROLL;
 
 // Resident CTAs per SM the FP32 stage kernels are compiled for (8-warp tiles;
 // the register budget follows from it).
@@ -243,8 +313,9 @@ constexpr size_t stage_smem_bytes()
 // One Runge-Kutta stage (STAGE 1..3), or L[psi] itself (STAGE 0), on the tile
 // of cells i0 .. i0 + 31 WARPS - 1 of one 1D domain.  All threads of the CTA
 // call it together; it uses dynamic shared memory from `smem`.
-template <typename Real, int Q, int STAGE, int WARPS>
-__device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0, unsigned char *smem_raw)
+template <typename Real, int Q, int STAGE, int WARPS, bool RET = false>
+__device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0, unsigned char *smem_raw,
+                                           uint64_t *mbar, uint32_t phase)
 {
     using V = P2<Real>;
     constexpr TabView TV = tab_view(Q);
@@ -260,25 +331,62 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     Real *s_q = s_T + SEG;
     Real *s_lnn = s_q + SEG;
     Real *s_lnT = s_lnn + SEG;
+    Real *s_lnchi = s_lnT + SEG;  // chi_RET-FM: nbar, then ln chi(nbar)
+    Real *s_nout = s_lnchi + SEG; // chi_RET-FM: density of the output, per owned cell
+    constexpr bool ret = RET;  // chi_RET-FM: a.nbar and a.nout are set
 
     const int t = threadIdx.x;
     const int64_t stride = a.stride;
     const V *__restrict__ in = static_cast<const V *>(a.in);
 
-    // 1. Stage cells i0-kHalo .. i0+tile+kHalo-1 of every row (16-byte vectors).
+    // 1. Stage cells i0-kHalo .. i0+tile+kHalo-1 of every row: one thread has
+    //    the TMA unit copy the Q row segments (SEG pairs each) while the others
+    //    load the tables; or every thread copies 16-byte vectors.  Source rows
+    //    start at pair r stride + i0: stride is even and i0 a multiple of 4, so
+    //    with 16-byte aligned buffers every segment starts 16-byte aligned.
     {
-        constexpr int PPV = 16 / sizeof(V);  // pairs per vector
-        constexpr int VPR = SEG / PPV;       // vectors per row
-        static_assert(SEG % PPV == 0, "staging shape");
-#pragma unroll 4
-        for (int e = t; e < Q * VPR; e += THREADS) {
-            const int r = e / VPR, vv = e - r * VPR;
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + r * stride + i0) + vv);
-            reinterpret_cast<uint4 *>(s_psi + r * SEG)[vv] = v;
+        static_assert((SEG * sizeof(V)) % 16 == 0 && (TileShape<WARPS>::tile * sizeof(V)) % 16 == 0,
+                      "TMA bulk copy alignment");
+        if (QL_STAGE_TMA) {
+            if (t == 0) {
+                fence_proxy_async_smem();  // the previous tile's reads of s_psi come first
+                mbar_arrive_expect_tx(mbar, uint32_t(Q * SEG * sizeof(V)));
+                for (int r = 0; r < Q; ++r)
+                    bulk_copy_g2s(s_psi + r * SEG, in + r * stride + i0, uint32_t(SEG * sizeof(V)), mbar);
+            }
+        } else {
+            constexpr int PPV = 16 / sizeof(V);  // pairs per vector
+            constexpr int VPR = SEG / PPV;       // vectors per row
+            static_assert(SEG % PPV == 0, "staging shape");
+#pragma unroll kStageLoadUnroll
+            for (int e = t; e < Q * VPR; e += THREADS) {
+                const int r = e / VPR, vv = e - r * VPR;
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in + r * stride + i0) + vv);
+                reinterpret_cast<uint4 *>(s_psi + r * SEG)[vv] = v;
+            }
         }
         for (int e = t; e < H * Q; e += THREADS) s_G[e] = QL_TAB[TV.G + H * Q + e];
+        // nbar of staged cell c sits at column i0 + c (the buffer has a row stride of columns)
+        if (ret)
+            for (int c = t; c < SEG; c += THREADS) s_lnchi[c] = static_cast<const Real *>(a.nbar)[i0 + c];
     }
-    __syncthreads();
+    if (QL_STAGE_TMA) {
+        // every thread waits for the copies; the give-up decision is CTA-wide
+        uint32_t polls = 0;
+        while (!mbar_try_wait(mbar, phase) && ++polls < kMbarPolls) {
+        }
+        if (__syncthreads_or(polls >= kMbarPolls)) {
+            if (t == 0) atomicOr(a.err, 2u);
+            // let copies still in flight land before the shared memory is reused
+            polls = 0;
+            while (!mbar_try_wait(mbar, phase) && ++polls < kMbarPolls) {
+            }
+            __syncthreads();
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
 
     // 2. Moments of staged cell c (cell i0 - kHalo + c), Sec. II.D, from raw
     //    sums over velocity pairs.  FP64 mode sums in FP64.  FP32 mode sums
@@ -358,6 +466,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
         s_q[c] = q;
         s_lnn[c] = log_(nf);
         s_lnT[c] = log_(Tf);
+        if (ret) {
+            // Eq. (chi_ret): chi_SET of the averaged density
+            const Real eb = Real(a.eta0) * s_lnchi[c] * Real(a.inv_rho_ref), omb = Real(1) - eb;
+            s_lnchi[c] = log_(Real(0.5) * (Real(2) - eb) / (omb * omb * omb));
+        }
     }
     __syncthreads();
 
@@ -379,7 +492,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     const Real rhat = n * Real(a.inv_rho_ref);
     const Real eta = Real(a.eta0) * rhat;
     const Real ome = Real(1) - eta;
-    const Real chi = Real(0.5) * (Real(2) - eta) / (ome * ome * ome);
+    const Real chi = ret ? exp_(s_lnchi[s]) : Real(0.5) * (Real(2) - eta) / (ome * ome * ome);
     const Real Y = Real(4) * eta * chi;
     const Real muf = fma(fma(Real(0.16 * (1.0 + 12.0 / 3.14159265358979323846)), Y, Real(0.8)), Y, Real(1));
     const Real sqT = T * rsqrt_(T);
@@ -394,8 +507,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     // Shakhov: A = (1 - Pr) q / (5 P_i T), P_i = n T
     const Real A = (Real(1) - Pr) * q * invT * invT / (Real(5) * n);
     const Real Yj = a.enskog ? Y : Real(0);
-    // d ln chi = eta (3/(1-eta) - 1/(2-eta)) d ln rho  (chi_SET depends on eta only)
-    const Real dlnchi = eta * (Real(3) / ome - Real(1) / (Real(2) - eta)) * dlnn;
+    // chi_SET: d ln chi = eta (3/(1-eta) - 1/(2-eta)) d ln rho (chi depends on the local eta only);
+    // chi_RET-FM: 6th-order difference of ln chi(nbar)
+    const Real dlnchi =
+        ret ? cd6_(s_lnchi, s) * inv_dx : eta * (Real(3) / ome - Real(1) / (Real(2) - eta)) * dlnn;
     const Real G = dlnchi + Real(2) * dlnn;
     // Targets over the equilibrium, cubic in xi = p_k - u:
     //   phi:   (1/tau)(1 + A xi (xi^2/T - 3)) - Y [xi G + 3/5 (xi^2/T - 1) du + 3/10 (xi^3/T + xi/3) dlnT]
@@ -435,6 +550,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     const V *__restrict__ base = static_cast<const V *>(a.base);
     V *out = static_cast<V *>(a.out);
     const int64_t col = kHalo + i;
+    // chi_RET-FM: the output density of the owned cell, summed over the velocity
+    // loop (only this thread touches s_nout[s])
+    if (RET && STAGE != 0 && owner) s_nout[s] = Real(0);
 
     // psi^n rows of the tile's cells (columns kHalo + i0 .. kHalo + i0 + tile - 1,
     // inside every row, whose stride leaves room for the staged segment): one
@@ -512,6 +630,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             }
             out[ip] = op;
             out[im] = om;
+            if (RET && STAGE != 0) s_nout[s] += op.x + om.x;
             if (STAGE != 0 && a.periodic) {
                 // periodic images in the ghost columns of the other end
                 if (i < kHalo) {
@@ -525,6 +644,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             }
         }
     }
+    if (RET && STAGE != 0 && owner) static_cast<Real *>(a.nout)[i] = s_nout[s];
 }
 
 template <typename Real>
@@ -533,11 +653,16 @@ struct StageOccupancy {
 };
 
 // One Runge-Kutta stage over a whole domain: CTA b updates tile b.
-template <typename Real, int Q, int STAGE>
+template <typename Real, int Q, int STAGE, bool RET>
 __global__ void __launch_bounds__(kThreads, StageOccupancy<Real>::value) fdlb_stage_kernel(StageArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<Real, Q, STAGE, kWarps>(a, int64_t(blockIdx.x) * kTile, smem_raw);
+    __shared__ __align__(8) uint64_t mbar;
+    if (QL_STAGE_TMA) {
+        if (threadIdx.x == 0) mbar_init(&mbar);
+        __syncthreads();
+    }
+    stage_tile<Real, Q, STAGE, kWarps, RET>(a, int64_t(blockIdx.x) * kTile, smem_raw, &mbar, 0u);
 }
 
 // Batched form: one persistent launch per Runge-Kutta stage over a work list
@@ -554,7 +679,13 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
     fdlb_batch_stage_kernel(BatchArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    for (int64_t w = blockIdx.x; w < b.nwork; w += gridDim.x) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (QL_STAGE_TMA) {
+        if (threadIdx.x == 0) mbar_init(&mbar);
+        __syncthreads();
+    }
+    uint32_t phase = 0;  // parity of the staging mbarrier, one phase per item
+    for (int64_t w = blockIdx.x; w < b.nwork; w += gridDim.x, phase ^= 1u) {
         const int2 it = b.work[w];
         const BatchInstance &I = b.inst[it.x];
         StageArgs a;
@@ -578,12 +709,14 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
         a.periodic = I.periodic;
         a.pad_ = 0;
         a.err = b.err + it.x;
+        a.nbar = nullptr;  // instances use chi_SET
+        a.nout = nullptr;
         const int64_t i0 = int64_t(it.y) * TileShape<WARPS>::tile;
         switch (I.Q) {
-        case 8: stage_tile<Real, 8, STAGE, WARPS>(a, i0, smem_raw); break;
-        case 16: stage_tile<Real, 16, STAGE, WARPS>(a, i0, smem_raw); break;
-        case 24: stage_tile<Real, 24, STAGE, WARPS>(a, i0, smem_raw); break;
-        case 32: stage_tile<Real, 32, STAGE, WARPS>(a, i0, smem_raw); break;
+        case 8: stage_tile<Real, 8, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
+        case 16: stage_tile<Real, 16, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
+        case 24: stage_tile<Real, 24, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
+        case 32: stage_tile<Real, 32, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
         default: break;
         }
         __syncthreads();  // shared memory is reused by the next item
@@ -641,6 +774,59 @@ __global__ void fdlb_periodic_ghost_kernel(P2<Real> *__restrict__ psi, int64_t n
 }
 
 // ---------------------------------------------------------------------------
+// chi_RET-FM.  Density sum_k phi_k of every interior cell of a state, in the
+// order of the stage kernel's output sum (pairs k = H + j, H - 1 - j).
+template <typename Real, int Q>
+__global__ void fdlb_density_kernel(const P2<Real> *__restrict__ psi, int64_t nx, int64_t stride,
+                                    Real *__restrict__ n)
+{
+    constexpr int H = Q / 2;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    Real acc = Real(0);
+    for (int j = 0; j < H; ++j)
+        acc += psi[int64_t(H + j) * stride + kHalo + i].x + psi[int64_t(H - 1 - j) * stride + kHalo + i].x;
+    n[i] = acc;
+}
+
+// Density of cell i (any integer) for the ball average: the interior cells,
+// then periodic images or the fixed ghost densities, cells beyond -3 / nx+2
+// taking the outermost ghost value.
+template <typename Real>
+__device__ __forceinline__ Real fm_density(const FmArgs &a, const Real *n, int64_t i)
+{
+    if (i >= 0 && i < a.nx) return n[i];
+    if (a.periodic) return n[((i % a.nx) + a.nx) % a.nx];
+    if (i < 0) return Real(a.ghost[i < -3 ? 0 : i + 3]);
+    const int64_t g = i - a.nx;
+    return Real(a.ghost[3 + (g > 2 ? 2 : g)]);
+}
+
+constexpr int kFmThreads = 256;
+
+// nbar of columns c0 .. c0 + 255 (cells c - kHalo), Eq. (chi_ret): the tile's
+// densities with W cells on each side are staged in shared memory, then each
+// thread sums 2 W + 1 weighted neighbours.
+template <typename Real>
+__global__ void __launch_bounds__(kFmThreads) fdlb_fm_kernel(FmArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *s_n = reinterpret_cast<Real *>(smem_raw);  // [kFmThreads + 2 W]
+    Real *s_K = s_n + kFmThreads + 2 * a.W;          // [2 W + 1]
+    const Real *__restrict__ n = static_cast<const Real *>(a.n);
+    const int64_t c0 = int64_t(blockIdx.x) * kFmThreads;
+    const int64_t cell0 = c0 - kHalo - a.W;  // cell of s_n[0]
+    for (int e = threadIdx.x; e < kFmThreads + 2 * a.W; e += kFmThreads) s_n[e] = fm_density<Real>(a, n, cell0 + e);
+    for (int e = threadIdx.x; e < 2 * a.W + 1; e += kFmThreads) s_K[e] = Real(a.K[e]);
+    __syncthreads();
+    const int64_t col = c0 + threadIdx.x;
+    if (col >= a.nx + 2 * kHalo) return;
+    Real acc = Real(0);
+    for (int d = 0; d <= 2 * a.W; ++d) acc = fma(s_K[d], s_n[threadIdx.x + d], acc);
+    static_cast<Real *>(a.nbar)[col] = acc;
+}
+
+// ---------------------------------------------------------------------------
 // Output fields (FP64) and per-block totals of mass, momentum and energy.
 template <typename Real, int Q>
 __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a, const double *__restrict__ tab)
@@ -650,18 +836,60 @@ __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a,
     const P2<Real> *__restrict__ psi = static_cast<const P2<Real> *>(a.psi);
     const int64_t i = int64_t(blockIdx.x) * kMomThreads + threadIdx.x;
     double M = 0, Pm = 0, E = 0;
+    // FP32 mode: p^j as double-FP32 pairs (hi, lo), built once per block
+    __shared__ float s_pw[6][Q];
+    if (sizeof(Real) == 4) {
+        if (threadIdx.x < Q) {
+            const double p = tab[TV.p + threadIdx.x];
+            const double pj[3] = {p, p * p, p * p * p};
+            for (int j = 0; j < 3; ++j) {
+                s_pw[2 * j][threadIdx.x] = float(pj[j]);
+                s_pw[2 * j + 1][threadIdx.x] = float(pj[j] - double(float(pj[j])));
+            }
+        }
+        __syncthreads();
+    }
     if (i < a.nx) {
         double S0 = 0, S1 = 0, S2 = 0, S3 = 0, R0 = 0, R1 = 0;
-        for (int k = 0; k < Q; ++k) {
-            const P2<Real> v = psi[int64_t(k) * a.stride + kHalo + i];
-            const double ph = double(v.x), th = double(v.y);
-            const double p = tab[TV.p + k];
-            S0 += ph;
-            S1 += p * ph;
-            S2 += p * p * ph;
-            S3 += p * p * p * ph;
-            R0 += th;
-            R1 += p * th;
+        if constexpr (sizeof(Real) == 4) {
+            // sums of exact products p^j phi (two_sum / fma error terms) in
+            // double-FP32, converted to FP64 once per cell: FP64 runs at a small
+            // fraction of the FP32 rate on this GPU
+            FF F[6] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            for (int k = 0; k < Q; ++k) {
+                const P2<Real> v = psi[int64_t(k) * a.stride + kHalo + i];
+                const float x[6] = {v.x, v.x, v.x, v.x, v.y, v.y};
+                const int pw[6] = {-1, 0, 1, 2, -1, 0};  // power index of p (-1: p^0)
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    float prod = x[m], perr = 0.f;
+                    if (pw[m] >= 0) {
+                        const float ph = s_pw[2 * pw[m]][k], pl = s_pw[2 * pw[m] + 1][k];
+                        prod = ph * x[m];
+                        perr = fmaf(pl, x[m], fmaf(ph, x[m], -prod));
+                    }
+                    const FF t = two_sum(F[m].h, prod);
+                    F[m] = {t.h, F[m].l + (t.l + perr)};
+                }
+            }
+            S0 = double(F[0].h) + double(F[0].l);
+            S1 = double(F[1].h) + double(F[1].l);
+            S2 = double(F[2].h) + double(F[2].l);
+            S3 = double(F[3].h) + double(F[3].l);
+            R0 = double(F[4].h) + double(F[4].l);
+            R1 = double(F[5].h) + double(F[5].l);
+        } else {
+            for (int k = 0; k < Q; ++k) {
+                const P2<Real> v = psi[int64_t(k) * a.stride + kHalo + i];
+                const double ph = double(v.x), th = double(v.y);
+                const double p = tab[TV.p + k];
+                S0 += ph;
+                S1 += p * ph;
+                S2 += p * p * ph;
+                S3 += p * p * p * ph;
+                R0 += th;
+                R1 += p * th;
+            }
         }
         const double n = S0, u = S1 / n;
         const double c2 = S2 - u * S1;
@@ -690,6 +918,79 @@ __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a,
         __syncthreads();
     }
     if (threadIdx.x < 3) a.partial[blockIdx.x * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// FP32 mode, domain totals only (ql_totals): mass, momentum and energy of every
+// cell as double-FP32 sums of exact products, a non-physical check on their
+// leading parts, and block sums reduced in double-FP32 by warp shuffles, so
+// that no FP64 arithmetic runs per cell.
+__device__ __forceinline__ void ff_acc(FF &F, float x)
+{
+    const FF t = two_sum(F.h, x);
+    F = {t.h, F.l + t.l};
+}
+__device__ __forceinline__ void ff_acc_prod(FF &F, float ph, float pl, float x)
+{
+    const float prod = ph * x;
+    const float perr = fmaf(pl, x, fmaf(ph, x, -prod));
+    const FF t = two_sum(F.h, prod);
+    F = {t.h, F.l + (t.l + perr)};
+}
+__device__ __forceinline__ FF ff_shfl_down(FF v, int off)
+{
+    return {__shfl_down_sync(0xffffffffu, v.h, off), __shfl_down_sync(0xffffffffu, v.l, off)};
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kMomThreads) fdlb_totals_f32_kernel(MomentArgs a, const double *__restrict__ tab)
+{
+    constexpr TabView TV = tab_view(Q);
+    constexpr int NW = kMomThreads / 32;
+    __shared__ float s_pw[4][Q];  // p and p^2 as (hi, lo)
+    __shared__ FF s_red[3][NW];
+    if (threadIdx.x < Q) {
+        const double p = tab[TV.p + threadIdx.x], p2 = p * p;
+        s_pw[0][threadIdx.x] = float(p);
+        s_pw[1][threadIdx.x] = float(p - double(float(p)));
+        s_pw[2][threadIdx.x] = float(p2);
+        s_pw[3][threadIdx.x] = float(p2 - double(float(p2)));
+    }
+    __syncthreads();
+    const P2<float> *__restrict__ psi = static_cast<const P2<float> *>(a.psi);
+    const int64_t i = int64_t(blockIdx.x) * kMomThreads + threadIdx.x;
+    FF tot[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (i < a.nx) {
+        FF S0{0.f, 0.f}, S1{0.f, 0.f}, S2{0.f, 0.f}, R0{0.f, 0.f};
+        for (int k = 0; k < Q; ++k) {
+            const P2<float> v = psi[int64_t(k) * a.stride + kHalo + i];
+            ff_acc(S0, v.x);
+            ff_acc_prod(S1, s_pw[0][k], s_pw[1][k], v.x);
+            ff_acc_prod(S2, s_pw[2][k], s_pw[3][k], v.x);
+            ff_acc(R0, v.y);
+        }
+        S0 = fast_two_sum(S0.h, S0.l);
+        S1 = fast_two_sum(S1.h, S1.l);
+        const FF E2 = ff_add(fast_two_sum(S2.h, S2.l), fast_two_sum(R0.h, R0.l));  // 2 x energy
+        // 3 n T = S2 + R0 - u S1 with u = S1 / n
+        const float n = S0.h, u = S1.h / n, e3 = E2.h - u * S1.h;
+        if (!(n > 0.f) || !(e3 > 0.f) || !isfinite(u) || !isfinite(e3)) atomicOr(a.err, 1u);
+        tot[0] = S0;
+        tot[1] = S1;
+        tot[2] = E2;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int off = 16; off > 0; off >>= 1) tot[c] = ff_add(tot[c], ff_shfl_down(tot[c], off));
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) s_red[c][warp] = tot[c];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        FF acc = s_red[threadIdx.x][0];
+        for (int w = 1; w < NW; ++w) acc = ff_add(acc, s_red[threadIdx.x][w]);
+        const double scale = threadIdx.x == 2 ? 0.5 * a.dx : a.dx;
+        a.partial[blockIdx.x * 3 + threadIdx.x] = (double(acc.h) + double(acc.l)) * scale;
+    }
 }
 
 }  // namespace qlbm

@@ -33,6 +33,12 @@ struct ql_ctx {
     double *d_tab64 = nullptr;    // kTabTotal
     unsigned *d_err = nullptr;
     std::vector<double> ghost_state;  // (rho, u, T) of the 2 kHalo ghost columns, fixed bc
+    // chi_RET-FM (Eq. chi_ret): ball half-width in cells, weights, interior
+    // densities of the latest stage output, and nbar of every column
+    int chi_mode = QL_CHI_SET, fm_w = 0;
+    double *d_fmk = nullptr;  // 2 fm_w + 1
+    void *d_n = nullptr;      // nx values of the working precision
+    void *d_nbar = nullptr;   // stride values (columns -kHalo .. ; the tail past nx + kHalo unused)
     std::string err;
 };
 
@@ -98,8 +104,39 @@ static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, voi
     a.periodic = c->periodic;
     a.pad_ = 0;
     a.err = c->d_err;
+    const bool ret = c->chi_mode == QL_CHI_RET_FM;
+    a.nbar = ret ? c->d_nbar : nullptr;
+    a.nout = ret && s != 0 ? c->d_n : nullptr;
     return c->precision == QL_FP32 ? launch_stage_f32(c->Q, s, a, c->stream)
                                    : launch_stage_f64(c->Q, s, a, c->stream);
+}
+
+// chi_RET-FM: nbar of every column from the densities in d_n.
+static cudaError_t fm_average(ql_ctx *c)
+{
+    FmArgs f;
+    f.n = c->d_n;
+    f.nbar = c->d_nbar;
+    f.K = c->d_fmk;
+    f.nx = c->nx;
+    f.W = c->fm_w;
+    f.periodic = c->periodic;
+    for (int g = 0; g < 6; ++g) f.ghost[g] = 0.0;
+    if (!c->periodic && !c->ghost_state.empty())
+        for (int g = 0; g < 3; ++g) {
+            f.ghost[g] = c->ghost_state[3 * (g + 1)];      // cells -3..-1: columns 1..3
+            f.ghost[3 + g] = c->ghost_state[3 * (kHalo + g)];  // cells nx..nx+2
+        }
+    return c->precision == QL_FP32 ? launch_fm_f32(f, c->stream) : launch_fm_f64(f, c->stream);
+}
+
+// chi_RET-FM: densities of the current state psi^n, then nbar.
+static cudaError_t refresh_nbar(ql_ctx *c)
+{
+    if (c->chi_mode != QL_CHI_RET_FM) return cudaSuccess;
+    cudaError_t e = c->precision == QL_FP32 ? launch_density_f32(c->Q, c->buf[0], c->nx, c->stride, c->d_n, c->stream)
+                                            : launch_density_f64(c->Q, c->buf[0], c->nx, c->stride, c->d_n, c->stream);
+    return e == cudaSuccess ? fm_average(c) : e;
 }
 
 static ql_status check_err_word(ql_ctx *c)
@@ -107,6 +144,7 @@ static ql_status check_err_word(ql_ctx *c)
     unsigned h = 0;
     QL_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     QL_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & 2u) return fail(c, QL_ECUDA, "a stage kernel gave up waiting for its tile's TMA copies");
     if (h & 1u) return fail(c, QL_ENONPHYSICAL, "non-physical state: n <= 0, T <= 0 or non-finite moments");
     return QL_OK;
 }
@@ -138,6 +176,9 @@ static void destroy_buffers(ql_ctx *c)
     dev_free(c, c->d_totals);
     dev_free(c, c->d_tab64);
     dev_free(c, c->d_err);
+    dev_free(c, c->d_fmk);
+    dev_free(c, c->d_n);
+    dev_free(c, c->d_nbar);
 }
 
 extern "C" {
@@ -158,8 +199,10 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     if (opts->precision != QL_FP32 && opts->precision != QL_FP64) return fail(nullptr, QL_EINVAL, "bad precision");
     if (!(opts->rho_ref > 0)) return fail(nullptr, QL_EINVAL, "rho_ref must be > 0");
     if (opts->pr_mode == QL_PR_CONST && !(opts->pr_const > 0)) return fail(nullptr, QL_EINVAL, "pr_const must be > 0");
+    if (opts->chi_mode != QL_CHI_SET && opts->chi_mode != QL_CHI_RET_FM) return fail(nullptr, QL_EINVAL, "bad chi_mode");
 
     ql_ctx *c = new ql_ctx();
+    c->chi_mode = opts->chi_mode;
     c->Q = vs->Q;
     c->precision = opts->precision;
     c->pr_mode = opts->pr_mode;
@@ -191,6 +234,12 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     c->chi0 = chi_set(c->eta0);
     // sigma = E_l l0 with l0 = Kn L; tau = (5 sqrt(2 pi)/16) Kn L chi0 / (rho^ chi sqrt T) (1 + 0.8 Y + ...)
     c->sigma = denseness * kn * grid->length;
+    if (c->chi_mode == QL_CHI_RET_FM) {
+        c->fm_w = fm_halfwidth(c->dx, c->sigma);
+        if (c->fm_w > QL_FM_MAX_HALFWIDTH)
+            return bail(QL_EUNSUPPORTED, "the chi_RET-FM ball reaches " + std::to_string(c->fm_w) +
+                                             " cells on each side; at most QL_FM_MAX_HALFWIDTH are supported");
+    }
     c->tau_pref = 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * kn * grid->length * c->chi0;
     {
         std::lock_guard<std::mutex> lk(g_mutex);
@@ -237,6 +286,19 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     c->d_err = static_cast<unsigned *>(dev_alloc(c, 256));
     if (!c->d_fields || !c->d_init || !c->d_partial || !c->d_totals || !c->d_tab64 || !c->d_err)
         return bail(QL_ENOMEM, "work buffer allocation failed");
+    if (c->chi_mode == QL_CHI_RET_FM) {
+        const size_t real = c->precision == QL_FP32 ? 4 : 8;
+        c->d_fmk = static_cast<double *>(dev_alloc(c, sizeof(double) * (2 * c->fm_w + 1)));
+        c->d_n = dev_alloc(c, real * c->nx);
+        c->d_nbar = dev_alloc(c, real * c->stride);
+        if (!c->d_fmk || !c->d_n || !c->d_nbar) return bail(QL_ENOMEM, "chi_RET-FM buffer allocation failed");
+        std::vector<double> K(2 * c->fm_w + 1);
+        fm_weights(c->dx, c->sigma, c->fm_w, K.data());
+        e = cudaMemcpyAsync(c->d_fmk, K.data(), sizeof(double) * K.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nbar, 0, real * c->stride, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // K goes out of scope
+        if (e != cudaSuccess) return bail(QL_ECUDA, std::string("chi_RET-FM set-up: ") + cudaGetErrorString(e));
+    }
     e = cudaMemcpyAsync(c->d_tab64, g_tab, sizeof(double) * kTabTotal, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 256, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, state_bytes, c->stream);
@@ -260,6 +322,9 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
             c->ghost_state[3 * g + 2] = T[col];
         }
     }
+    e = refresh_nbar(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("chi_RET-FM set-up: ") + cudaGetErrorString(e));
     *out = c;
     return QL_OK;
 }
@@ -267,10 +332,16 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
 ql_status ql_step(ql_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
+    const bool ret = c->chi_mode == QL_CHI_RET_FM;
     for (int64_t s = 0; s < nsteps; ++s) {
+        // with chi_RET-FM each stage also writes the densities of its output,
+        // from which nbar for the next stage is averaged
         cudaError_t e = stage(c, 1, c->buf[0], c->buf[0], c->buf[1]);
+        if (e == cudaSuccess && ret) e = fm_average(c);
         if (e == cudaSuccess) e = stage(c, 2, c->buf[1], c->buf[0], c->buf[2]);
+        if (e == cudaSuccess && ret) e = fm_average(c);
         if (e == cudaSuccess) e = stage(c, 3, c->buf[2], c->buf[0], c->buf[0]);
+        if (e == cudaSuccess && ret) e = fm_average(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
     }
     return QL_OK;
@@ -392,6 +463,7 @@ ql_status ql_set_state(ql_ctx *c, const double *phi, const double *theta)
                                                 : launch_periodic_ghosts_f64(Q, c->buf[0], nx, c->stride, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "ghost kernel");
     }
+    QL_CUDA(c, refresh_nbar(c));
     QL_CUDA(c, cudaStreamSynchronize(c->stream));
     return QL_OK;
 }
@@ -429,6 +501,7 @@ ql_status ql_load_fields(ql_ctx *c, const double *rho, const double *u, const do
                         : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
                                           c->stride, c->d_tab64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    QL_CUDA(c, refresh_nbar(c));
     QL_CUDA(c, cudaStreamSynchronize(c->stream));
     return QL_OK;
 }

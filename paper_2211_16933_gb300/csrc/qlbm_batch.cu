@@ -370,11 +370,13 @@ ql_status ql_batch_sync(ql_batch *b, uint32_t *flags)
     std::vector<unsigned> h(b->n);
     QB_CUDA(b, cudaMemcpyAsync(h.data(), b->d_err, sizeof(unsigned) * b->n, cudaMemcpyDeviceToHost, b->stream));
     QB_CUDA(b, cudaStreamSynchronize(b->stream));
-    bool bad = false;
+    bool bad = false, gave_up = false;
     for (int64_t i = 0; i < b->n; ++i) {
         if (flags) flags[i] = h[i];
         bad |= (h[i] & 1u) != 0;
+        gave_up |= (h[i] & 2u) != 0;
     }
+    if (gave_up) return bfail(b, QL_ECUDA, "a stage kernel gave up waiting for its tile's TMA copies");
     if (bad) return bfail(b, QL_ENONPHYSICAL, "non-physical state in at least one instance");
     return QL_OK;
 }
@@ -412,6 +414,7 @@ ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, doubl
     unsigned h = 0;
     QB_CUDA(b, cudaMemcpyAsync(&h, b->d_err + i, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
     QB_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (h & 2u) return bfail(b, QL_ECUDA, "a stage kernel gave up waiting for its tile's TMA copies");
     if (h & 1u) return bfail(b, QL_ENONPHYSICAL, "non-physical state in instance " + std::to_string(i));
     return QL_OK;
 }

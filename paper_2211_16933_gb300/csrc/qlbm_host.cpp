@@ -1,4 +1,5 @@
 // Host-side physics in FP64 (see qlbm_host.h).
+#include <cmath>
 #include "qlbm_host.h"
 
 #include <math.h>
@@ -90,6 +91,33 @@ double cs_z(double eta) { return 1.0 + 4.0 * eta * chi_set(eta); }
 double cs_dz(double eta) { return 4.0 * (chi_set(eta) + eta * dchi_deta(eta)); }
 
 double denseness_of_eta(double eta) { return 6.0 * sqrt(2.0) * eta * chi_set(eta); }
+
+// The part of a ball of radius sigma at x < t (|t| <= sigma) is a spherical cap
+// of height h = sigma + t and volume pi h^2 (3 sigma - h) / 3; divided by the
+// ball's volume 4 pi sigma^3 / 3.
+static double ball_fraction_below(double t, double sigma)
+{
+    double h = sigma + t;
+    if (h <= 0.0) return 0.0;
+    if (h >= 2.0 * sigma) return 1.0;
+    return h * h * (3.0 * sigma - h) / (4.0 * sigma * sigma * sigma);
+}
+
+int fm_halfwidth(double dx, double sigma)
+{
+    // cell d reaches into the ball when (|d| - 1/2) dx < sigma
+    int W = int(std::ceil(sigma / dx - 0.5));
+    if (W < 0) W = 0;
+    while (W > 0 && (W - 0.5) * dx >= sigma) --W;
+    while ((W + 0.5) * dx < sigma) ++W;
+    return W;
+}
+
+void fm_weights(double dx, double sigma, int W, double *K)
+{
+    for (int d = -W; d <= W; ++d)
+        K[d + W] = ball_fraction_below((d + 0.5) * dx, sigma) - ball_fraction_below((d - 0.5) * dx, sigma);
+}
 
 bool eta_of_denseness(double El, double *eta)
 {

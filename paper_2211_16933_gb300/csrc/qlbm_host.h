@@ -33,6 +33,13 @@ bool initial_fields(int kind, const double *prm, int64_t nx, double length, int 
                     double eta0, double rho_ref, const double *urho, const double *uu, const double *uT,
                     const double *ughost, int halo, double *rho, double *u, double *T);
 
+// Eq. (chi_ret) in 1D with cells constant over their width: the cell at offset
+// d from a cell centre holds the fraction K_d of the volume of the ball of
+// radius sigma around that centre.  fm_halfwidth is the largest |d| with
+// K_d > 0; fm_weights fills K_{-W} .. K_W (2 W + 1 values).
+int fm_halfwidth(double dx, double sigma);
+void fm_weights(double dx, double sigma, int W, double *K);
+
 // All kernel tables (layout of tab_view in qlbm_internal.h).
 bool build_tables(double *all);
 

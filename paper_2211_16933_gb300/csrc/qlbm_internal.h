@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "qlbm.h"
+
 #ifdef __CUDACC__
 #define QL_HD __host__ __device__
 #else
@@ -70,7 +72,26 @@ struct StageArgs {
     double inv_dx, dt;
     double eta0, inv_rho_ref, tau_pref, pr_const;
     int pr_mode, enskog, periodic, pad_;
-    unsigned *err;  // device error word; bit 0: non-physical cell
+    unsigned *err;  // device error word; bit 0: non-physical cell, bit 1: a TMA staging wait gave up
+    // chi_RET-FM only (else null): nbar of every column of the stage input
+    // (nx + 2 kHalo values of the working precision), and the density of
+    // every interior cell of the stage output, written by the kernel.
+    const void *nbar;
+    void *nout;
+};
+
+// chi_RET-FM: nbar of every column (cells -kHalo .. nx+kHalo-1) from the
+// interior densities n, as the weighted sum over offsets -W .. W (weights K,
+// FP64); beyond the interior the density continues periodically or, fixed bc,
+// as ghost[0..2] (cells -3..-1) and ghost[3..5] (cells nx..nx+2), cells
+// further out taking the value of cell -3 / nx + 2.
+struct FmArgs {
+    const void *n;
+    void *nbar;
+    const double *K;
+    int64_t nx;
+    int W, periodic;
+    double ghost[6];
 };
 
 // Batched form: instances packed in three arenas (psi^n, psi^(1), psi^(2)),
@@ -110,6 +131,11 @@ cudaError_t launch_init_f64(int Q, const double *rho, const double *u, const dou
 // Copies the kHalo cells next to each end into the ghost columns of the
 // other end (periodic images), all Q rows.
 cudaError_t launch_periodic_ghosts_f32(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s);
+// Density sum_k phi_k of every interior cell of a state (chi_RET-FM).
+cudaError_t launch_density_f32(int Q, const void *psi, int64_t nx, int64_t stride, void *n, cudaStream_t s);
+cudaError_t launch_density_f64(int Q, const void *psi, int64_t nx, int64_t stride, void *n, cudaStream_t s);
+cudaError_t launch_fm_f32(const FmArgs &a, cudaStream_t s);
+cudaError_t launch_fm_f64(const FmArgs &a, cudaStream_t s);
 cudaError_t launch_periodic_ghosts_f64(int Q, void *psi, int64_t nx, int64_t stride, cudaStream_t s);
 
 // Output fields in FP64 per interior cell and per-block partial totals.

@@ -85,6 +85,8 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     if (bc->kind != QL_BC_PERIODIC && bc->kind != QL_BC_FIXED) return nfail(QL_EINVAL, "bad bc kind");
     if (opts->precision != QL_FP32 && opts->precision != QL_FP64) return nfail(QL_EINVAL, "bad precision");
     if (opts->pr_mode == QL_PR_CONST && !(opts->pr_const > 0)) return nfail(QL_EINVAL, "bad pr_const");
+    if (opts->chi_mode != QL_CHI_SET)
+        return nfail(QL_EUNSUPPORTED, "ql_step_noalloc supports chi_SET only (chi_RET-FM needs density buffers)");
     if (row_stride < qlbm::row_stride(grid->nx))
         return nfail(QL_EINVAL, "row_stride " + std::to_string(row_stride) + " is below the " +
                                     std::to_string(qlbm::row_stride(grid->nx)) + " pairs this nx needs");
@@ -140,6 +142,8 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     a.periodic = bc->kind == QL_BC_PERIODIC;
     a.pad_ = 0;
     a.err = err;
+    a.nbar = nullptr;
+    a.nout = nullptr;
     a.base = rows;
     for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
         void *ins[3] = {rows, B, C}, *outs[3] = {B, C, rows};
@@ -154,6 +158,7 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaSetDevice(prev);
     if (e != cudaSuccess) return nfail(QL_ECUDA, std::string("ql_step_noalloc: ") + cudaGetErrorString(e));
+    if (h & 2u) return nfail(QL_ECUDA, "a stage kernel gave up waiting for its tile's TMA copies");
     if (h & 1u) return nfail(QL_ENONPHYSICAL, "non-physical state: n <= 0, T <= 0 or non-finite moments");
     return QL_OK;
 }

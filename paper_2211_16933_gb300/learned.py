@@ -30,8 +30,8 @@ FIELDS = ("rho", "u", "T", "q", "Pxx")
 
 def pair_specs(n: int, seed0: int):
     """Seeded pair parameters: alternating sound waves (Q = 16) and shocks (Q = 32),
-    E_l ~ U[0.02, 0.3], Mach ~ U[1.2, 3] (shock temperatures in units of twice the
-    upstream temperature, as in the batched workload)."""
+    E_l ~ U[0.02, 0.3], Mach ~ U[1.2, 3] (upstream temperature inputs.SHOCK_T_UPSTREAM, as in
+    the batched workload)."""
     out = []
     for j in range(n):
         rng = np.random.default_rng(seed0 + j)
@@ -42,7 +42,7 @@ def pair_specs(n: int, seed0: int):
                             prm=(1.0, 1.0, float(rng.uniform(5e-3, 5e-2)))))
         else:
             out.append(dict(kind="shock", Q=32, denseness=El, kn=1.0 / 128.0, length=128.0,
-                            prm=(1.0, 0.5, mach, 4.0)))
+                            prm=(1.0, inputs.SHOCK_T_UPSTREAM, mach, 4.0)))
     return out
 
 

@@ -20,6 +20,8 @@ QL_FP64, QL_FP32 = 0, 1
 QL_BC_PERIODIC, QL_BC_FIXED = 0, 1
 QL_INIT_SOUND, QL_INIT_RIEMANN, QL_INIT_SHOCK, QL_INIT_FIELDS = 0, 1, 2, 3
 QL_PR_CONST, QL_PR_DENSE = 0, 1
+QL_CHI_SET, QL_CHI_RET_FM = 0, 1
+QL_FM_MAX_HALFWIDTH = 256
 SUPPORTED_Q = (8, 16, 24, 32)
 EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_get_state", "ql_set_state",
             "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",
@@ -62,7 +64,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class ql_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("pr_mode", C.c_int32), ("enskog", C.c_int32), ("device", C.c_int32),
-                ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
+                ("chi_mode", C.c_int32), ("pad_", C.c_int32), ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -451,7 +453,8 @@ class Solver:
 
     def __init__(self, Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND,
                  prm=(1.0, 1.0, 1e-3), rho=None, u=None, T=None, ghost=None, precision=QL_FP64,
-                 pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, device=0, use_torch=True):
+                 pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, device=0, use_torch=True,
+                 chi_mode=None):
         self.Q, self.nx, self.precision = Q, nx, precision
         vs = ql_velset(Q, 0)
         grid = ql_grid(nx, length, dt)
@@ -469,6 +472,7 @@ class Solver:
         o = ql_opts()
         o.precision, o.pr_mode, o.enskog, o.device = precision, pr_mode, enskog, device
         o.pr_const, o.rho_ref = pr_const, rho_ref
+        o.chi_mode = QL_CHI_SET if chi_mode is None else chi_mode
         self._torch_blocks = {}
         if use_torch:
             import torch

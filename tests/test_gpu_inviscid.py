@@ -1,0 +1,48 @@
+"""The shock tube at small Knudsen number against the exact inviscid solution of the dense gas (Sec. III.B,
+"Inviscid limit"): left state eta = 0.05 (E_l = 0.4825), right state eta / 8, T = 1, u = 0, chi_SET.  At
+Kn = 2e-5 the viscous and heat-conduction layers are a few 1e-3 wide at t = 0.15, so the plateau values
+and the fan match the Euler solution to a fraction of a percent, and the shock sits within a few cells of
+the exact position."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import riemann as R
+from paper_2211_16933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sod_tube_approaches_the_inviscid_solution(gpu, precision):
+    q = gpu
+    Q, nx, L, El, kn, t_end = 16, 8192, 1.0, 0.4825, 2e-5, 0.15
+    p, _ = q.ql_velocity_set(Q)
+    dt = inputs.cfl_dt(L / nx, float(np.abs(p).max()))
+    steps = int(round(t_end / dt))
+    s = q.Solver(Q, nx, L, dt, El, kn, bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN,
+                 prm=(1.0, 0.0, 1.0, 0.125, 0.0, 1.0), precision=precision, pr_mode=q.QL_PR_DENSE)
+    s.step(steps)
+    f = s.moments()
+    s.close()
+    t = steps * dt
+    st = R.ShockTube(R.DenseGas(O.eta_from_denseness(El)), 1.0, 1.0, 0.125, 1.0)
+    x = (np.arange(nx) + 0.5) * L / nx
+    xi = (x - 0.5 * L) / t
+    r_ex, u_ex, T_ex = st.sample(xi)
+    # inside the fan and the two plateaus, away from the layers at the edges of each region
+    pad = 0.02 / t
+    regions = [(st.xi_head + pad, st.xi_tail - pad), (st.xi_tail + pad, st.uc - pad), (st.uc + pad, st.xi_s - pad)]
+    for a, b in regions:
+        sel = (xi > a) & (xi < b)
+        assert sel.sum() > 100
+        for got, ref in ((f["rho"], r_ex), (f["u"], u_ex), (f["T"], T_ex)):
+            err = np.abs(got[sel] - ref[sel]).max()
+            assert err <= 5e-3 * max(1.0, np.abs(ref[sel]).max()), (a, b, err)
+    # shock position: where rho crosses the mean of the post-shock and right densities
+    mid = 0.5 * (st.rho2 + 0.125)
+    i = np.flatnonzero((f["rho"][:-1] >= mid) & (f["rho"][1:] < mid) & (x[:-1] > 0.5 * L + st.uc * t))[0]
+    x_s = x[i] + (f["rho"][i] - mid) / (f["rho"][i] - f["rho"][i + 1]) * (x[i + 1] - x[i])
+    assert abs(x_s - (0.5 * L + st.xi_s * t)) <= 4 * L / nx

@@ -27,7 +27,7 @@ TOL = {0: 1e-10, 1: 1e-5}          # fields, by precision (QL_FP64 = 0, QL_FP32 
 TOL_PSI = {0: 1e-10, 1: 2e-5}
 
 
-def _setup(q, w, precision, dt=None, fields=None, ghost=None, enskog=1):
+def _setup(q, w, precision, dt=None, fields=None, ghost=None, enskog=1, chi_mode=0):
     """Oracle model + initial state and a GPU solver for the same workload dict."""
     Q, nx, L = w["Q"], w["nx"], w["length"]
     p, _ = O.quadrature(Q)
@@ -35,7 +35,7 @@ def _setup(q, w, precision, dt=None, fields=None, ghost=None, enskog=1):
     bc = O.BC_PERIODIC if w["bc"] == "periodic" else O.BC_FIXED
     prm = 1 if w["pr_mode"] == "dense" else 0
     m = O.make_model(Q, nx, L, dt, w["denseness"], w["kn"], pr_mode=prm, pr_const=w["pr_const"], bc=bc,
-                     enskog=enskog)
+                     enskog=enskog, chi_mode=chi_mode)
     kind = {"sound": O.INIT_SOUND, "riemann": O.INIT_RIEMANN, "shock": O.INIT_SHOCK, "fields": 3}[w["init"]]
     kw = {}
     if kind == 3:
@@ -50,7 +50,7 @@ def _setup(q, w, precision, dt=None, fields=None, ghost=None, enskog=1):
             O.set_ghosts_from_init(m, kind, w["prm"])
     ph, th = O.equilibrium_state(m, r, u, T)
     s = q.Solver(Q, nx, L, dt, w["denseness"], w["kn"], bc=bc, init_kind=kind, prm=w["prm"] if kind != 3 else (),
-                 precision=precision, pr_mode=prm, pr_const=w["pr_const"], enskog=enskog, **kw)
+                 precision=precision, pr_mode=prm, pr_const=w["pr_const"], enskog=enskog, chi_mode=chi_mode, **kw)
     return m, ph, th, s
 
 
@@ -234,3 +234,71 @@ def test_state_roundtrip(gpu):
     b, c = s.state()
     np.testing.assert_array_equal(b, a)
     np.testing.assert_array_equal(c, th)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", ["periodic", "fixed"])
+def test_ret_fm_rhs_and_steps_match_oracle(gpu, precision, bc):
+    """chi_RET-FM (Eq. chi_ret): sigma / dx = 3.7, so the ball reaches 4 cells on each side; 3 tiles and
+    a ragged tail; the RHS of an off-equilibrium state, then 6 steps (each stage feeds the averaged
+    density of its output to the next)."""
+    nx = 3 * 248 + 17
+    w = _smooth_workload(16, nx, bc)
+    w["kn"] = 3.7 / (nx * w["denseness"])  # sigma = E_l Kn L
+    f = inputs.smooth_periodic_fields(nx, seed=77)
+    ghost = None
+    if bc == "fixed":
+        ghost = [(f[0][0], f[1][0], f[2][0])] * 3 + [(f[0][-1] * 0.9, f[1][-1], f[2][-1])] * 3
+    m, ph, th, s = _setup(gpu, w, precision, fields=f, ghost=ghost, chi_mode=1)
+    assert O.fm_halfwidth(m.dx, m.sigma) == 4
+    noise = inputs.state_noise(ph.shape, seed=78, scale=1e-2)
+    ph = ph * noise
+    s.set_state(ph, th)
+    if precision == 1:
+        ph, th = (a.astype(np.float32).astype(np.float64) for a in s.state())
+    Lp_o, Lt_o = O.rhs(m, ph, th)
+    Lp_g, Lt_g = s.rhs()
+    for a, b in ((Lp_g, Lp_o), (Lt_g, Lt_o)):
+        if precision == 0:
+            scale = np.abs(b).max(axis=0) + 1e-300
+            assert float((np.abs(a - b).max(axis=0) / scale).max()) <= 1e-11
+        else:
+            assert float(np.abs(a - b).max() / np.abs(b).max()) <= 2e-4
+    ph, th = O.run(m, ph, th, 6)
+    s.step(6)
+    _check(m, ph, th, s, precision)
+
+
+def test_ret_fm_differs_from_set(gpu):
+    """The averaged density changes the result: the chi_RET-FM and chi_SET right-hand sides of the same
+    state differ far beyond the FP64 tolerance, and the chi_RET-FM one matches its oracle."""
+    nx = 300
+    w = _smooth_workload(16, nx)
+    w["kn"] = 3.7 / (nx * w["denseness"])
+    f = inputs.smooth_periodic_fields(nx, seed=5, amp=(0.2, 0.1, 0.05))
+    m, ph, th, s_ret = _setup(gpu, w, 0, fields=f, chi_mode=1)
+    _, _, _, s_set = _setup(gpu, w, 0, fields=f, chi_mode=0)
+    Lr, _ = s_ret.rhs()
+    Ls, _ = s_set.rhs()
+    assert np.abs(Lr - Ls).max() > 1e-6 * np.abs(Ls).max()
+    Lo, _ = O.rhs(m, ph, th)
+    assert np.abs(Lr - Lo).max() <= 1e-11 * np.abs(Lo).max()
+
+
+@pytest.mark.parametrize("Q", [16, 32])
+def test_fp32_totals_kernel_matches_field_totals(gpu, Q):
+    """The FP32 totals-only kernel (double-FP32 sums and reductions) gives the domain totals of the field
+    kernel (FP64 per cell) to 1e-12, on several blocks and a ragged tail, and reports a negative density."""
+    nx = 5 * 256 + 77
+    w = _smooth_workload(Q, nx)
+    m, ph, th, s = _setup(gpu, w, 1, fields=inputs.smooth_periodic_fields(nx, seed=Q, amp=(0.2, 0.3, 0.1)))
+    s.step(3)
+    t_only = s.totals()
+    t_fields = s.moments()["totals"]
+    np.testing.assert_allclose(t_only, t_fields, rtol=1e-12, atol=1e-14)
+    ph2, th2 = s.state()
+    ph2[nx // 2] *= -1.0
+    s.set_state(ph2, th2)
+    with pytest.raises(gpu.QLError) as e:
+        s.totals()
+    assert e.value.status == gpu.QL_ENONPHYSICAL

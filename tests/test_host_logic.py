@@ -88,6 +88,28 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
     assert e.value.status in (q.QL_EINVAL, q.QL_ECUDA)
 
 
+def test_chi_ret_fm_options_are_checked_before_touching_the_gpu(qlbm_lib):
+    """chi_mode must be SET or RET-FM, and a chi_RET-FM ball reaching more than QL_FM_MAX_HALFWIDTH cells is
+    unsupported; ql_step_noalloc takes chi_SET only."""
+    q = qlbm_lib
+    kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-3), use_torch=False)
+    with pytest.raises(q.QLError) as e:
+        q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, chi_mode=7, **kw)
+    assert e.value.status == q.QL_EINVAL
+    nx, El = 4096, 1.1
+    kn = (q.QL_FM_MAX_HALFWIDTH + 20) / (nx * El)  # sigma / dx = QL_FM_MAX_HALFWIDTH + 20
+    with pytest.raises(q.QLError) as e:
+        q.Solver(16, nx, 1.0, 1e-5, El, kn, chi_mode=q.QL_CHI_RET_FM, **kw)
+    assert e.value.status == q.QL_EUNSUPPORTED and "QL_FM_MAX_HALFWIDTH" in str(e.value)
+    vs, grid, b = q.ql_velset(16, 0), q.ql_grid(512, 1.0, 1e-4), q.ql_bc(q.QL_BC_PERIODIC, 0)
+    o = q.ql_opts()
+    o.precision, o.pr_mode, o.enskog, o.rho_ref, o.pr_const = q.QL_FP32, q.QL_PR_CONST, 1, 1.0, 2.0 / 3.0
+    o.chi_mode = q.QL_CHI_RET_FM
+    with pytest.raises(q.QLError) as e:
+        q.ql_step_noalloc(vs, grid, 0.1, 0.1, b, o, 1 << 12, (512 + 264 + 31) // 32 * 32, 1)
+    assert e.value.status == q.QL_EUNSUPPORTED
+
+
 def test_noalloc_rejects_bad_layouts_before_touching_the_gpu(qlbm_lib):
     """Argument checks of ql_step_noalloc run before any device call: a stride below the minimum, an odd FP32
     stride (rows would start 8-byte aligned) and a misaligned state pointer are rejected."""
