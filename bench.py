@@ -471,6 +471,29 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dispersion(args):
+    """Sound-wave dispersion study (Sec. III.A): a batch of sound waves over a sweep of E_l, the density-mode
+    amplitude sampled in time, a Levenberg-Marquardt fit of c_s, alpha_a, alpha_t against linear theory."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import dispersion as D
+    torch.cuda.set_device(0)
+    B.build()
+    El = np.geomspace(0.01, 6.3, args.sweep)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows, updates = D.study(El, t_end=5.0, samples=500)
+    el = time.perf_counter() - t0
+    line = {"metric": "cell-velocity updates/s", "value": updates / el, "unit": "updates/s", "n_gpus": 1,
+            "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sound_wave_dispersion_sweep_{args.sweep}", "nx": 128, "Q": 16, "kn": 0.005,
+                       "amplitude": 1e-3, "t_end": 5.0, "samples": 500,
+                       "timing": "whole study incl. 500 projections and host fits"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,7 +506,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sod", "batch", "learned"], default="sod")
+    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion"], default="sod")
+    ap.add_argument("--sweep", type=int, default=16)
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--eval-pairs", type=int, default=1000)
     ap.add_argument("--tts-pairs", type=int, default=16)
@@ -502,6 +526,9 @@ def main():
         return
     if args.workload == "learned" and args.impl == "ours":
         run_learned(args)
+        return
+    if args.workload == "dispersion" and args.impl == "ours":
+        run_dispersion(args)
         return
     if args.impl == "reference":
         run_reference(args, w)

@@ -260,6 +260,12 @@ ql_status ql_batch_sync(ql_batch *b, uint32_t *flags);
 ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, double *T, double *P, double *q,
                            double *Pxx, double *totals);
 
+/* Amplitude of density mode m of every instance (Sec. III.A: the projection
+ * (2/nx) sum_j rho_j cos(2 pi m x_j / L) used to follow a sound wave), written
+ * as n doubles to the device array out (caller-owned).  Asynchronous on the
+ * batch's stream.  QL_EINVAL for a null batch or out, or m < 0. */
+ql_status ql_batch_project(ql_batch *b, int32_t mode, double *out);
+
 /* Fields of every instance on the device, averaged over blocks of nx/ncoarse
  * cells (ncoarse must divide every instance's nx; ncoarse = nx gives the
  * fields themselves): out (device, f64, n * 5 * ncoarse) holds, for instance
@@ -380,6 +386,21 @@ ql_status ql_eta_of_denseness(double denseness, double *eta0);
  * equation of state P = rho T (1 + b rho chi) and c_V = 3/2, at density rho
  * and temperature T, for eta = eta0 rho / rho_ref. */
 double ql_sound_speed2(double eta0, double rho_ref, double rho, double T);
+
+/* Linear modes of a sound wave of wave number k on the uniform state
+ * (rho, T) of a model with these parameters (Sec. III.A, Eqs. sw_cs and
+ * sw_coeff), from the transport coefficients the kinetic model carries:
+ * mu = tau P_i (Sec. II.B), lambda = (5/2) mu / Pr, the bulk viscosity of Eq.
+ * (bulk_viscosity) as a fraction of Eq. (viscosity), c_V = 3/2 and the
+ * equation of state P = rho T (1 + b rho chi):
+ *   alpha_t = lambda k^2 / (rho c_P),
+ *   alpha_a = k^2 / (2 rho) [4 mu / 3 + mu_v + (gamma - 1) lambda / c_P].
+ * out (host, 5 doubles) = {c_s, alpha_a, alpha_a with mu_v = 0, alpha_t,
+ * gamma}.  A density perturbation started with no pressure perturbation
+ * evolves as rho~(t) = rho~(0) [(1 - 1/gamma) exp(-alpha_t t) + (1/gamma)
+ * exp(-alpha_a t) cos(k c_s t)] (Eq. sw_solution).  QL_EINVAL on bad input. */
+ql_status ql_sound_modes(double denseness, double kn, double length, double rho_ref, int32_t pr_mode,
+                         double pr_const, double rho, double T, double k, double *out);
 
 /* Standing normal shock of Mach number mach > 1 into (rho1, T1), Eq.
  * (rankine_hugoniot) with the dense equation of state: out (host, 4 doubles)

@@ -89,6 +89,7 @@ def lib():
         L.oq_fm_halfwidth.restype = C.c_int
         L.oq_fm_halfwidth.argtypes = [C.c_double, C.c_double]
         L.oq_fm_average.argtypes = [C.POINTER(Model), _D, _D]
+        L.oq_sound_modes.argtypes = [C.POINTER(Model), C.c_double, C.c_double, C.c_double, _D]
         L.oq_rhs.argtypes = [C.POINTER(Model), _D, _D, _D, _D]
         L.oq_rk3_step.argtypes = [C.POINTER(Model), _D, _D]
         L.oq_run.argtypes = [C.POINTER(Model), _D, _D, C.c_long]
@@ -248,6 +249,13 @@ def fm_average(m: Model, n_ext):
     assert n_ext.shape == (m.nx + 6,)
     out = np.zeros_like(n_ext)
     lib().oq_fm_average(C.byref(m), _p(n_ext), _p(out))
+    return out
+
+
+def sound_modes(m: Model, rho: float, T: float, k: float):
+    """(c_s, alpha_a, alpha_a without bulk viscosity, alpha_t, gamma) of a sound wave of wave number k."""
+    out = np.zeros(5)
+    lib().oq_sound_modes(C.byref(m), rho, T, k, _p(out))
     return out
 
 

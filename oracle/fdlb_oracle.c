@@ -697,6 +697,43 @@ double oq_sound_speed2(double eta0, double rho_ref, double rho, double T)
     return P / rho + 2.0 * P * (1.0 + Y) / (3.0 * rho) + b * P * (chi + rho * dchi_drho) / (1.0 + Y);
 }
 
+/* ------------------------------------------------------------------------
+ * Sec. III.A (sound waves), Eqs. (sw_cs), (sw_coeff); READING c21: linear
+ * modes of a wave of wave number k on the uniform state (rho, T) of the model.
+ * The kinetic model carries
+ *   mu     = tau rho T                        (tau = mu / P_i, Sec. II.B),
+ *   lambda = (5/2) mu / Pr                    (Shakhov Prandtl number),
+ *   mu_v   = mu (16/(5 pi)) Y^2 / (1 + 0.8 Y + 4/25 (1 + 12/pi) Y^2),
+ *            the ratio of Eq. (bulk_viscosity) to Eq. (viscosity), Y = b rho chi;
+ * the equation of state P = rho T Z(eta), Z = 1 + 4 eta chi, gives
+ *   (dP/drho)_T = T (Z + eta dZ/deta), c_V = 3/2, gamma = c_s^2 / (dP/drho)_T,
+ *   c_P = gamma c_V, and
+ *   alpha_t = lambda k^2 / (rho c_P),
+ *   alpha_a = k^2 / (2 rho) [4 mu / 3 + mu_v + (gamma - 1) lambda / c_P].
+ * out = {c_s, alpha_a, alpha_a without mu_v, alpha_t, gamma}.
+ * ---------------------------------------------------------------------- */
+void oq_sound_modes(const oq_model *m, double rho, double T, double k, double *out)
+{
+    double eta = m->eta0 * rho / m->rho_ref;
+    double chi = oq_chi_set(eta);
+    double Y = 4.0 * eta * chi;
+    double dchi = (5.0 - 2.0 * eta) / (2.0 * pow(1.0 - eta, 4.0));
+    double Z = 1.0 + Y, dZ = 4.0 * chi + 4.0 * eta * dchi;
+    double Prho = T * (Z + eta * dZ);
+    double cs2 = oq_sound_speed2(m->eta0, m->rho_ref, rho, T);
+    double gamma = cs2 / Prho, cV = 1.5, cP = gamma * cV;
+    double tau = oq_tau(m, rho, T);
+    double mu = tau * rho * T;
+    double Pr = oq_prandtl(m, rho);
+    double lambda = 2.5 * mu / Pr;
+    double muv = mu * (16.0 / (5.0 * M_PI)) * Y * Y / (1.0 + 0.8 * Y + 4.0 / 25.0 * (1.0 + 12.0 / M_PI) * Y * Y);
+    out[0] = sqrt(cs2);
+    out[1] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + muv + (gamma - 1.0) * lambda / cP);
+    out[2] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + (gamma - 1.0) * lambda / cP);
+    out[3] = lambda * k * k / (rho * cP);
+    out[4] = gamma;
+}
+
 /* Pressure of the dense gas, P = rho T (1 + b rho chi), Sec. II.B. */
 static double oq_pressure(double eta0, double rho_ref, double rho, double T)
 {

@@ -71,11 +71,11 @@ cudaError_t QL_FN(launch_stage_)(int Q, int stage, const StageArgs &a, cudaStrea
 }
 
 // ---- batched stages
-template <int STAGE, int WARPS>
-static cudaError_t batch_sw(int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
+template <int Q, int STAGE, int WARPS>
+static cudaError_t batch_qsw(int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
 {
-    constexpr size_t smem = stage_smem_bytes<QL_REAL, kMaxQ, WARPS>();
-    auto kern = fdlb_batch_stage_kernel<QL_REAL, STAGE, WARPS>;
+    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, WARPS>();
+    auto kern = fdlb_batch_stage_kernel<QL_REAL, Q, STAGE, WARPS>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -89,29 +89,42 @@ static cudaError_t batch_sw(int grid, const BatchArgs &b, cudaStream_t s, bool q
     return cudaGetLastError();
 }
 
-template <int WARPS>
-static cudaError_t batch_w(int stage, int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
+template <int Q, int WARPS>
+static cudaError_t batch_qw(int stage, int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
 {
     switch (stage) {
-    case 1: return batch_sw<1, WARPS>(grid, b, s, query, ctas);
-    case 2: return batch_sw<2, WARPS>(grid, b, s, query, ctas);
-    case 3: return batch_sw<3, WARPS>(grid, b, s, query, ctas);
+    case 1: return batch_qsw<Q, 1, WARPS>(grid, b, s, query, ctas);
+    case 2: return batch_qsw<Q, 2, WARPS>(grid, b, s, query, ctas);
+    case 3: return batch_qsw<Q, 3, WARPS>(grid, b, s, query, ctas);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t QL_FN(launch_batch_stage_)(int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s)
+template <int WARPS>
+static cudaError_t batch_w(int Q, int stage, int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
 {
-    if (warps == 8) return batch_w<8>(stage, grid, b, s, false, nullptr);
-    if (warps == 4) return batch_w<4>(stage, grid, b, s, false, nullptr);
+    switch (Q) {
+    case 8: return batch_qw<8, WARPS>(stage, grid, b, s, query, ctas);
+    case 16: return batch_qw<16, WARPS>(stage, grid, b, s, query, ctas);
+    case 24: return batch_qw<24, WARPS>(stage, grid, b, s, query, ctas);
+    case 32: return batch_qw<32, WARPS>(stage, grid, b, s, query, ctas);
+    }
     return cudaErrorInvalidValue;
 }
 
+cudaError_t QL_FN(launch_batch_stage_)(int Q, int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s)
+{
+    if (warps == 8) return batch_w<8>(Q, stage, grid, b, s, false, nullptr);
+    if (warps == 4) return batch_w<4>(Q, stage, grid, b, s, false, nullptr);
+    return cudaErrorInvalidValue;
+}
+
+// Resident CTAs per SM of the largest velocity set's kernel (the most shared memory).
 int QL_FN(batch_ctas_per_sm_)(int stage, int warps)
 {
     int n = 0;
-    cudaError_t e = warps == 8 ? batch_w<8>(stage, 0, BatchArgs{}, nullptr, true, &n)
-                               : batch_w<4>(stage, 0, BatchArgs{}, nullptr, true, &n);
+    cudaError_t e = warps == 8 ? batch_w<8>(kMaxQ, stage, 0, BatchArgs{}, nullptr, true, &n)
+                               : batch_w<4>(kMaxQ, stage, 0, BatchArgs{}, nullptr, true, &n);
     return e == cudaSuccess ? n : 0;
 }
 

@@ -58,6 +58,13 @@ __device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
 }
 __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
+// Precision-exact overloads: float arguments stay in FP32 (FP64 runs at a
+// small fraction of the FP32 rate on this GPU).
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+
 template <typename Real>
 __device__ __forceinline__ Real rsqrt_(Real x);
 template <>
@@ -182,7 +189,7 @@ __device__ __forceinline__ P2<Real> weno5_face2(P2<Real> fm2, P2<Real> fm1, P2<R
     const V c1 = fma2(sp2(Real(1.0 / 30.0)), Dm2n, mul2(sp2(Real(1.0 / 12.0)), Dm1));
     const V c2 = fma2(sp2(Real(0.1)), Dm1, D0x);
     const V c3 = fma2(sp2(Real(-0.05)), D1, D0x);
-    const V sc = mk2(pow2_recip_(fmax(b1.x, fmax(b2.x, b3.x))), pow2_recip_(fmax(b1.y, fmax(b2.y, b3.y))));
+    const V sc = mk2(pow2_recip_(max_(b1.x, max_(b2.x, b3.x))), pow2_recip_(max_(b1.y, max_(b2.y, b3.y))));
     b1 = mul2(b1, sc);
     b2 = mul2(b2, sc);
     b3 = mul2(b3, sc);
@@ -258,12 +265,6 @@ constexpr uint32_t kMbarPolls = 1u << 22;
 // 1: stage the tile's rows with TMA bulk copies; 0: with 16-byte loads.
 #ifndef QL_STAGE_TMA
 #define QL_STAGE_TMA 1
-#endif
-
-// Velocity pairs ahead of the current one whose psi^n rows stages 2 and 3
-// prefetch into L2.
-#ifndef QL_PSIN_PREFETCH_AHEAD
-#define QL_PSIN_PREFETCH_AHEAD 1
 #endif
 
 // Sixth-order central difference of App. A.3 (times dx), centred on s.
@@ -411,8 +412,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
                 const V sm = add2(fa, fb), df = sub2(fa, fb);
                 s01 = add2(s01, sm);
                 s11 = fma2(sp2(p), df, s11);
-                s2 = fma(QL_TAB[TV.p2 + H + j], sm.x, s2);
-                s3 = fma(QL_TAB[TV.p3 + H + j], df.x, s3);
+                s2 = fma_(QL_TAB[TV.p2 + H + j], sm.x, s2);
+                s3 = fma_(QL_TAB[TV.p3 + H + j], df.x, s3);
             }
             if constexpr (kFF) {
                 // error-free accumulation: h takes the rounded sum, l its errors
@@ -454,7 +455,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             nf = Real(n);
         }
         // 2 q = sum xi^3 phi + sum xi theta = S3 + R1 - u (3 S2 + R0) + 2 u^2 S1
-        const Real q = Real(0.5) * (tS3 + tR1 - uf * fma(Real(3), tS2, tR0) + Real(2) * uf * uf * (uf * nf));
+        const Real q = Real(0.5) * (tS3 + tR1 - uf * fma_(Real(3), tS2, tR0) + Real(2) * uf * uf * (uf * nf));
         const int64_t i = i0 - kHalo + c;
         if (i >= 0 && i < a.nx) {
             if (!(nf > Real(0)) || !(Tf > Real(0)) || !isfinite(uf) || !isfinite(q) || !isfinite(nf) || !isfinite(Tf))
@@ -494,13 +495,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     const Real ome = Real(1) - eta;
     const Real chi = ret ? exp_(s_lnchi[s]) : Real(0.5) * (Real(2) - eta) / (ome * ome * ome);
     const Real Y = Real(4) * eta * chi;
-    const Real muf = fma(fma(Real(0.16 * (1.0 + 12.0 / 3.14159265358979323846)), Y, Real(0.8)), Y, Real(1));
+    const Real muf = fma_(fma_(Real(0.16 * (1.0 + 12.0 / 3.14159265358979323846)), Y, Real(0.8)), Y, Real(1));
     const Real sqT = T * rsqrt_(T);
     const Real inv_tau = rhat * chi * sqT / (Real(a.tau_pref) * muf);
     Real Pr = Real(a.pr_const);
     if (a.pr_mode) {
         const Real laf =
-            fma(fma(Real(0.36 * (1.0 + 32.0 / (9.0 * 3.14159265358979323846))), Y, Real(1.2)), Y, Real(1));
+            fma_(fma_(Real(0.36 * (1.0 + 32.0 / (9.0 * 3.14159265358979323846))), Y, Real(1.2)), Y, Real(1));
         Pr = Real(2.0 / 3.0) * muf / laf;
     }
     const Real invT = Real(1) / T;
@@ -517,11 +518,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     //   theta: (1/tau)(1 + A xi (xi^2/T - 1)) - Y [xi G + 3/5 (xi^2/T - 1/3) du + 3/10 (xi^3/T + 7 xi/3) dlnT]
     // times n g_k and 2 T n g_k; the pairs below hold (phi, theta) coefficients
     // already multiplied by n and 2 T n.
-    const Real a0 = fma(Real(0.6) * Yj, du, inv_tau);
+    const Real a0 = fma_(Real(0.6) * Yj, du, inv_tau);
     const Real a1 = -Real(3) * A * inv_tau - Yj * G - Real(0.1) * Yj * dlnT;
     const Real a2 = -Real(0.6) * Yj * du * invT;
     const Real a3 = (A * inv_tau - Real(0.3) * Yj * dlnT) * invT;
-    const Real b0 = fma(Real(0.2) * Yj, du, inv_tau);
+    const Real b0 = fma_(Real(0.2) * Yj, du, inv_tau);
     const Real b1 = -A * inv_tau - Yj * G - Real(0.7) * Yj * dlnT;
     const Real nphi = n, nth = Real(2) * T * n;
     const V C0 = mk2(a0 * nphi, b0 * nth), C1 = mk2(a1 * nphi, b1 * nth);
@@ -537,8 +538,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
         const Real Tm1 = T - Real(1);
 #pragma unroll
         for (int m = 1; m < H; ++m) {
-            const Real ce = fma(QL_TAB[TV.ca + 2 * m] * u, cm1, QL_TAB[TV.cb + 2 * m] * Tm1 * cm2);
-            const Real co = fma(QL_TAB[TV.ca + 2 * m + 1] * u, ce, QL_TAB[TV.cb + 2 * m + 1] * Tm1 * cm1);
+            const Real ce = fma_(QL_TAB[TV.ca + 2 * m] * u, cm1, QL_TAB[TV.cb + 2 * m] * Tm1 * cm2);
+            const Real co = fma_(QL_TAB[TV.ca + 2 * m + 1] * u, ce, QL_TAB[TV.cb + 2 * m + 1] * Tm1 * cm1);
             ch[m] = mk2(ce, co);
             cm2 = ce;
             cm1 = co;
@@ -555,28 +556,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     if (RET && STAGE != 0 && owner) s_nout[s] = Real(0);
 
     // psi^n rows of the tile's cells (columns kHalo + i0 .. kHalo + i0 + tile - 1,
-    // inside every row, whose stride leaves room for the staged segment): one
-    // thread prefetches the rows of pair j + QL_PSIN_PREFETCH_AHEAD into L2 while
-    // pair j is computed, so the loads of psi^n below hit L2.  The byte offsets
-    // are multiples of 16: stride is a multiple of 32 pairs, kHalo + i0 of 4 pairs
-    // (tile = 31 WARPS with WARPS a multiple of 4) and tile x sizeof(V) of 16.
-    constexpr int AHEAD = QL_PSIN_PREFETCH_AHEAD;
+    // inside every row, whose stride leaves room for the staged segment): before
+    // the velocity loop one thread asks the TMA unit to bring all of them into
+    // L2 (2 Q x tile pairs, 64 KB per CTA in FP32), so the loads of psi^n in the
+    // loop hit L2.  Byte offsets are multiples of 16: stride is even, kHalo + i0
+    // a multiple of 4 pairs, tile x sizeof(V) a multiple of 16.
     constexpr uint32_t kRowBytes = uint32_t(TileShape<WARPS>::tile * sizeof(V));
-    static_assert(kRowBytes % 16 == 0 && (TileShape<WARPS>::tile * sizeof(V)) % 16 == 0, "bulk prefetch size");
-    if (STAGE >= 2 && AHEAD > 0 && t == 0) {
-        for (int j = 0; j < AHEAD && j < H; ++j) {
-            prefetch_l2_bulk(base + int64_t(H + j) * stride + kHalo + i0, kRowBytes);
-            prefetch_l2_bulk(base + int64_t(H - 1 - j) * stride + kHalo + i0, kRowBytes);
-        }
-    }
+    static_assert(kRowBytes % 16 == 0, "bulk prefetch size");
+    if (STAGE >= 2 && t == 0)
+        for (int r = 0; r < Q; ++r) prefetch_l2_bulk(base + int64_t(r) * stride + kHalo + i0, kRowBytes);
 
 #pragma unroll 1
     for (int j = 0; j < H; ++j) {
         const int kp = H + j, km = H - 1 - j;
-        if (STAGE >= 2 && AHEAD > 0 && t == 0 && j + AHEAD < H) {
-            prefetch_l2_bulk(base + int64_t(H + j + AHEAD) * stride + kHalo + i0, kRowBytes);
-            prefetch_l2_bulk(base + int64_t(H - 1 - j - AHEAD) * stride + kHalo + i0, kRowBytes);
-        }
+
         const int64_t ip = int64_t(kp) * stride + col, im = int64_t(km) * stride + col;
         // psi^n of this cell, loaded before the arithmetic that hides its latency
         // (every lane's column lies inside the row: ghost or padding columns at worst)
@@ -665,16 +658,16 @@ __global__ void __launch_bounds__(kThreads, StageOccupancy<Real>::value) fdlb_st
     stage_tile<Real, Q, STAGE, kWarps, RET>(a, int64_t(blockIdx.x) * kTile, smem_raw, &mbar, 0u);
 }
 
-// Batched form: one persistent launch per Runge-Kutta stage over a work list
-// of (instance, tile) items of many independent domains with their own size,
-// velocity set and gas parameters.  Each CTA walks the list with stride
-// gridDim.x.
+// Batched form: per Runge-Kutta stage, one persistent launch per velocity set
+// over the work list of (instance, tile) items of the instances with that Q
+// (independent domains with their own size and gas parameters).  Each CTA
+// walks the list with stride gridDim.x.
 template <int WARPS>
 struct BatchOccupancy {
     static constexpr int value = WARPS == 8 ? QL_STAGE_MINBLOCKS_F32 : 2 * QL_STAGE_MINBLOCKS_F32 - 1;
 };
 
-template <typename Real, int STAGE, int WARPS>
+template <typename Real, int Q, int STAGE, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy<WARPS>::value : 1)
     fdlb_batch_stage_kernel(BatchArgs b)
 {
@@ -712,13 +705,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
         a.nbar = nullptr;  // instances use chi_SET
         a.nout = nullptr;
         const int64_t i0 = int64_t(it.y) * TileShape<WARPS>::tile;
-        switch (I.Q) {
-        case 8: stage_tile<Real, 8, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
-        case 16: stage_tile<Real, 16, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
-        case 24: stage_tile<Real, 24, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
-        case 32: stage_tile<Real, 32, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase); break;
-        default: break;
-        }
+        stage_tile<Real, Q, STAGE, WARPS>(a, i0, smem_raw, &mbar, phase);  // every item of this list has this Q
         __syncthreads();  // shared memory is reused by the next item
     }
 }
@@ -822,7 +809,7 @@ __global__ void __launch_bounds__(kFmThreads) fdlb_fm_kernel(FmArgs a)
     const int64_t col = c0 + threadIdx.x;
     if (col >= a.nx + 2 * kHalo) return;
     Real acc = Real(0);
-    for (int d = 0; d <= 2 * a.W; ++d) acc = fma(s_K[d], s_n[threadIdx.x + d], acc);
+    for (int d = 0; d <= 2 * a.W; ++d) acc = fma_(s_K[d], s_n[threadIdx.x + d], acc);
     static_cast<Real *>(a.nbar)[col] = acc;
 }
 

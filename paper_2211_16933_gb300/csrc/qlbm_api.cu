@@ -570,6 +570,14 @@ double ql_sound_speed2(double eta0, double rho_ref, double rho, double T)
     return sound_speed2(eta0, rho_ref, rho, T);
 }
 
+ql_status ql_sound_modes(double denseness, double kn, double length, double rho_ref, int32_t pr_mode,
+                         double pr_const, double rho, double T, double k, double *out)
+{
+    if (!out || !sound_modes(denseness, kn, length, rho_ref, pr_mode, pr_const, rho, T, k, out))
+        return fail(nullptr, QL_EINVAL, "bad arguments to ql_sound_modes");
+    return QL_OK;
+}
+
 ql_status ql_rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach, double *out)
 {
     if (!out || !rankine_hugoniot(eta0, rho_ref, rho1, T1, mach, out))

@@ -30,6 +30,8 @@ struct ql_batch {
     BatchInstance *d_inst = nullptr;
     int2 *d_work[2] = {nullptr, nullptr};  // work lists for kBatchWarps[0], kBatchWarps[1]
     int64_t nwork[2] = {0, 0};
+    // each list holds the items of the instances with Q = kQList[g] at [qstart, qstart + qcount)
+    int64_t qstart[2][kNumQ] = {}, qcount[2][kNumQ] = {};
     void *arena[3] = {nullptr, nullptr, nullptr};
     size_t arena_bytes = 0;
     unsigned *d_err = nullptr;
@@ -90,17 +92,24 @@ static void batch_release(ql_batch *b)
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
+// One Runge-Kutta stage of every instance: a launch per velocity set present.
 static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
 {
-    BatchArgs a;
-    a.inst = b->d_inst;
     const int wi = warps == kBatchWarps[0] ? 0 : 1;
-    a.work = b->d_work[wi];
-    a.nwork = b->nwork[wi];
-    for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
-    a.err = b->d_err;
-    return b->precision == QL_FP32 ? launch_batch_stage_f32(stage, warps, grid, a, b->stream)
-                                   : launch_batch_stage_f64(stage, warps, grid, a, b->stream);
+    for (int g = 0; g < kNumQ; ++g) {
+        if (b->qcount[wi][g] == 0) continue;
+        BatchArgs a;
+        a.inst = b->d_inst;
+        a.work = b->d_work[wi] + b->qstart[wi][g];
+        a.nwork = b->qcount[wi][g];
+        for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
+        a.err = b->d_err;
+        const cudaError_t e = b->precision == QL_FP32
+                                  ? launch_batch_stage_f32(kQList[g], stage, warps, grid, a, b->stream)
+                                  : launch_batch_stage_f64(kQList[g], stage, warps, grid, a, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Fields of every instance averaged over blocks of nx/ncoarse cells:
@@ -147,6 +156,37 @@ __global__ void batch_fields_kernel(const BatchInstance *__restrict__ inst, cons
         acc[4] += c2;
     }
     for (int q = 0; q < 5; ++q) out[(int64_t(i) * 5 + q) * ncoarse + c] = acc[q] / double(f);
+}
+
+// Sec. III.A: amplitude of density mode m of every instance,
+//   out[i] = (2 / nx) sum_j rho_j cos(2 pi m x_j / L),  x_j = (j + 1/2) L / nx,
+// with rho_j = sum_k phi_k.  One block per instance, FP64 sums, fixed-order
+// tree reduction.
+constexpr int kProjThreads = 256;
+template <typename Real>
+__global__ void __launch_bounds__(kProjThreads) batch_project_kernel(const BatchInstance *__restrict__ inst,
+                                                                     const void *__restrict__ arena, int mode,
+                                                                     double *__restrict__ out)
+{
+    using V = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+    __shared__ double red[kProjThreads];
+    const int i = blockIdx.x;
+    const BatchInstance I = inst[i];
+    const V *psi = static_cast<const V *>(arena) + I.off;
+    const double w = 2.0 * 3.14159265358979323846 * double(mode) / double(I.nx);
+    double acc = 0.0;
+    for (int64_t c = threadIdx.x; c < I.nx; c += kProjThreads) {
+        double rho = 0.0;
+        for (int k = 0; k < I.Q; ++k) rho += double(psi[int64_t(k) * I.stride + kHalo + c].x);
+        acc += rho * cos(w * (double(c) + 0.5));
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kProjThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = 2.0 * red[0] / double(I.nx);
 }
 
 static int ctas_per_sm(ql_batch *b, int warps)
@@ -222,13 +262,19 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
                             fields[i].data() + 2 * ncol))
             return bail(QL_EINVAL, id + "invalid initial state for this init kind / boundary");
     }
-    // work lists: all tiles of instance 0, then instance 1, ...
+    // work lists, grouped by velocity set: all tiles of the first instance with
+    // Q = kQList[0], then of the next one, ..., then the instances with kQList[1], ...
     std::vector<int2> work[2];
     for (int wi = 0; wi < 2; ++wi) {
         const int tile = 31 * kBatchWarps[wi];
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t nt = (b->inst[i].nx + tile - 1) / tile;
-            for (int64_t t = 0; t < nt; ++t) work[wi].push_back(make_int2(int(i), int(t)));
+        for (int g = 0; g < kNumQ; ++g) {
+            b->qstart[wi][g] = int64_t(work[wi].size());
+            for (int64_t i = 0; i < n; ++i) {
+                if (b->inst[i].Q != kQList[g]) continue;
+                const int64_t nt = (b->inst[i].nx + tile - 1) / tile;
+                for (int64_t t = 0; t < nt; ++t) work[wi].push_back(make_int2(int(i), int(t)));
+            }
+            b->qcount[wi][g] = int64_t(work[wi].size()) - b->qstart[wi][g];
         }
         b->nwork[wi] = int64_t(work[wi].size());
     }
@@ -430,6 +476,17 @@ ql_status ql_batch_fields(ql_batch *b, int32_t ncoarse, double *out)
         batch_fields_kernel<float><<<grid, 128, 0, b->stream>>>(b->d_inst, b->arena[0], b->d_tab64, ncoarse, out);
     else
         batch_fields_kernel<double><<<grid, 128, 0, b->stream>>>(b->d_inst, b->arena[0], b->d_tab64, ncoarse, out);
+    QB_CUDA(b, cudaGetLastError());
+    return QL_OK;
+}
+
+ql_status ql_batch_project(ql_batch *b, int32_t mode, double *out)
+{
+    if (!b || !out || mode < 0) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_project");
+    if (b->precision == QL_FP32)
+        batch_project_kernel<float><<<unsigned(b->n), kProjThreads, 0, b->stream>>>(b->d_inst, b->arena[0], mode, out);
+    else
+        batch_project_kernel<double><<<unsigned(b->n), kProjThreads, 0, b->stream>>>(b->d_inst, b->arena[0], mode, out);
     QB_CUDA(b, cudaGetLastError());
     return QL_OK;
 }

@@ -146,6 +146,33 @@ double sound_speed2(double eta0, double rho_ref, double rho, double T)
     return T * (Z + eta * cs_dz(eta)) + (2.0 / 3.0) * T * Z * Z;
 }
 
+bool sound_modes(double denseness, double kn, double length, double rho_ref, int pr_mode, double pr_const,
+                 double rho, double T, double k, double *out)
+{
+    double eta0;
+    if (!eta_of_denseness(denseness, &eta0) || !(rho > 0) || !(T > 0) || !(kn > 0) || !(length > 0)) return false;
+    const double pi = kPi;
+    // tau = (5 sqrt(2 pi)/16) Kn L chi0 / (rho^ chi sqrt T) (1 + 0.8 Y + 4/25 (1 + 12/pi) Y^2)
+    const double eta = eta0 * rho / rho_ref, chi = chi_set(eta), Y = 4.0 * eta * chi;
+    const double muf = 1.0 + 0.8 * Y + 0.16 * (1.0 + 12.0 / pi) * Y * Y;
+    const double laf = 1.0 + 1.2 * Y + 0.36 * (1.0 + 32.0 / (9.0 * pi)) * Y * Y;
+    const double tau = 5.0 * sqrt(2.0 * pi) / 16.0 * kn * length * chi_set(eta0) * muf / (rho / rho_ref * chi * sqrt(T));
+    const double mu = tau * rho * T;                       // kinetic model: mu = tau P_i
+    const double Pr = pr_mode == 1 ? (2.0 / 3.0) * muf / laf : pr_const;
+    const double lambda = 2.5 * mu / Pr;                   // Shakhov: Pr = c_P mu / lambda, c_P = 5/2
+    const double muv = mu * (16.0 / (5.0 * pi)) * Y * Y / muf;  // Eq. (bulk_viscosity) / Eq. (viscosity)
+    // thermodynamics of P = rho T Z(eta): c_s^2 = (dP/drho)_T + T (dP/dT)^2 / (rho^2 c_V)
+    const double Z = cs_z(eta), Prho = T * (Z + eta * cs_dz(eta)), PT = rho * Z, cV = 1.5;
+    const double cs2 = Prho + T * PT * PT / (rho * rho * cV);
+    const double gamma = cs2 / Prho, cP = gamma * cV;
+    out[0] = sqrt(cs2);
+    out[1] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + muv + (gamma - 1.0) * lambda / cP);
+    out[2] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + (gamma - 1.0) * lambda / cP);
+    out[3] = lambda * k * k / (rho * cP);
+    out[4] = gamma;
+    return true;
+}
+
 // Energy balance per unit mass flux across a standing shock, for a trial
 // downstream density; mass and momentum balance give u2 and P2.
 static double rh_residual(double eta0, double rho_ref, double rho1, double u1, double T1, double rho2,

@@ -23,6 +23,12 @@ bool eta_of_denseness(double El, double *eta);
 // c_s^2 = T (Z + eta Z') + (2/3) T Z^2, eta = eta0 rho / rho_ref.
 double sound_speed2(double eta0, double rho_ref, double rho, double T);
 
+// Sec. III.A, Eqs. (sw_cs), (sw_coeff): linear modes of a sound wave of wave
+// number k on the uniform state (rho, T) of the model with these parameters.
+// out = {c_s, alpha_a, alpha_a without bulk viscosity, alpha_t, gamma}.
+bool sound_modes(double denseness, double kn, double length, double rho_ref, int pr_mode, double pr_const,
+                 double rho, double T, double k, double *out);
+
 // Eq. (rankine_hugoniot) for a standing shock.  out = {u1, rho2, u2, T2}.
 bool rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach, double *out);
 

@@ -151,8 +151,9 @@ constexpr int kMomThreads = 256;
 inline int64_t moment_blocks(int64_t nx) { return (nx + kMomThreads - 1) / kMomThreads; }
 // One batched stage over the work list: `grid` persistent CTAs of `warps`
 // warps (8 or 4; the work list must be built for the same tile width).
-cudaError_t launch_batch_stage_f32(int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
-cudaError_t launch_batch_stage_f64(int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
+// One launch over the work items of the instances with velocity-set size Q.
+cudaError_t launch_batch_stage_f32(int Q, int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
+cudaError_t launch_batch_stage_f64(int Q, int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
 // Resident CTAs per SM of the batched kernel (occupancy calculator).
 int batch_ctas_per_sm_f32(int stage, int warps);
 int batch_ctas_per_sm_f64(int stage, int warps);

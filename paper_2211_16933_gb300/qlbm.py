@@ -28,7 +28,7 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error",
             "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
             "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc",
-            "ql_batch_fields", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
+            "ql_batch_fields", "ql_batch_project", "ql_sound_modes", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
             "ql_closure_train_step", "ql_closure_params", "ql_closure_destroy", "ql_closure_last_error")
 
 
@@ -125,6 +125,8 @@ def lib():
         L.ql_step_noalloc.argtypes = [C.POINTER(ql_velset), C.POINTER(ql_grid), C.c_double, C.c_double,
                                       C.POINTER(ql_bc), C.POINTER(ql_opts), V, C.c_int64, C.c_int64]
         L.ql_batch_fields.argtypes = [V, C.c_int32, V]
+        L.ql_batch_project.argtypes = [V, C.c_int32, V]
+        L.ql_sound_modes.argtypes = [C.c_double] * 4 + [C.c_int32] + [C.c_double] * 4 + [_DP]
         F = C.POINTER(C.c_float)
         L.ql_closure_create.argtypes = [C.POINTER(ql_closure_desc), C.POINTER(ql_opts), C.POINTER(V)]
         L.ql_closure_forward.argtypes = [V, V, V, C.c_int64, V]
@@ -288,6 +290,17 @@ def ql_batch_fields(b, ncoarse, out_ptr):
     _bcheck(lib().ql_batch_fields(b, ncoarse, C.c_void_p(out_ptr)), b)
 
 
+def ql_batch_project(b, mode, out_ptr):
+    _bcheck(lib().ql_batch_project(b, mode, C.c_void_p(out_ptr)), b)
+
+
+def ql_sound_modes(denseness, kn, length, rho, T, k, rho_ref=1.0, pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0):
+    """(c_s, alpha_a, alpha_a without bulk viscosity, alpha_t, gamma) of a sound wave, Eqs. sw_cs / sw_coeff."""
+    out = np.zeros(5)
+    _check(lib().ql_sound_modes(denseness, kn, length, rho_ref, pr_mode, pr_const, rho, T, k, _ptr(out)))
+    return out
+
+
 def make_instance(Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND, prm=(),
                   pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, keep=None, rho=None, u=None, T=None,
                   ghost=None):
@@ -359,6 +372,10 @@ class Batch:
     def fields(self, ncoarse, out):
         """out: a device tensor of n * 5 * ncoarse float64 (its data pointer is passed)."""
         ql_batch_fields(self.b, ncoarse, out.data_ptr())
+
+    def project(self, mode, out):
+        """Density mode amplitudes of all instances into a device tensor of n float64."""
+        ql_batch_project(self.b, mode, out.data_ptr())
 
     def close(self):
         if getattr(self, "b", None) is not None:

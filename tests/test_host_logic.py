@@ -88,6 +88,19 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
     assert e.value.status in (q.QL_EINVAL, q.QL_ECUDA)
 
 
+@pytest.mark.parametrize("El,kn,pr_mode", [(0.01, 1e-3, 1), (0.4825, 0.05, 1), (6.3, 0.005, 1), (1.1, 0.01, 0)])
+def test_sound_modes_match_oracle(qlbm_lib, El, kn, pr_mode):
+    """ql_sound_modes (c_s from the thermodynamic identity, tau from its closed form) against the oracle
+    (c_s from the printed formula, tau = mu / P_i); both pinned through their parts."""
+    import math
+    q = qlbm_lib
+    m = O.make_model(16, 64, 1.0, 1e-3, El, kn, pr_mode=pr_mode, pr_const=0.7)
+    for rho, T in ((1.0, 1.0), (0.6, 1.4)):
+        a = O.sound_modes(m, rho, T, 2 * math.pi)
+        b = q.ql_sound_modes(El, kn, 1.0, rho, T, 2 * math.pi, pr_mode=pr_mode, pr_const=0.7)
+        np.testing.assert_allclose(b, a, rtol=1e-13)
+
+
 def test_chi_ret_fm_options_are_checked_before_touching_the_gpu(qlbm_lib):
     """chi_mode must be SET or RET-FM, and a chi_RET-FM ball reaching more than QL_FM_MAX_HALFWIDTH cells is
     unsupported; ql_step_noalloc takes chi_SET only."""

@@ -41,6 +41,8 @@ MUTATIONS = {
     "fm_periodic_wrap": ("src = ((i % nx) + nx) % nx + OQ_NG;", "src = ((i % nx) + nx) % nx;"),
     "ret_dlnchi": ("double dlnchi = m->chi_mode == 1 ? oq_cd6(lnchi + j - 3, m->dx)", "double dlnchi = m->chi_mode == 1 ? 0.5 * oq_cd6(lnchi + j - 3, m->dx)"),
     "ret_tau_local_chi": ("double tau = oq_tau_chi(m, n, chi, T);", "double tau = oq_tau(m, n, T);"),
+    "sound_alpha_a_gamma": ("out[1] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + muv + (gamma - 1.0) * lambda / cP);", "out[1] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + muv + gamma * lambda / cP);"),
+    "sound_alpha_t_cp": ("out[3] = lambda * k * k / (rho * cP);", "out[3] = lambda * k * k / (rho * cV);"),
     "ret_prandtl_local_chi": ("double Pr = m->pr_mode == 0 ? m->pr_const : oq_prandtl_dense(Y);", "double Pr = oq_prandtl(m, n);"),
 }
 

@@ -608,3 +608,41 @@ def test_ret_fm_conserves_mass_and_is_mirror_symmetric():
     Lpr, Ltr = O.rhs(m, ph[::-1, ::-1].copy(), th[::-1, ::-1].copy())
     np.testing.assert_allclose(Lpr, Lp[::-1, ::-1], rtol=1e-9, atol=1e-13)
     np.testing.assert_allclose(Ltr, Lt[::-1, ::-1], rtol=1e-9, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Sound-wave modes (Eqs. sw_cs, sw_coeff)
+
+
+@pytest.mark.parametrize("El", [0.01, 0.4825, 1.917, 6.3])
+def test_sound_modes_are_the_small_k_roots_of_the_linear_hydrodynamic_equations(El):
+    """The closed forms for c_s, alpha_a and alpha_t agree with the roots of the secular cubic of the
+    linearised mass, momentum and energy equations with the same coefficients (perturbations exp(ikx - alpha t))
+    to O((k l)^2); the roots are found by numpy's polynomial solver."""
+    m = O.make_model(16, 64, 1.0, 1e-3, El, 1e-3)
+    rho, T, k = 1.0, 1.0, 2 * math.pi
+    cs, aa, aa0, at, gamma = O.sound_modes(m, rho, T, k)
+    # coefficients of the linear equations, from the same model pieces
+    eta = m.eta0 * rho
+    chi = O.chi_set(eta)
+    Y = 4 * eta * chi
+    dchi = (5 - 2 * eta) / (2 * (1 - eta) ** 4)
+    Z, dZ = 1 + Y, 4 * chi + 4 * eta * dchi
+    Prho, PT = T * (Z + eta * dZ), rho * Z
+    mu = O.tau(m, rho, T) * rho * T
+    lam = 2.5 * mu / O.prandtl(m, rho)
+    muv = mu * 16 / (5 * math.pi) * Y * Y / (1 + 0.8 * Y + 0.16 * (1 + 12 / math.pi) * Y * Y)
+    D, cV = 4 * mu / 3 + muv, 1.5
+    a, c = rho, rho * cV
+    coeffs = [-a * c, k * k * (a * lam + c * D), -(k ** 4 * D * lam + k * k * T * PT ** 2 + k * k * rho * Prho * c),
+              k ** 4 * rho * Prho * lam]
+    roots = np.roots(coeffs)
+    real = roots[np.abs(roots.imag) < 1e-12 * np.abs(roots).max()].real
+    cplx = roots[roots.imag > 0][0]
+    kl = k * mu / (rho * cs)  # k times a viscous length
+    assert abs(cplx.imag - k * cs) <= 2 * kl ** 2 * k * cs
+    assert abs(cplx.real - aa) <= 2 * kl ** 2 * aa
+    assert abs(real[0] - at) <= 2 * kl ** 2 * at
+    # the thermodynamic identity c_s^2 = gamma (dP/drho)_T with c_P - c_V = T PT^2 / (rho^2 Prho)
+    assert gamma * cV - cV == pytest.approx(T * PT ** 2 / (rho ** 2 * Prho), rel=1e-12)
+    assert aa >= aa0 and (aa - aa0) / aa < (0.5 if El > 1 else 0.05)
