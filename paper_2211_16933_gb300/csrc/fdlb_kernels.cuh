@@ -304,6 +304,12 @@ constexpr size_t stage_smem_bytes()
 #endif
 constexpr int kStageLoadUnroll = QL_STAGE_LOAD_UNROLL;
 
+// Velocity pairs of the update loop per iteration.
+#ifndef QL_VLOOP_UNROLL
+#define QL_VLOOP_UNROLL 1
+#endif
+constexpr int kVelocityLoopUnroll = QL_VLOOP_UNROLL;
+
 // Resident CTAs per SM the FP32 stage kernels are compiled for (8-warp tiles;
 // the register budget follows from it).
 #ifndef QL_STAGE_MINBLOCKS_F32
@@ -566,7 +572,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     if (STAGE >= 2 && t == 0)
         for (int r = 0; r < Q; ++r) prefetch_l2_bulk(base + int64_t(r) * stride + kHalo + i0, kRowBytes);
 
-#pragma unroll 1
+#pragma unroll kVelocityLoopUnroll
     for (int j = 0; j < H; ++j) {
         const int kp = H + j, km = H - 1 - j;
 

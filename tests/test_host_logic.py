@@ -101,6 +101,20 @@ def test_sound_modes_match_oracle(qlbm_lib, El, kn, pr_mode):
         np.testing.assert_allclose(b, a, rtol=1e-13)
 
 
+def test_sound_modes_and_projection_reject_bad_arguments(qlbm_lib):
+    q = qlbm_lib
+    import math
+    for bad in (dict(denseness=-1.0), dict(denseness=50.0), dict(kn=0.0), dict(rho=-1.0), dict(T=0.0)):
+        args = dict(denseness=0.1, kn=0.01, length=1.0, rho=1.0, T=1.0, k=2 * math.pi)
+        args.update(bad)
+        with pytest.raises(q.QLError) as e:
+            q.ql_sound_modes(**args)
+        assert e.value.status == q.QL_EINVAL
+    # a null batch is rejected before any device work
+    st = q.lib().ql_batch_project(None, 1, None)
+    assert st == q.QL_EINVAL
+
+
 def test_chi_ret_fm_options_are_checked_before_touching_the_gpu(qlbm_lib):
     """chi_mode must be SET or RET-FM, and a chi_RET-FM ball reaching more than QL_FM_MAX_HALFWIDTH cells is
     unsupported; ql_step_noalloc takes chi_SET only."""
