@@ -63,7 +63,8 @@ enum { QL_CHI_SET = 0, QL_CHI_RET_FM = 1 };
 
 /* Velocity set, Sec. II.D: the Q roots p_k of the probabilists' Hermite
  * polynomial He_Q with weights w_k = Q!/He_{Q+1}(p_k)^2 (kind 0 is the only
- * kind).  This build has kernels for Q in {8, 16, 24, 32}. */
+ * kind).  This build has kernels for Q in {8, 16, 20, 24, 32, 40} (the batched
+ * form: {8, 16, 24, 32}). */
 typedef struct {
     int32_t Q;
     int32_t kind;

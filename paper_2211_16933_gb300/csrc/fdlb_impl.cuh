@@ -64,8 +64,10 @@ cudaError_t QL_FN(launch_stage_)(int Q, int stage, const StageArgs &a, cudaStrea
     switch (Q) {
     case 8: return stage_dispatch<8>(stage, a, s);
     case 16: return stage_dispatch<16>(stage, a, s);
+    case 20: return stage_dispatch<20>(stage, a, s);
     case 24: return stage_dispatch<24>(stage, a, s);
     case 32: return stage_dispatch<32>(stage, a, s);
+    case 40: return stage_dispatch<40>(stage, a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -123,8 +125,8 @@ cudaError_t QL_FN(launch_batch_stage_)(int Q, int stage, int warps, int grid, co
 int QL_FN(batch_ctas_per_sm_)(int stage, int warps)
 {
     int n = 0;
-    cudaError_t e = warps == 8 ? batch_w<8>(kMaxQ, stage, 0, BatchArgs{}, nullptr, true, &n)
-                               : batch_w<4>(kMaxQ, stage, 0, BatchArgs{}, nullptr, true, &n);
+    cudaError_t e = warps == 8 ? batch_w<8>(kBatchMaxQ, stage, 0, BatchArgs{}, nullptr, true, &n)
+                               : batch_w<4>(kBatchMaxQ, stage, 0, BatchArgs{}, nullptr, true, &n);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -137,8 +139,10 @@ cudaError_t QL_FN(launch_init_)(int Q, const double *rho, const double *u, const
     switch (Q) {
     case 8: fdlb_init_kernel<QL_REAL, 8><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
     case 16: fdlb_init_kernel<QL_REAL, 16><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
+    case 20: fdlb_init_kernel<QL_REAL, 20><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
     case 24: fdlb_init_kernel<QL_REAL, 24><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
     case 32: fdlb_init_kernel<QL_REAL, 32><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
+    case 40: fdlb_init_kernel<QL_REAL, 40><<<blocks, 256, 0, s>>>(rho, u, T, p, nx, stride, tab64); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -159,8 +163,10 @@ cudaError_t QL_FN(launch_density_)(int Q, const void *psi, int64_t nx, int64_t s
     switch (Q) {
     case 8: fdlb_density_kernel<QL_REAL, 8><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
     case 16: fdlb_density_kernel<QL_REAL, 16><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
+    case 20: fdlb_density_kernel<QL_REAL, 20><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
     case 24: fdlb_density_kernel<QL_REAL, 24><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
     case 32: fdlb_density_kernel<QL_REAL, 32><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
+    case 40: fdlb_density_kernel<QL_REAL, 40><<<blocks, 256, 0, s>>>(p, nx, stride, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -183,8 +189,10 @@ cudaError_t QL_FN(launch_moments_)(int Q, const MomentArgs &a, const double *tab
             switch (Q) {
             case 8: fdlb_totals_f32_kernel<8><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
             case 16: fdlb_totals_f32_kernel<16><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+            case 20: fdlb_totals_f32_kernel<20><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
             case 24: fdlb_totals_f32_kernel<24><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
             case 32: fdlb_totals_f32_kernel<32><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+            case 40: fdlb_totals_f32_kernel<40><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
             default: return cudaErrorInvalidValue;
             }
             return cudaGetLastError();
@@ -193,8 +201,10 @@ cudaError_t QL_FN(launch_moments_)(int Q, const MomentArgs &a, const double *tab
     switch (Q) {
     case 8: fdlb_moments_kernel<QL_REAL, 8><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
     case 16: fdlb_moments_kernel<QL_REAL, 16><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+    case 20: fdlb_moments_kernel<QL_REAL, 20><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
     case 24: fdlb_moments_kernel<QL_REAL, 24><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
     case 32: fdlb_moments_kernel<QL_REAL, 32><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
+    case 40: fdlb_moments_kernel<QL_REAL, 40><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

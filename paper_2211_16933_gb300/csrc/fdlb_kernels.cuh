@@ -306,7 +306,7 @@ constexpr int kStageLoadUnroll = QL_STAGE_LOAD_UNROLL;
 
 // Velocity pairs of the update loop per iteration.
 #ifndef QL_VLOOP_UNROLL
-#define QL_VLOOP_UNROLL 1
+#define QL_VLOOP_UNROLL 2
 #endif
 constexpr int kVelocityLoopUnroll = QL_VLOOP_UNROLL;
 
@@ -646,14 +646,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     if (RET && STAGE != 0 && owner) static_cast<Real *>(a.nout)[i] = s_nout[s];
 }
 
-template <typename Real>
+// FP32: QL_STAGE_MINBLOCKS_F32 CTAs per SM up to Q = 32; Q = 40 holds twice the
+// Hermite coefficients and 80 KB of staged rows, and runs 2 CTAs per SM.
+template <typename Real, int Q>
 struct StageOccupancy {
-    static constexpr int value = sizeof(Real) == 4 ? QL_STAGE_MINBLOCKS_F32 : 1;
+    static constexpr int value = sizeof(Real) == 4 ? (Q > 32 ? 2 : QL_STAGE_MINBLOCKS_F32) : 1;
 };
 
 // One Runge-Kutta stage over a whole domain: CTA b updates tile b.
 template <typename Real, int Q, int STAGE, bool RET>
-__global__ void __launch_bounds__(kThreads, StageOccupancy<Real>::value) fdlb_stage_kernel(StageArgs a)
+__global__ void __launch_bounds__(kThreads, StageOccupancy<Real, Q>::value) fdlb_stage_kernel(StageArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;

@@ -191,7 +191,7 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     bool qok = false;
     for (int j = 0; j < kNumQ; ++j) qok |= vs->Q == kQList[j];
     if (vs->kind != 0) return fail(nullptr, QL_EINVAL, "velocity set kind must be 0 (Gauss-Hermite)");
-    if (!qok) return fail(nullptr, QL_EUNSUPPORTED, "Q must be one of 8, 16, 24, 32");
+    if (!qok) return fail(nullptr, QL_EUNSUPPORTED, "Q must be one of 8, 16, 20, 24, 32, 40");
     if (grid->nx < 8 || grid->nx > (int64_t(1) << 31)) return fail(nullptr, QL_EINVAL, "nx must be in [8, 2^31]");
     if (!(grid->length > 0) || !(grid->dt > 0)) return fail(nullptr, QL_EINVAL, "length and dt must be > 0");
     if (!(denseness > 0) || !(kn > 0)) return fail(nullptr, QL_EINVAL, "denseness and kn must be > 0");

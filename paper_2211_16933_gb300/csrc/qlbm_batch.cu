@@ -30,8 +30,8 @@ struct ql_batch {
     BatchInstance *d_inst = nullptr;
     int2 *d_work[2] = {nullptr, nullptr};  // work lists for kBatchWarps[0], kBatchWarps[1]
     int64_t nwork[2] = {0, 0};
-    // each list holds the items of the instances with Q = kQList[g] at [qstart, qstart + qcount)
-    int64_t qstart[2][kNumQ] = {}, qcount[2][kNumQ] = {};
+    // each list holds the items of the instances with Q = kBatchQList[g] at [qstart, qstart + qcount)
+    int64_t qstart[2][kNumBatchQ] = {}, qcount[2][kNumBatchQ] = {};
     void *arena[3] = {nullptr, nullptr, nullptr};
     size_t arena_bytes = 0;
     unsigned *d_err = nullptr;
@@ -96,7 +96,7 @@ static void batch_release(ql_batch *b)
 static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
 {
     const int wi = warps == kBatchWarps[0] ? 0 : 1;
-    for (int g = 0; g < kNumQ; ++g) {
+    for (int g = 0; g < kNumBatchQ; ++g) {
         if (b->qcount[wi][g] == 0) continue;
         BatchArgs a;
         a.inst = b->d_inst;
@@ -105,8 +105,8 @@ static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
         for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
         a.err = b->d_err;
         const cudaError_t e = b->precision == QL_FP32
-                                  ? launch_batch_stage_f32(kQList[g], stage, warps, grid, a, b->stream)
-                                  : launch_batch_stage_f64(kQList[g], stage, warps, grid, a, b->stream);
+                                  ? launch_batch_stage_f32(kBatchQList[g], stage, warps, grid, a, b->stream)
+                                  : launch_batch_stage_f64(kBatchQList[g], stage, warps, grid, a, b->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -228,7 +228,7 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
     for (int64_t i = 0; i < n; ++i) {
         const ql_instance &I = in[i];
         bool qok = false;
-        for (int j = 0; j < kNumQ; ++j) qok |= I.vs.Q == kQList[j];
+        for (int j = 0; j < kNumBatchQ; ++j) qok |= I.vs.Q == kBatchQList[j];
         const std::string id = "instance " + std::to_string(i) + ": ";
         if (!qok || I.vs.kind != 0) return bail(QL_EUNSUPPORTED, id + "Q must be one of 8, 16, 24, 32");
         if (I.grid.nx < 8 || I.grid.nx > (int64_t(1) << 31) || !(I.grid.length > 0) || !(I.grid.dt > 0))
@@ -263,14 +263,14 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
             return bail(QL_EINVAL, id + "invalid initial state for this init kind / boundary");
     }
     // work lists, grouped by velocity set: all tiles of the first instance with
-    // Q = kQList[0], then of the next one, ..., then the instances with kQList[1], ...
+    // Q = kBatchQList[0], then of the next one, ..., then the instances with kBatchQList[1], ...
     std::vector<int2> work[2];
     for (int wi = 0; wi < 2; ++wi) {
         const int tile = 31 * kBatchWarps[wi];
-        for (int g = 0; g < kNumQ; ++g) {
+        for (int g = 0; g < kNumBatchQ; ++g) {
             b->qstart[wi][g] = int64_t(work[wi].size());
             for (int64_t i = 0; i < n; ++i) {
-                if (b->inst[i].Q != kQList[g]) continue;
+                if (b->inst[i].Q != kBatchQList[g]) continue;
                 const int64_t nt = (b->inst[i].nx + tile - 1) / tile;
                 for (int64_t t = 0; t < nt; ++t) work[wi].push_back(make_int2(int(i), int(t)));
             }

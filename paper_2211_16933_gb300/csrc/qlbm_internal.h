@@ -14,10 +14,15 @@
 
 namespace qlbm {
 
-// Velocity-set sizes with compiled kernels.
-constexpr int kNumQ = 4;
-constexpr int kQList[kNumQ] = {8, 16, 24, 32};
-constexpr int kMaxQ = 32;
+// Velocity-set sizes with compiled single-domain kernels (Q = 20 is the
+// paper's set for sigma = 0.1, Q = 40 a near-ballistic one), and the subset
+// the batched form compiles.
+constexpr int kNumQ = 6;
+constexpr int kQList[kNumQ] = {8, 16, 20, 24, 32, 40};
+constexpr int kMaxQ = 40;
+constexpr int kNumBatchQ = 4;
+constexpr int kBatchQList[kNumBatchQ] = {8, 16, 24, 32};
+constexpr int kBatchMaxQ = 32;
 
 // CTA geometry of the stage kernel.  A CTA stages kSeg consecutive cells of
 // every (component, velocity) row in shared memory: kTile cells it updates
@@ -50,8 +55,8 @@ QL_HD constexpr int tab_size(int Q) { return Q * Q + 5 * Q; }
 QL_HD constexpr int tab_offset(int Q)
 {
     // tables of the sizes in kQList, in ascending order
-    return (Q > 8 ? tab_size(8) : 0) + (Q > 16 ? tab_size(16) : 0) + (Q > 24 ? tab_size(24) : 0) +
-           (Q > 32 ? tab_size(32) : 0);
+    return (Q > 8 ? tab_size(8) : 0) + (Q > 16 ? tab_size(16) : 0) + (Q > 20 ? tab_size(20) : 0) +
+           (Q > 24 ? tab_size(24) : 0) + (Q > 32 ? tab_size(32) : 0) + (Q > 40 ? tab_size(40) : 0);
 }
 constexpr int kTabTotal = tab_offset(1 << 30);
 struct TabView {

@@ -78,7 +78,7 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     if (!vs || !grid || !bc || !opts || !psi || nsteps < 0) return nfail(QL_EINVAL, "null argument or nsteps < 0");
     bool qok = false;
     for (int j = 0; j < kNumQ; ++j) qok |= vs->Q == kQList[j];
-    if (!qok || vs->kind != 0) return nfail(QL_EUNSUPPORTED, "Q must be one of 8, 16, 24, 32");
+    if (!qok || vs->kind != 0) return nfail(QL_EUNSUPPORTED, "Q must be one of 8, 16, 20, 24, 32, 40");
     if (grid->nx < 8 || grid->nx > (int64_t(1) << 31) || !(grid->length > 0) || !(grid->dt > 0))
         return nfail(QL_EINVAL, "bad grid");
     if (!(denseness > 0) || !(kn > 0) || !(opts->rho_ref > 0)) return nfail(QL_EINVAL, "bad gas parameters");

@@ -89,7 +89,7 @@ def _smooth_workload(Q, nx, bc="periodic"):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("Q", [8, 16, 24, 32])
+@pytest.mark.parametrize("Q", [8, 16, 20, 24, 32, 40])
 def test_rhs_matches_oracle(gpu, Q, precision):
     """L[psi] of Eq. (cast) on an off-equilibrium periodic state spanning 3 tiles + a ragged tail."""
     nx = 3 * 248 + 17
@@ -113,7 +113,7 @@ def test_rhs_matches_oracle(gpu, Q, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("Q", [8, 16, 24, 32])
+@pytest.mark.parametrize("Q", [8, 16, 20, 24, 32, 40])
 @pytest.mark.parametrize("bc", ["periodic", "fixed"])
 def test_steps_match_oracle(gpu, Q, precision, bc):
     nx = 3 * 248 + 17

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol(qlbm_lib):
     assert set(qlbm_lib.EXPORTED) == set(names)
 
 
-@pytest.mark.parametrize("Q", [8, 16, 24, 32, 48, 64])
+@pytest.mark.parametrize("Q", [8, 16, 20, 24, 32, 40, 48, 64])
 def test_velocity_set_matches_oracle(qlbm_lib, Q):
     p, w = qlbm_lib.ql_velocity_set(Q)
     po, wo = O.quadrature(Q)
