@@ -117,6 +117,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """Largest value of x over the ranks of the default process group (x itself for one rank); the
+    reduction runs on the current GPU for NCCL and on the host for gloo."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, max_seconds: float) -> float:
+    """Units processed by all ranks (weak scaling: the same work per rank) over the slowest rank's time."""
+    return units_per_rank * ws / max_seconds
+
+
 def _oracle_sample(w, steps, warmup):
     """Times the FP64 oracle on a window of the workload; returns (updates/s, seconds, sample text)."""
     import oracle as O
@@ -207,12 +225,8 @@ def run_ours(args, w):
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = sum(step_ms)
     s.sync()
-    t = torch.tensor([total_ms], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
-    updates = nx * Q * args.steps * ws
-    value = updates / (max_ms * 1e-3)
+    max_ms = max_over_ranks(total_ms, ws)
+    value = whole_job_rate(nx * Q * args.steps, ws, max_ms * 1e-3)
 
     # roofline of the stage kernel: algorithmic bytes = 16 words per update per step
     # (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2, words of phi and theta)
@@ -250,12 +264,8 @@ def run_ours(args, w):
             q.ql_totals(s.ctx, tot.numpy())
         q.ql_moments(s.ctx, *[o.numpy() for o in outs], tot.numpy())
         barrier()
-        el = time.perf_counter() - t0
-        t = torch.tensor([el], device="cuda")
-        if ws > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el = float(t.item())
-        e2e = {"value": nx * Q * ke * ws / el, "unit": "updates/s",
+        el = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": whole_job_rate(nx * Q * ke, ws, el), "unit": "updates/s",
                "h2d_bytes_per_step": 3 * 8 * nx / ke, "d2h_bytes_per_step": 3 * 8 + 6 * 8 * nx / ke,
                "steps": ke, "pattern": "load fields (pinned) + K x (step, totals) + all fields"}
 
