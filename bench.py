@@ -38,6 +38,19 @@ def _peaks():
         return None
 
 
+def _tensor_roofline(achieved_tflops):
+    """The closure's training step (BF16 mma.sync with FP32 accumulation; convolution FLOPs of the forward and
+    both backward passes) against the measured dense BF16 rate; sustained figure, the step runs for seconds."""
+    peaks = _peaks()
+    if peaks and "bf16_tflops_sustained" in peaks:
+        peak, src = float(peaks["bf16_tflops_sustained"]), "measured (sustained)"
+    else:
+        peak, src = 1700.0, "fallback (sustained)"
+    return {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved_tflops / peak, "traffic": None, "peak_source": src,
+            "kernel": "closure training step: conv_kernel, wgrad_kernel, transposed conv_kernel"}
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_16933_gb300", "csrc")
@@ -470,7 +483,8 @@ def run_learned(args):
                        "batch": args.train_batch, "lr": args.lr, "lr_schedule": "cosine to lr/20"},
             # per training step: pack, 5 convs, mse, 5 wgrads + 5 partial sums, 4 edge terms + 4 transposed
             # convs, adam, 5 weight casts
-            "gpu_launches": 31 * (nsamp // args.train_batch), "train_conv_tflops": train_tflops, "data_generation_s": t_gen,
+            "gpu_launches": 31 * (nsamp // args.train_batch), "train_conv_tflops": train_tflops,
+            "roofline": _tensor_roofline(train_tflops), "data_generation_s": t_gen,
             "train_s": t_train, "loss_per_epoch": losses, "held_out": held,
             "time_to_solution": {"pairs": n, "coarse_fp32_batch_plus_net_s": t_learned,
                                  "fine_fp32_batch_s": t_fine32, "plain_fp64_fine_sequential_s": t_fine64,

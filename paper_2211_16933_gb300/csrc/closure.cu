@@ -15,6 +15,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -26,7 +27,32 @@ constexpr int kTaps = 5;
 constexpr int kTM = 64;  // positions per CTA tile
 typedef __nv_bfloat16 bf16;
 
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// ldmatrix: lanes 8i..8i+7 give the 16-byte row addresses of 8x8 matrix i; each
+// lane receives, per matrix, the element pair (row lane/4, columns 2 (lane%4),
+// +1) of the matrix, or of its transpose with .trans (the mma.sync fragment
+// layouts).
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const bf16 *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t (&r)[2], const bf16 *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(smem_u32(p)));
+}
 
 __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, const uint32_t *b)
 {
@@ -59,157 +85,173 @@ enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
 //     positions outside the sample are zero; at the two end positions of a
 //     replicate-padded sample edge[b][side][co] is added (edge_grad_kernel);
 //     then times (mask[b][x][co] > 0), stored bf16 (ReLU backward).
-// One CTA: kTM positions of one sample, all COUT channels; 4 warps x 16 positions.
+// Persistent CTAs: the layer's weights are loaded into shared memory once, then
+// each CTA walks (sample, 64-position tile) items with a grid stride; per item
+// 4 warps x 16 positions, all COUT channels, as an implicit GEMM (M = positions,
+// N = COUT, K = 5 CIN) on mma.sync m16n8k16 with ldmatrix fragments.
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w,
                                                    const float *__restrict__ bias, const int *__restrict__ periodic,
-                                                   int X, void *__restrict__ out, const bf16 *__restrict__ mask,
+                                                   int X, int B, void *__restrict__ out, const bf16 *__restrict__ mask,
                                                    const float *__restrict__ edge)
 {
-    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "padded channels");
-    constexpr int WS = CIN + 8;  // smem row stride (bf16), avoids bank conflicts
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0, "padded channels");
+    constexpr int WS = CIN + 8;  // smem row stride (bf16): 16-byte rows, no ldmatrix bank conflicts
     extern __shared__ __align__(16) unsigned char smem[];
-    bf16 *win = reinterpret_cast<bf16 *>(smem);  // [kTM + 4][WS]
-    bf16 *ws = win + (kTM + 4) * WS;             // [COUT * 5][WS]
-    const int b = blockIdx.y, x0 = blockIdx.x * kTM, t = threadIdx.x;
-    const bool per = periodic[b] != 0;
-    const int mode = per ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
+    bf16 *ws = reinterpret_cast<bf16 *>(smem);  // [COUT * 5][WS]
+    bf16 *win = ws + COUT * kTaps * WS;         // [kTM + 4][WS]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
     constexpr int VPR = CIN / 8;  // 16-byte vectors per row
-    for (int e = t; e < (kTM + 4) * VPR; e += blockDim.x) {
-        const int r = e / VPR, v = e % VPR;
-        bool inside;
-        const int p = wrap_pos(x0 - 2 + r, X, mode, &inside);
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (inside) val = *reinterpret_cast<const uint4 *>(in + (size_t(b) * X + p) * CIN + v * 8);
-        *reinterpret_cast<uint4 *>(win + r * WS + v * 8) = val;
-    }
     for (int e = t; e < COUT * kTaps * VPR; e += blockDim.x) {
         const int r = e / VPR, v = e % VPR;
         *reinterpret_cast<uint4 *>(ws + r * WS + v * 8) = *reinterpret_cast<const uint4 *>(w + r * CIN + v * 8);
     }
-    __syncthreads();
-
-    const int lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
+    const int tiles = (X + kTM - 1) / kTM;
     const int m0 = warp * 16;
-    float acc[COUT / 8][4];
+    // ldmatrix row of this lane: matrix mat = lane / 8, row t8 = lane % 8
+    const int t8 = lane & 7, mat = lane >> 3;
+    for (int item = blockIdx.x; item < B * tiles; item += gridDim.x) {
+        const int b = item / tiles, x0 = (item % tiles) * kTM;
+        const bool per = periodic[b] != 0;
+        const int mode = per ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
+        __syncthreads();  // the previous item's window is no longer read
+        for (int e = t; e < (kTM + 4) * VPR; e += blockDim.x) {
+            const int r = e / VPR, v = e % VPR;
+            bool inside;
+            const int p = wrap_pos(x0 - 2 + r, X, mode, &inside);
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (inside) val = *reinterpret_cast<const uint4 *>(in + (size_t(b) * X + p) * CIN + v * 8);
+            *reinterpret_cast<uint4 *>(win + r * WS + v * 8) = val;
+        }
+        __syncthreads();
+
+        float acc[COUT / 8][4];
 #pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
 #pragma unroll
-    for (int j = 0; j < kTaps; ++j) {
+        for (int j = 0; j < kTaps; ++j) {
 #pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            const int cb = kc * 16 + 2 * tg;
-            const bf16 *ra = win + (m0 + j + g) * WS + cb;
-            uint32_t a[4] = {ld32(ra), ld32(ra + 8 * WS), ld32(ra + 8), ld32(ra + 8 * WS + 8)};
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                // A[m][k] = win[m0 + m + j][16 kc + k]: matrices (m 0-7 | 8-15) x (k 0-7 | 8-15)
+                uint32_t a[4];
+                ldsm_x4(a, win + (m0 + j + (mat & 1) * 8 + t8) * WS + kc * 16 + (mat >> 1) * 8);
 #pragma unroll
-            for (int n = 0; n < COUT / 8; ++n) {
-                const bf16 *rb = ws + ((n * 8 + g) * kTaps + j) * WS + cb;
-                uint32_t bb[2] = {ld32(rb), ld32(rb + 8)};
-                mma16816(acc[n], a, bb);
+                for (int n = 0; n < COUT / 8; n += 2) {
+                    // B[k][co] = ws[co * 5 + j][16 kc + k]: matrices (co 0-7: k 0-7, 8-15), (co 8-15: ...)
+                    uint32_t bb[4];
+                    ldsm_x4(bb, ws + ((n * 8 + (mat >> 1) * 8 + t8) * kTaps + j) * WS + kc * 16 + (mat & 1) * 8);
+                    mma16816(acc[n], a, bb);
+                    mma16816(acc[n + 1], a, bb + 2);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) {
-        const int co = n * 8 + 2 * tg;
+        for (int n = 0; n < COUT / 8; ++n) {
+            const int co = n * 8 + 2 * tg;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int x = x0 + m0 + g + 8 * h;
-            if (x >= X) continue;
-            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
-            const size_t o = (size_t(b) * X + x) * COUT + co;
-            if (EPI != EPI_MASK_BF16) {
-                v0 += bias[co];
-                v1 += bias[co + 1];
-            }
-            if (EPI == EPI_RELU_BF16) {
-                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) =
-                    __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
-            } else if (EPI == EPI_F32) {
-                *reinterpret_cast<float2 *>(static_cast<float *>(out) + o) = make_float2(v0, v1);
-            } else {
-                if (!per && (x == 0 || x == X - 1)) {
-                    const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + co;
-                    v0 += eg[0];
-                    v1 += eg[1];
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + m0 + g + 8 * h;
+                if (x >= X) continue;
+                float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
+                const size_t o = (size_t(b) * X + x) * COUT + co;
+                if (EPI != EPI_MASK_BF16) {
+                    v0 += bias[co];
+                    v1 += bias[co + 1];
                 }
-                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + o);
-                v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
-                v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
-                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) = __floats2bfloat162_rn(v0, v1);
+                if (EPI == EPI_RELU_BF16) {
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) =
+                        __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                } else if (EPI == EPI_F32) {
+                    *reinterpret_cast<float2 *>(static_cast<float *>(out) + o) = make_float2(v0, v1);
+                } else {
+                    if (!per && (x == 0 || x == X - 1)) {
+                        const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + co;
+                        v0 += eg[0];
+                        v1 += eg[1];
+                    }
+                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + o);
+                    v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+                    v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) = __floats2bfloat162_rn(v0, v1);
+                }
             }
         }
     }
 }
 
 // Weight and bias gradients of one layer:
-//   dW[co][j][ci] = sum_{b,x} dz[b][x][co] in[b][x + j - 2][ci],  db[co] = sum dz[b][x][co].
-// Each CTA accumulates over its share of the (sample, tile) pairs and writes a
-// partial; reduce_partials_kernel sums the partials in a fixed order.
-// 8 warps: warp (mw, nw) holds couts [16 mw, 16 mw + 16) and half of the
-// 5 CIN columns.
+//   dW[co][j][ci] = sum_{b,x} dz[b][x][co] in[b][x + j - 2][ci],  db[co] = sum dz[b][x][co],
+// a GEMM with M = COUT, N = 5 CIN, K = positions.  Each CTA accumulates over
+// its share of the (sample, tile) items and writes a partial;
+// reduce_partials_kernel sums the partials in a fixed order.  The dz tile and
+// the input window are staged channels-last with 16-byte copies; the
+// transposed operands (K = positions contiguous) come from ldmatrix .trans.
+// 8 warps: warp (mw, nw) holds couts [16 mw, 16 mw + 16) and NTW of the N/8
+// column tiles.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ in,
                                                     const int *__restrict__ periodic, int X, int ntiles,
                                                     float *__restrict__ partial)
 {
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0, "padded channels");
     constexpr int N = kTaps * CIN;
-    constexpr int MT = (COUT + 15) / 16;  // m tiles (COUT = 8 pads to one)
-    constexpr int NT = N / 8;             // n tiles
-    constexpr int NW = 8 / MT;  // warps along N
+    constexpr int MT = COUT / 16;            // m tiles
+    constexpr int NT = N / 8;                // n tiles
+    constexpr int NW = 8 / MT;               // warps along N
     constexpr int NTW = (NT + NW - 1) / NW;  // n tiles per warp
-    constexpr int PS = kTM + 8;              // smem row stride (positions)
+    constexpr int DS = COUT + 8, IS = CIN + 8;  // smem row strides (bf16)
     extern __shared__ __align__(16) unsigned char smem[];
-    bf16 *gt = reinterpret_cast<bf16 *>(smem);  // [16 MT][PS]  dz transposed, rows >= COUT zero
-    bf16 *it0 = gt + 16 * MT * PS;              // [CIN][PS]    input window transposed
-    bf16 *it1 = it0 + CIN * PS;                 // [CIN][PS]    same, shifted by one position
-    float *dbs = reinterpret_cast<float *>(it1 + CIN * PS);  // [16 MT]
+    bf16 *sdz = reinterpret_cast<bf16 *>(smem);  // [kTM][DS]     dz tile, positions x couts
+    bf16 *sin = sdz + kTM * DS;                  // [kTM + 4][IS] input window, positions x cins
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
+    const int t8 = lane & 7, mat = lane >> 3;
     const int mw = warp % MT, nw = warp / MT;
     float acc[NTW][4];
 #pragma unroll
     for (int n = 0; n < NTW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
     float db = 0.f;
+    const int tiles = (X + kTM - 1) / kTM;
     for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
-        const int b = item / ((X + kTM - 1) / kTM), x0 = (item % ((X + kTM - 1) / kTM)) * kTM;
+        const int b = item / tiles, x0 = (item % tiles) * kTM;
         const int mode = periodic[b] != 0 ? PAD_PERIODIC : PAD_REPLICATE;
         __syncthreads();
-        for (int e = t; e < 16 * MT * kTM; e += blockDim.x) {
-            const int p = e / (16 * MT), co = e % (16 * MT);
+        for (int e = t; e < kTM * (COUT / 8); e += blockDim.x) {
+            const int p = e / (COUT / 8), v = e % (COUT / 8);
             const int x = x0 + p;
-            bf16 v = __float2bfloat16(0.f);
-            if (co < COUT && x < X) v = dz[(size_t(b) * X + x) * COUT + co];
-            gt[co * PS + p] = v;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (x < X) val = *reinterpret_cast<const uint4 *>(dz + (size_t(b) * X + x) * COUT + v * 8);
+            *reinterpret_cast<uint4 *>(sdz + p * DS + v * 8) = val;
         }
-        for (int e = t; e < (kTM + 5) * CIN; e += blockDim.x) {
-            const int p = e / CIN, ci = e % CIN;
+        for (int e = t; e < (kTM + 4) * (CIN / 8); e += blockDim.x) {
+            const int p = e / (CIN / 8), v = e % (CIN / 8);
             bool inside;
             const int x = wrap_pos(x0 - 2 + p, X, mode, &inside);
-            bf16 v = __float2bfloat16(0.f);
-            if (inside) v = in[(size_t(b) * X + x) * CIN + ci];
-            if (p < kTM + 4) it0[ci * PS + p] = v;
-            if (p >= 1) it1[ci * PS + p - 1] = v;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (inside) val = *reinterpret_cast<const uint4 *>(in + (size_t(b) * X + x) * CIN + v * 8);
+            *reinterpret_cast<uint4 *>(sin + p * IS + v * 8) = val;
         }
         __syncthreads();
-        // bias gradient: thread t < 16 MT sums row t of dz^T
+        // bias gradient: thread t < COUT sums column t of the dz tile
         if (t < COUT) {
             float s = 0.f;
-            for (int p = 0; p < kTM; ++p) s += __bfloat162float(gt[t * PS + p]);
+            for (int p = 0; p < kTM; ++p) s += __bfloat162float(sdz[p * DS + t]);
             db += s;
         }
 #pragma unroll
         for (int k0 = 0; k0 < kTM; k0 += 16) {
-            const bf16 *ra = gt + (16 * mw + g) * PS + k0 + 2 * tg;
-            uint32_t a[4] = {ld32(ra), ld32(ra + 8 * PS), ld32(ra + 8), ld32(ra + 8 * PS + 8)};
+            // A[m = co][k = position] = sdz[k0 + k][16 mw + m]: transposed 8x8 blocks
+            // (co 0-7 | 8-15) x (positions 0-7 | 8-15)
+            uint32_t a[4];
+            ldsm_x4_trans(a, sdz + (k0 + (mat >> 1) * 8 + t8) * DS + 16 * mw + (mat & 1) * 8);
 #pragma unroll
             for (int n = 0; n < NTW; ++n) {
                 const int nt = nw * NTW + n;
                 if (nt >= NT) break;
-                const int col = nt * 8 + g;
-                const int j = col / CIN, ci = col % CIN;
-                // B[k][n] = in[x0 + k0 + k + j - 2][ci] = window position k0 + k + j
-                const bf16 *src = (j & 1) ? it1 + ci * PS + k0 + 2 * tg + j - 1 : it0 + ci * PS + k0 + 2 * tg + j;
-                uint32_t bb[2] = {ld32(src), ld32(src + 8)};
+                // column tile nt: tap j, cins [ci0, ci0 + 8); B[k][c] = in[x0 + k0 + k + j - 2][ci0 + c]
+                // = sin[k0 + k + j][ci0 + c]: transposed blocks for k 0-7 and 8-15 (lanes 0-15)
+                const int j = (nt * 8) / CIN, ci0 = (nt * 8) % CIN;
+                uint32_t bb[2];
+                ldsm_x2_trans(bb, sin + (k0 + (mat & 1) * 8 + t8 + j) * IS + ci0);
                 mma16816(acc[n], a, bb);
             }
         }
@@ -224,14 +266,11 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz,
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int co = 16 * mw + g + 8 * h;
-            if (co < COUT) {
-                P[co * N + col] = acc[n][2 * h];
-                P[co * N + col + 1] = acc[n][2 * h + 1];
-            }
+            P[co * N + col] = acc[n][2 * h];
+            P[co * N + col + 1] = acc[n][2 * h + 1];
         }
     }
     if (t < COUT) P[COUT * N + t] = db;
-    (void)dbs;
 }
 
 // Replicate padding feeds the end values a[0] and a[X-1] of a sample into the
@@ -250,6 +289,8 @@ __global__ void edge_grad_kernel(const bf16 *__restrict__ dz, const bf16 *__rest
         const bf16 *d0 = dz + (size_t(b) * X + (side ? X - 1 : 0)) * cout;
         const bf16 *d1 = dz + (size_t(b) * X + (side ? X - 2 : 1)) * cout;
         const int ja = side ? 3 : 0, jb = side ? 4 : 1, jn = side ? 4 : 0;
+        // independent iterations: keep 16 in flight (the loads are L2 hits)
+#pragma unroll 16
         for (int co = 0; co < cout; ++co) {
             const float wa = __bfloat162float(w[(co * kTaps + ja) * cin + ci]);
             const float wb = __bfloat162float(w[(co * kTaps + jb) * cin + ci]);
@@ -261,14 +302,20 @@ __global__ void edge_grad_kernel(const bf16 *__restrict__ dz, const bf16 *__rest
     edge[(size_t(b) * 2 + side) * cin + ci] = s;
 }
 
-// out[i] = sum_c partial[c][i] in a fixed order.
+// out[i] = sum_c partial[c][i] in a fixed order: four interleaved running sums
+// (c mod 4), combined pairwise, so that loads overlap and results stay
+// deterministic.
 __global__ void reduce_partials_kernel(const float *__restrict__ partial, int nparts, int len, float *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
-    float s = 0.f;
-    for (int c = 0; c < nparts; ++c) s += partial[size_t(c) * len + i];
-    out[i] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int c = 0;
+    for (; c + 4 <= nparts; c += 4)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s[r] += partial[size_t(c + r) * len + i];
+    for (int r = 0; c < nparts; ++c, ++r) s[r] += partial[size_t(c) * len + i];
+    out[i] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 // Input features (f32 [B][X][cin_real]) -> normalised bf16 [B][X][CINP].
@@ -372,7 +419,14 @@ cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const 
     auto k = conv_kernel<CIN, COUT, EPI>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k<<<dim3((X + kTM - 1) / kTM, B), 128, smem, s>>>(in, w, bias, per, X, out, mask, edge);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
+    if (e != cudaSuccess) return e;
+    const int items = B * ((X + kTM - 1) / kTM);
+    const int grid = std::max(1, std::min(items, std::max(1, sms) * std::max(1, per_sm)));
+    k<<<grid, 128, smem, s>>>(in, w, bias, per, X, B, out, mask, edge);
     return cudaGetLastError();
 }
 
@@ -395,9 +449,7 @@ template <int CIN, int COUT>
 cudaError_t wgrad_launch(const bf16 *dz, const bf16 *in, const int *per, int B, int X, int grid, float *partial,
                          cudaStream_t s)
 {
-    constexpr int MT = (COUT + 15) / 16;
-    constexpr int PS = kTM + 8;
-    constexpr size_t smem = sizeof(bf16) * (16 * MT * PS + 2 * CIN * PS) + sizeof(float) * 16 * MT;
+    constexpr size_t smem = sizeof(bf16) * (kTM * (COUT + 8) + (kTM + 4) * (CIN + 8));
     auto k = wgrad_kernel<CIN, COUT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;

@@ -115,6 +115,15 @@ def test_sound_modes_and_projection_reject_bad_arguments(qlbm_lib):
     assert st == q.QL_EINVAL
 
 
+def test_batch_create_rejects_an_empty_batch(qlbm_lib):
+    q = qlbm_lib
+    o = q.ql_opts()
+    o.precision = q.QL_FP32
+    with pytest.raises(q.QLError) as e:
+        q.ql_batch_create([], o)
+    assert e.value.status == q.QL_EINVAL
+
+
 def test_chi_ret_fm_options_are_checked_before_touching_the_gpu(qlbm_lib):
     """chi_mode must be SET or RET-FM, and a chi_RET-FM ball reaching more than QL_FM_MAX_HALFWIDTH cells is
     unsupported; ql_step_noalloc takes chi_SET only."""
