@@ -63,8 +63,11 @@ enum { QL_CHI_SET = 0, QL_CHI_RET_FM = 1 };
 
 /* Velocity set, Sec. II.D: the Q roots p_k of the probabilists' Hermite
  * polynomial He_Q with weights w_k = Q!/He_{Q+1}(p_k)^2 (kind 0 is the only
- * kind).  This build has kernels for Q in {8, 16, 20, 24, 32, 40} (the batched
- * form: {8, 16, 24, 32}). */
+ * kind).  Tiled kernels exist for Q in {8, 16, 20, 24, 32, 40} (the batched
+ * form: {8, 16, 24, 32}); any other even Q up to 200 (the paper's
+ * near-ballistic runs use 200) runs on a generic FP64 path whose per-cell
+ * work grows as Q^2: FP64 and chi_SET only, for domains of the paper's sizes
+ * (hundreds to thousands of cells). */
 typedef struct {
     int32_t Q;
     int32_t kind;

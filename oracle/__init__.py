@@ -22,7 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-QMAX = 64
+QMAX = 200
 NG = 3
 
 

@@ -30,7 +30,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OQ_QMAX 64
+#define OQ_QMAX 200
 #define OQ_NG 3 /* ghost cells per side: WENO-5 and the 6th-order gradient reach 3 cells */
 
 #ifndef M_PI
@@ -125,12 +125,16 @@ static double oq_factorial(int n)
 /* Sec. II.D: the velocity set is the Q roots r_k of He_Q, in ascending order,
  * with weights w_k = Q! / [He_{Q+1}(r_k)]^2.  The roots are bracketed by a
  * sign-change scan of He_Q on a fine grid and refined by bisection to the
- * last representable midpoint.  Returns 0 on success. */
+ * last representable midpoint.  READING c2b: for Q > 100, where Q! or He_{Q+1}^2
+ * leave the double range, the same weight is evaluated through the identity
+ * Q! / He_{Q+1}^2 = 1 / ((Q + 1) h_{Q+1}^2) with h_l = He_l / sqrt(l!) from
+ * h_{l+1} = (p h_l - sqrt(l) h_{l-1}) / sqrt(l + 1).  Returns 0 on success. */
 int oq_quadrature(int Q, double *p, double *w)
 {
     if (Q < 1 || Q > OQ_QMAX) return -1;
     double R = sqrt(4.0 * Q + 2.0) + 1.0; /* all roots lie inside (-R, R) */
-    int nscan = 200 * Q * Q;
+    /* scan steps far below the smallest root spacing (about pi / sqrt(2 Q + 1)) */
+    int nscan = Q <= 64 ? 200 * Q * Q : 2000 * Q;
     double h = 2.0 * R / nscan;
     int found = 0;
     double xa = -R, fa = oq_hermite(Q, xa);
@@ -159,10 +163,22 @@ int oq_quadrature(int Q, double *p, double *w)
         fa = fb;
     }
     if (found != Q) return -2;
-    double qf = oq_factorial(Q);
-    for (int k = 0; k < Q; ++k) {
-        double hq1 = oq_hermite(Q + 1, p[k]);
-        w[k] = qf / (hq1 * hq1);
+    if (Q <= 100) {
+        double qf = oq_factorial(Q);
+        for (int k = 0; k < Q; ++k) {
+            double hq1 = oq_hermite(Q + 1, p[k]);
+            w[k] = qf / (hq1 * hq1);
+        }
+    } else {
+        for (int k = 0; k < Q; ++k) {
+            double hm = 1.0, h = p[k];
+            for (int l = 1; l <= Q; ++l) {
+                double hn = (p[k] * h - sqrt((double)l) * hm) / sqrt((double)(l + 1));
+                hm = h;
+                h = hn;
+            }
+            w[k] = 1.0 / ((Q + 1) * h * h);
+        }
     }
     return 0;
 }

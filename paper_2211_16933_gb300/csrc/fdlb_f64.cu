@@ -6,3 +6,4 @@ static __constant__ double QL_TAB[kTabTotal];
 #define QL_REAL double
 #define QL_SUFFIX f64
 #include "fdlb_impl.cuh"
+#include "fdlb_lq.cuh"

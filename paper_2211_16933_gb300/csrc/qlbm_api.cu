@@ -19,7 +19,10 @@ struct ql_ctx {
     int64_t nx = 0, stride = 0;
     double L = 0, dx = 0, dt = 0, El = 0, kn = 0, pr_const = 2.0 / 3.0, rho_ref = 1.0;
     double eta0 = 0, chi0 = 1, sigma = 0, tau_pref = 0;
-    double p[kMaxQ] = {}, w[kMaxQ] = {};
+    std::vector<double> p, w;  // velocity set (Q)
+    // velocity sets without compiled tiled kernels run on the generic FP64 path
+    bool lq = false;
+    double *d_lqtab = nullptr, *d_lqmom = nullptr, *d_lqcoef = nullptr;
     cudaStream_t stream = nullptr;
     ql_alloc_fn alloc = nullptr;
     ql_free_fn free_fn = nullptr;
@@ -87,6 +90,29 @@ static void dev_free(ql_ctx *c, void *p)
 
 static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, void *out)
 {
+    if (c->lq) {
+        LqArgs l;
+        l.in = in;
+        l.base = base;
+        l.out = out;
+        l.nx = c->nx;
+        l.stride = c->stride;
+        l.Q = c->Q;
+        l.periodic = c->periodic;
+        l.pr_mode = c->pr_mode;
+        l.enskog = c->enskog;
+        l.inv_dx = 1.0 / c->dx;
+        l.dt = c->dt;
+        l.eta0 = c->eta0;
+        l.inv_rho_ref = 1.0 / c->rho_ref;
+        l.tau_pref = c->tau_pref;
+        l.pr_const = c->pr_const;
+        l.tab = c->d_lqtab;
+        l.mom = c->d_lqmom;
+        l.coef = c->d_lqcoef;
+        l.err = c->d_err;
+        return launch_lq_stage(s, l, c->stream);
+    }
     StageArgs a;
     a.in = in;
     a.base = base;
@@ -157,7 +183,9 @@ static ql_status upload_fields_and_init(ql_ctx *c, const double *rho, const doub
     memcpy(h.data() + ncol, u, sizeof(double) * ncol);
     memcpy(h.data() + 2 * ncol, T, sizeof(double) * ncol);
     QL_CUDA(c, cudaMemcpyAsync(c->d_init, h.data(), sizeof(double) * 3 * ncol, cudaMemcpyHostToDevice, c->stream));
-    cudaError_t e = c->precision == QL_FP32
+    cudaError_t e = c->lq ? launch_lq_init(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
+                                           c->stride, c->d_lqtab, c->stream)
+                    : c->precision == QL_FP32
                         ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
                                           c->stride, c->d_tab64, c->stream)
                         : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
@@ -179,6 +207,9 @@ static void destroy_buffers(ql_ctx *c)
     dev_free(c, c->d_fmk);
     dev_free(c, c->d_n);
     dev_free(c, c->d_nbar);
+    dev_free(c, c->d_lqtab);
+    dev_free(c, c->d_lqmom);
+    dev_free(c, c->d_lqcoef);
 }
 
 extern "C" {
@@ -191,7 +222,12 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     bool qok = false;
     for (int j = 0; j < kNumQ; ++j) qok |= vs->Q == kQList[j];
     if (vs->kind != 0) return fail(nullptr, QL_EINVAL, "velocity set kind must be 0 (Gauss-Hermite)");
-    if (!qok) return fail(nullptr, QL_EUNSUPPORTED, "Q must be one of 8, 16, 20, 24, 32, 40");
+    const bool lq = !qok && vs->Q >= 2 && vs->Q <= kLargeMaxQ && vs->Q % 2 == 0;
+    if (!qok && !lq) return fail(nullptr, QL_EUNSUPPORTED, "Q must be even and at most 200");
+    if (lq && opts->precision != QL_FP64)
+        return fail(nullptr, QL_EUNSUPPORTED, "velocity sets other than 8, 16, 20, 24, 32, 40 run in FP64 only");
+    if (lq && opts->chi_mode != QL_CHI_SET)
+        return fail(nullptr, QL_EUNSUPPORTED, "velocity sets other than 8, 16, 20, 24, 32, 40 use chi_SET only");
     if (grid->nx < 8 || grid->nx > (int64_t(1) << 31)) return fail(nullptr, QL_EINVAL, "nx must be in [8, 2^31]");
     if (!(grid->length > 0) || !(grid->dt > 0)) return fail(nullptr, QL_EINVAL, "length and dt must be > 0");
     if (!(denseness > 0) || !(kn > 0)) return fail(nullptr, QL_EINVAL, "denseness and kn must be > 0");
@@ -203,6 +239,7 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
 
     ql_ctx *c = new ql_ctx();
     c->chi_mode = opts->chi_mode;
+    c->lq = lq;
     c->Q = vs->Q;
     c->precision = opts->precision;
     c->pr_mode = opts->pr_mode;
@@ -248,10 +285,22 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
             g_tab_built = true;
         }
     }
-    const TabView tv = tab_view(c->Q);
-    for (int k = 0; k < c->Q; ++k) {
-        c->p[k] = g_tab[tv.p + k];
-        c->w[k] = g_tab[tv.G + k * c->Q];  // w_k h_0 = w_k
+    c->p.assign(c->Q, 0.0);
+    c->w.assign(c->Q, 0.0);
+    std::vector<double> lqtab;
+    if (c->lq) {
+        lqtab.assign(size_t(c->Q) * c->Q + 5 * size_t(c->Q), 0.0);
+        if (!build_table_q(c->Q, lqtab.data())) return bail(QL_EINVAL, "velocity-set construction failed");
+        for (int k = 0; k < c->Q; ++k) {
+            c->p[k] = lqtab[k];
+            c->w[k] = lqtab[3 * size_t(c->Q) + size_t(k) * c->Q];  // w_k h_0 = w_k
+        }
+    } else {
+        const TabView tv = tab_view(c->Q);
+        for (int k = 0; k < c->Q; ++k) {
+            c->p[k] = g_tab[tv.p + k];
+            c->w[k] = g_tab[tv.G + k * c->Q];  // w_k h_0 = w_k
+        }
     }
 
     // initial fields on the host, ghost columns included
@@ -286,6 +335,15 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     c->d_err = static_cast<unsigned *>(dev_alloc(c, 256));
     if (!c->d_fields || !c->d_init || !c->d_partial || !c->d_totals || !c->d_tab64 || !c->d_err)
         return bail(QL_ENOMEM, "work buffer allocation failed");
+    if (c->lq) {
+        c->d_lqtab = static_cast<double *>(dev_alloc(c, sizeof(double) * lqtab.size()));
+        c->d_lqmom = static_cast<double *>(dev_alloc(c, sizeof(double) * 6 * ncol));
+        c->d_lqcoef = static_cast<double *>(dev_alloc(c, sizeof(double) * 9 * c->nx));
+        if (!c->d_lqtab || !c->d_lqmom || !c->d_lqcoef) return bail(QL_ENOMEM, "large-Q buffer allocation failed");
+        e = cudaMemcpyAsync(c->d_lqtab, lqtab.data(), sizeof(double) * lqtab.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // lqtab goes out of scope
+        if (e != cudaSuccess) return bail(QL_ECUDA, std::string("large-Q tables: ") + cudaGetErrorString(e));
+    }
     if (c->chi_mode == QL_CHI_RET_FM) {
         const size_t real = c->precision == QL_FP32 ? 4 : 8;
         c->d_fmk = static_cast<double *>(dev_alloc(c, sizeof(double) * (2 * c->fm_w + 1)));
@@ -371,8 +429,9 @@ static ql_status run_moments(ql_ctx *c, bool fields)
     a.Pxx = fields ? f + 5 * c->nx : nullptr;
     a.partial = c->d_partial;
     a.err = c->d_err;
-    cudaError_t e = c->precision == QL_FP32 ? launch_moments_f32(c->Q, a, c->d_tab64, c->stream)
-                                            : launch_moments_f64(c->Q, a, c->d_tab64, c->stream);
+    cudaError_t e = c->lq                      ? launch_lq_moments(c->Q, a, c->d_lqtab, c->stream)
+                    : c->precision == QL_FP32 ? launch_moments_f32(c->Q, a, c->d_tab64, c->stream)
+                                              : launch_moments_f64(c->Q, a, c->d_tab64, c->stream);
     if (e == cudaSuccess) e = launch_reduce_totals(c->d_partial, moment_blocks(c->nx), c->d_totals, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel");
     return QL_OK;
@@ -495,7 +554,9 @@ ql_status ql_load_fields(ql_ctx *c, const double *rho, const double *u, const do
         QL_CUDA(c, cudaMemcpyAsync(c->d_init + f * ncol + kHalo + nx, gh[f] + kHalo, sizeof(double) * kHalo,
                                    cudaMemcpyHostToDevice, c->stream));
     }
-    cudaError_t e = c->precision == QL_FP32
+    cudaError_t e = c->lq ? launch_lq_init(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
+                                           c->stride, c->d_lqtab, c->stream)
+                    : c->precision == QL_FP32
                         ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
                                           c->stride, c->d_tab64, c->stream)
                         : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,

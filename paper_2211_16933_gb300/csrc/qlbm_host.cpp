@@ -312,6 +312,26 @@ bool initial_fields(int kind, const double *prm, int64_t nx, double length, int 
     return true;
 }
 
+bool build_table_q(int Q, double *tab)
+{
+    // layout of tab_view with offset 0: p, p^2, p^3, G[k][l] = w_k h_l(p_k), ca, cb
+    if (Q < 2 || Q > kLargeMaxQ) return false;
+    std::vector<double> p(Q), w(Q), h(Q + 2);
+    if (!gh_quadrature(Q, p.data(), w.data())) return false;
+    const int G = 3 * Q, ca = 3 * Q + Q * Q, cb = 4 * Q + Q * Q;
+    for (int k = 0; k < Q; ++k) {
+        tab[k] = p[k];
+        tab[Q + k] = p[k] * p[k];
+        tab[2 * Q + k] = p[k] * p[k] * p[k];
+        hermite_normalised(Q - 1, p[k], h.data());
+        for (int l = 0; l < Q; ++l) tab[G + k * Q + l] = w[k] * h[l];
+    }
+    tab[ca] = tab[ca + 1] = tab[cb] = tab[cb + 1] = 0.0;
+    for (int l = 1; l < Q; ++l) tab[ca + l] = 1.0 / sqrt(double(l));
+    for (int l = 2; l < Q; ++l) tab[cb + l] = sqrt(double(l - 1) / double(l));
+    return true;
+}
+
 bool build_tables(double *all)
 {
     memset(all, 0, sizeof(double) * kTabTotal);

@@ -46,6 +46,10 @@ bool initial_fields(int kind, const double *prm, int64_t nx, double length, int 
 int fm_halfwidth(double dx, double sigma);
 void fm_weights(double dx, double sigma, int W, double *K);
 
+// Tables of one velocity set of any size 2 <= Q <= kLargeMaxQ in the layout of
+// tab_view(Q) with offset 0 (Q * Q + 5 Q doubles), for the large-Q FP64 path.
+bool build_table_q(int Q, double *tab);
+
 // All kernel tables (layout of tab_view in qlbm_internal.h).
 bool build_tables(double *all);
 

@@ -20,6 +20,9 @@ namespace qlbm {
 constexpr int kNumQ = 6;
 constexpr int kQList[kNumQ] = {8, 16, 20, 24, 32, 40};
 constexpr int kMaxQ = 40;
+// Other even sizes up to kLargeMaxQ (the paper's near-ballistic runs use 200)
+// run on the generic FP64 path of fdlb_lq.cuh.
+constexpr int kLargeMaxQ = 200;
 constexpr int kNumBatchQ = 4;
 constexpr int kBatchQList[kNumBatchQ] = {8, 16, 24, 32};
 constexpr int kBatchMaxQ = 32;
@@ -154,6 +157,27 @@ struct MomentArgs {
 };
 constexpr int kMomThreads = 256;
 inline int64_t moment_blocks(int64_t nx) { return (nx + kMomThreads - 1) / kMomThreads; }
+// Generic-Q FP64 path (velocity sets without compiled kernels).  Per stage:
+// cell moments of every column, per-cell collision coefficients, then one
+// thread per (cell, velocity) for fluxes, equilibrium and update.  tab holds
+// tab_view(Q) with offset 0; mom 6 x (nx + 2 kHalo) doubles (n, u, T, q, ln n,
+// ln T); coef 9 x nx doubles.
+struct LqArgs {
+    const void *in;
+    const void *base;
+    void *out;
+    int64_t nx, stride;
+    int Q, periodic, pr_mode, enskog;
+    double inv_dx, dt, eta0, inv_rho_ref, tau_pref, pr_const;
+    const double *tab;
+    double *mom, *coef;
+    unsigned *err;
+};
+cudaError_t launch_lq_stage(int stage, const LqArgs &a, cudaStream_t s);
+cudaError_t launch_lq_init(int Q, const double *rho, const double *u, const double *T, void *psi, int64_t nx,
+                           int64_t stride, const double *tab, cudaStream_t s);
+cudaError_t launch_lq_moments(int Q, const MomentArgs &a, const double *tab, cudaStream_t s);
+
 // One batched stage over the work list: `grid` persistent CTAs of `warps`
 // warps (8 or 4; the work list must be built for the same tile width).
 // One launch over the work items of the instances with velocity-set size Q.

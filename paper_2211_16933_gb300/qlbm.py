@@ -22,7 +22,8 @@ QL_INIT_SOUND, QL_INIT_RIEMANN, QL_INIT_SHOCK, QL_INIT_FIELDS = 0, 1, 2, 3
 QL_PR_CONST, QL_PR_DENSE = 0, 1
 QL_CHI_SET, QL_CHI_RET_FM = 0, 1
 QL_FM_MAX_HALFWIDTH = 256
-SUPPORTED_Q = (8, 16, 20, 24, 32, 40)
+SUPPORTED_Q = (8, 16, 20, 24, 32, 40)  # tiled kernels; other even Q <= 200 run the generic FP64 path
+MAX_Q = 200
 SUPPORTED_BATCH_Q = (8, 16, 24, 32)
 EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_get_state", "ql_set_state",
             "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",

@@ -73,7 +73,7 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
     q = qlbm_lib
     kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-3), use_torch=False)
     with pytest.raises(q.QLError) as e:
-        q.Solver(12, 64, 1.0, 1e-3, 0.1, 0.1, **kw)
+        q.Solver(13, 64, 1.0, 1e-3, 0.1, 0.1, **kw)
     assert e.value.status == q.QL_EUNSUPPORTED
     for bad in (dict(nx=4), dict(dt=-1.0), dict(denseness=0.0), dict(kn=-1.0)):
         args = dict(Q=16, nx=64, length=1.0, dt=1e-3, denseness=0.1, kn=0.1)
@@ -122,6 +122,17 @@ def test_batch_create_rejects_an_empty_batch(qlbm_lib):
     with pytest.raises(q.QLError) as e:
         q.ql_batch_create([], o)
     assert e.value.status == q.QL_EINVAL
+
+
+def test_large_q_requirements_are_checked_before_touching_the_gpu(qlbm_lib):
+    """Velocity sets without tiled kernels: even Q up to 200, FP64, chi_SET."""
+    q = qlbm_lib
+    kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-3), use_torch=False)
+    for Q, prec, chi in ((201, q.QL_FP64, 0), (202, q.QL_FP64, 0), (51, q.QL_FP64, 0), (64, q.QL_FP32, 0),
+                         (64, q.QL_FP64, q.QL_CHI_RET_FM)):
+        with pytest.raises(q.QLError) as e:
+            q.Solver(Q, 64, 1.0, 1e-4, 0.1, 0.1, precision=prec, chi_mode=chi, **kw)
+        assert e.value.status == q.QL_EUNSUPPORTED, (Q, prec, chi)
 
 
 def test_chi_ret_fm_options_are_checked_before_touching_the_gpu(qlbm_lib):

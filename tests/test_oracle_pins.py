@@ -73,13 +73,17 @@ def test_tau_scales_with_sigma_at_fixed_eta():
 
 
 # ----------------------------------------------------------------- Sec. II.D quadrature
-@pytest.mark.parametrize("Q", [7, 8, 16, 24, 32, 48])
+@pytest.mark.parametrize("Q", [7, 8, 16, 24, 32, 48, 101, 150, 200])
 def test_quadrature_matches_gauss_hermite_library(Q):
+    """Up to Q = 100 the weights follow the printed formula; beyond it the normalised identity (READING c2b)."""
     p, w = O.quadrature(Q)
     x, wl = np.polynomial.hermite_e.hermegauss(Q)
     wl = wl / math.sqrt(2 * math.pi)
     np.testing.assert_allclose(p, x, rtol=0, atol=1e-12 * max(1.0, abs(x).max()))
-    np.testing.assert_allclose(w, wl, rtol=1e-11, atol=0)
+    # weights of the outermost nodes fall below 1e-300 for large Q; compare where they are representable
+    sel = wl > 1e-280
+    np.testing.assert_allclose(w[sel], wl[sel], rtol=1e-11, atol=0)
+    assert w.sum() == pytest.approx(1.0, abs=1e-13)
 
 
 @pytest.mark.parametrize("Q", [8, 16, 24, 32])
@@ -130,14 +134,16 @@ def test_equilibrium_moments_exact_up_to_order_Q_minus_1(Q):
     np.testing.assert_allclose(O.equilibrium(p, w, 1.0, 0.0, 1.0), w, rtol=1e-15)
 
 
-def test_moments_of_equilibrium_state():
-    """Moments of (phi, theta) = (n g_k, 2 T n g_k) return (n, u, T, Pi = n T, q = 0)."""
-    p, w = O.quadrature(16)
+@pytest.mark.parametrize("Q", [16, 64, 200])
+def test_moments_of_equilibrium_state(Q):
+    """Moments of (phi, theta) = (n g_k, 2 T n g_k) return (n, u, T, Pi = n T, q = 0), also for the large
+    velocity sets of the near-ballistic runs."""
+    p, w = O.quadrature(Q)
     for n, u, T in ((1.0, 0.0, 1.0), (0.7, -0.3, 1.6), (2.0, 1.1, 0.8)):
         f = O.equilibrium(p, w, n, u, T)
         mo = O.moments(p, f, 2 * T * f)
-        np.testing.assert_allclose(mo[:4], (n, u, T, n * T), rtol=1e-12, atol=1e-15)
-        assert abs(mo[4]) < 1e-12
+        np.testing.assert_allclose(mo[:4], (n, u, T, n * T), rtol=1e-11, atol=1e-14)
+        assert abs(mo[4]) < 1e-11
 
 
 # ----------------------------------------------------------------- Sec. II.B-C collision terms
