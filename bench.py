@@ -51,12 +51,21 @@ def _tensor_roofline(achieved_tflops):
             "kernel": "closure training step: conv_kernel, wgrad_kernel, transposed conv_kernel"}
 
 
-def _kernel_hash():
+# Sources the stage kernels of each precision are compiled from (the unit and what it includes).
+_STAGE_SOURCES = {
+    "fp32": ("paper_2211_16933_gb300/csrc/fdlb_f32.cu", "paper_2211_16933_gb300/csrc/fdlb_impl.cuh",
+             "paper_2211_16933_gb300/csrc/fdlb_kernels.cuh", "paper_2211_16933_gb300/csrc/qlbm_internal.h",
+             "include/qlbm.h"),
+    "fp64": ("paper_2211_16933_gb300/csrc/fdlb_f64.cu", "paper_2211_16933_gb300/csrc/fdlb_impl.cuh",
+             "paper_2211_16933_gb300/csrc/fdlb_kernels.cuh", "paper_2211_16933_gb300/csrc/fdlb_lq.cuh",
+             "paper_2211_16933_gb300/csrc/qlbm_internal.h", "include/qlbm.h"),
+}
+
+
+def _kernel_hash(precision_name="fp32"):
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2211_16933_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.startswith("fdlb_") or f == "qlbm_internal.h":
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in _STAGE_SOURCES[precision_name]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -65,7 +74,7 @@ def _traffic(precision_name):
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
         e = t.get(precision_name)
-        if e and e.get("kernel_hash") == _kernel_hash():
+        if e and e.get("kernel_hash") == _kernel_hash(precision_name):
             return e["dram_bytes_per_launch"]
     except Exception:
         pass

@@ -416,11 +416,19 @@ void oq_weno5_weights(double b1, double b2, double b3, double *om)
     if (z1) { om[0] = 1.0; om[1] = 0.0; om[2] = 0.0; return; }
     if (z2) { om[0] = 0.0; om[1] = 1.0; om[2] = 0.0; return; }
     if (z3) { om[0] = 0.0; om[1] = 0.0; om[2] = 1.0; return; }
-    double t1 = d1 / (b1 * b1), t2 = d2 / (b2 * b2), t3 = d3 / (b3 * b3);
-    double s = t1 + t2 + t3;
-    om[0] = t1 / s;
-    om[1] = t2 / s;
-    om[2] = t3 / s;
+    /* (d_q / b_q^2) / sum_s (d_s / b_s^2) written as d_q / sum_s d_s (b_q / b_s)^2
+     * (READING c23): the same quotient, but no square of an indicator is formed,
+     * so indicators below 1e-154 (outer nodes of large velocity sets) do not
+     * underflow to inf / inf; a ratio that overflows gives the weight 0. */
+    const double d[3] = {d1, d2, d3}, b[3] = {b1, b2, b3};
+    for (int q = 0; q < 3; ++q) {
+        double s = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            double t = b[q] / b[r];
+            s += d[r] * (t * t);
+        }
+        om[q] = d[q] / s;
+    }
 }
 
 /* App. A.2, Eqs. (weno5_flux_x), (weno5_sigma): WENO-5 value of f at the

@@ -19,7 +19,7 @@ MUTATIONS = {
     "j1_phi_missing_Y": ("j1phi[k] = -Y * bphi * fmb[k];", "j1phi[k] = -bphi * fmb[k];"),
     "j1_phi_du_coeff": ("0.6 * (xi * xi / T - 1.0) * du +", "0.6 * (xi * xi / T - 1.0 / 3.0) * du +"),
     "shakhov_phi_poly": ("(1.0 + a * (xi * xi / T - 3.0) * xi * q)", "(1.0 + a * (xi * xi / T - 1.0) * xi * q)"),
-    "weno_weight_power": ("t2 = d2 / (b2 * b2)", "t2 = d2 / b2"),
+    "weno_weight_power": ("s += d[r] * (t * t);", "s += d[r] * t;"),
     "weno_candidate_sign": ("F3 = f0 / 3.0 + 5.0 * fp1 / 6.0 - fp2 / 6.0", "F3 = f0 / 3.0 + 5.0 * fp1 / 6.0 + fp2 / 6.0"),
     "weno_mirror_index": ("s[r] = ef[(size_t)(j + 3 - r) * Q + k];", "s[r] = ef[(size_t)(j + 2 - r) * Q + k];"),
     "cd6_coeff": ("3.0 * q[4] / 4.0", "3.0 * q[4] / 5.0"),

@@ -255,6 +255,21 @@ def test_weno_weights_limits_of_general_formula():
     np.testing.assert_allclose(O.weno5_weights(*b), t / t.sum(), rtol=1e-15)
 
 
+def test_weno_is_scale_invariant_down_to_the_smallest_weights():
+    """The weights depend on the ratios of the indicators only and the face value is homogeneous of degree one
+    in f: both hold at the magnitudes of the outer nodes of Q = 200 (psi ~ 1e-165, indicators ~ 1e-330 would
+    underflow if squared; READING c23), where the quotient form gives inf / inf."""
+    for b in ((0.2, 0.5, 0.9), (1.0, 1e-30, 3.0), (2.0, 1.0, 1e-100)):
+        ref = O.weno5_weights(*b)
+        for c in (1e-200, 1e-150, 1e150, 1e200):  # every scaled indicator stays a normal double
+            got = O.weno5_weights(*(c * x for x in b))
+            np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-300)
+    f = np.array([0.3, -0.1, 0.7, 1.2, 0.4])
+    ref = O.weno5_face(f)
+    for c in (2.0 ** -540, 1e-160, 1e-100):
+        assert O.weno5_face(c * f) == pytest.approx(c * ref, rel=1e-13)
+
+
 def _weno_derivative(f, dx):
     """(face_{i+1/2} - face_{i-1/2})/dx on a periodic array, positive advection."""
     N = len(f)
