@@ -93,17 +93,34 @@ __device__ __forceinline__ float rcp_<float>(float x) { return __fdividef(1.0f, 
 template <>
 __device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
 
-// 2^-e for x in [2^e, 2^(e+1)): an exact power-of-two rescaling factor, x >= 0.
+// An exact power of two s with s x in [1, 4), for finite x >= 0 (s = 2^(e'-bias)
+// where e' is the complement of x's exponent field with its lowest bit
+// cleared; x = 0 gives a large finite s): one logic operation.
 __device__ __forceinline__ float pow2_recip_(float x)
 {
-    const unsigned e = __float_as_uint(x) & 0x7F800000u;
-    return __uint_as_float(0x7F000000u - e);
+    return __uint_as_float(~__float_as_uint(x) & 0x7F000000u);
 }
 __device__ __forceinline__ double pow2_recip_(double x)
 {
-    const int e = __double2hiint(x) & 0x7FF00000;
-    return __hiloint2double(0x7FE00000 - e, 0);
+    return __hiloint2double(~__double2hiint(x) & 0x7FE00000, 0);
 }
+
+// max(a, b, c) of finite values (a single three-input max in FP32).
+__device__ __forceinline__ float max3_(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double max3_(double a, double b, double c) { return fmax(a, fmax(b, c)); }
+
+// Smallest positive normal number of the working precision.
+template <typename Real>
+__device__ __forceinline__ Real min_normal_();
+template <>
+__device__ __forceinline__ float min_normal_<float>() { return 1.17549435e-38f; }
+template <>
+__device__ __forceinline__ double min_normal_<double>() { return 2.2250738585072014e-308; }
 
 // ---------------------------------------------------------------------------
 // Double-FP32 arithmetic: a value held as the unevaluated sum h + l of two
@@ -189,7 +206,7 @@ __device__ __forceinline__ P2<Real> weno5_face2(P2<Real> fm2, P2<Real> fm1, P2<R
     const V c1 = fma2(sp2(Real(1.0 / 30.0)), Dm2n, mul2(sp2(Real(1.0 / 12.0)), Dm1));
     const V c2 = fma2(sp2(Real(0.1)), Dm1, D0x);
     const V c3 = fma2(sp2(Real(-0.05)), D1, D0x);
-    const V sc = mk2(pow2_recip_(max_(b1.x, max_(b2.x, b3.x))), pow2_recip_(max_(b1.y, max_(b2.y, b3.y))));
+    const V sc = mk2(pow2_recip_(max3_(b1.x, b2.x, b3.x)), pow2_recip_(max3_(b1.y, b2.y, b3.y)));
     b1 = mul2(b1, sc);
     b2 = mul2(b2, sc);
     b3 = mul2(b3, sc);
@@ -200,8 +217,11 @@ __device__ __forceinline__ P2<Real> weno5_face2(P2<Real> fm2, P2<Real> fm1, P2<R
     // D = 0 only when two or three indicators vanish.  beta_q = 0 means the three
     // values of stencil q are equal, so two vanishing indicators make the union of
     // those stencils constant, the candidates that carry weight in Table weno_x
-    // equal f0 there, and the face value is f0 (num = 0 in that case too).
-    const V rD = mk2(D.x > Real(0) ? rcp_(D.x) : Real(0), D.y > Real(0) ? rcp_(D.y) : Real(0));
+    // equal f0 there, and the face value is f0: num = 0 in that case too, and D is
+    // raised to the smallest normal number so that its reciprocal stays finite
+    // (a D below it would have no finite FP32 reciprocal either).
+    const Real dmin = min_normal_<Real>();
+    const V rD = mk2(rcp_(max_(D.x, dmin)), rcp_(max_(D.y, dmin)));
     return fma2(num, rD, f0);
 }
 
@@ -629,17 +649,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             out[ip] = op;
             out[im] = om;
             if (RET && STAGE != 0) s_nout[s] += op.x + om.x;
-            if (STAGE != 0 && a.periodic) {
-                // periodic images in the ghost columns of the other end
-                if (i < kHalo) {
-                    out[ip + a.nx] = op;
-                    out[im + a.nx] = om;
-                }
-                if (i >= a.nx - kHalo) {
-                    out[ip - a.nx] = op;
-                    out[im - a.nx] = om;
-                }
-            }
+        }
+    }
+    if (STAGE != 0 && a.periodic && owner && (i < kHalo || i >= a.nx - kHalo)) {
+        // periodic images in the ghost columns of the other end: this thread
+        // copies the column it has just written (its own stores, read back)
+        for (int k = 0; k < Q; ++k) {
+            const V v = out[int64_t(k) * stride + col];
+            if (i < kHalo) out[int64_t(k) * stride + col + a.nx] = v;
+            if (i >= a.nx - kHalo) out[int64_t(k) * stride + col - a.nx] = v;
         }
     }
     if (RET && STAGE != 0 && owner) static_cast<Real *>(a.nout)[i] = s_nout[s];
