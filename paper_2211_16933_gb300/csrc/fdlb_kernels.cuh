@@ -304,12 +304,13 @@ struct TileShape {
 };
 
 // Shared memory of one stage CTA: the staged rows, the table rows of p > 0,
-// 6 per-cell arrays, and 2 more for chi_RET-FM.
+// 6 per-cell arrays, 2 more for chi_RET-FM, and 3 pairs per velocity pair.
 template <typename Real, int Q, int WARPS, bool RET = false>
 constexpr size_t stage_smem_bytes()
 {
     constexpr int SEG = TileShape<WARPS>::seg;
-    return sizeof(P2<Real>) * size_t(Q) * SEG + sizeof(Real) * (size_t(Q / 2) * Q + (RET ? 8 : 6) * size_t(SEG));
+    return sizeof(P2<Real>) * size_t(Q) * SEG + sizeof(Real) * (size_t(Q / 2) * Q + (RET ? 8 : 6) * size_t(SEG)) +
+           sizeof(P2<Real>) * 3 * size_t(Q / 2);
 }
 
 // 1: the FP32 mode combines its per-cell conserved sums in FP64 instead of
@@ -326,7 +327,7 @@ constexpr int kStageLoadUnroll = QL_STAGE_LOAD_UNROLL;
 
 // Velocity pairs of the update loop per iteration.
 #ifndef QL_VLOOP_UNROLL
-#define QL_VLOOP_UNROLL 2
+#define QL_VLOOP_UNROLL 4
 #endif
 constexpr int kVelocityLoopUnroll = QL_VLOOP_UNROLL;
 
@@ -360,7 +361,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     Real *s_lnT = s_lnn + SEG;
     Real *s_lnchi = s_lnT + SEG;  // chi_RET-FM: nbar, then ln chi(nbar)
     Real *s_nout = s_lnchi + SEG; // chi_RET-FM: density of the output, per owned cell
+    // per velocity pair j: (p, p), (p^2, p^2), (w dt p / dx, w dt p / dx)
+    V *s_pt = reinterpret_cast<V *>(s_n + SEG * (RET ? 8 : 6));
     constexpr bool ret = RET;  // chi_RET-FM: a.nbar and a.nout are set
+    // Runge-Kutta weight of v = psi + dt L in the stage output (c psi^n + w v):
+    // 1, 1/4 and fl(2/3), whose complement 1 - w is exact (Sterbenz)
+    const Real rk_w = STAGE == 2 ? Real(0.25) : (STAGE == 3 ? Real(2.0 / 3.0) : Real(1));
 
     const int t = threadIdx.x;
     const int64_t stride = a.stride;
@@ -393,6 +399,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             }
         }
         for (int e = t; e < H * Q; e += THREADS) s_G[e] = QL_TAB[TV.G + H * Q + e];
+        if (t < H) {
+            const Real p = QL_TAB[TV.p + H + t];
+            const Real adv = STAGE == 0 ? Real(a.inv_dx) : Real(a.dt) * rk_w * Real(a.inv_dx);
+            s_pt[3 * t] = sp2(p);
+            s_pt[3 * t + 1] = sp2(QL_TAB[TV.p2 + H + t]);
+            s_pt[3 * t + 2] = sp2(p * adv);
+        }
         // nbar of staged cell c sits at column i0 + c (the buffer has a row stride of columns)
         if (ret)
             for (int c = t; c < SEG; c += THREADS) s_lnchi[c] = static_cast<const Real *>(a.nbar)[i0 + c];
@@ -519,25 +532,26 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     const Real rhat = n * Real(a.inv_rho_ref);
     const Real eta = Real(a.eta0) * rhat;
     const Real ome = Real(1) - eta;
-    const Real chi = ret ? exp_(s_lnchi[s]) : Real(0.5) * (Real(2) - eta) / (ome * ome * ome);
+    const Real rome = rcp_(ome);
+    const Real chi = ret ? exp_(s_lnchi[s]) : Real(0.5) * (Real(2) - eta) * (rome * rome * rome);
     const Real Y = Real(4) * eta * chi;
     const Real muf = fma_(fma_(Real(0.16 * (1.0 + 12.0 / 3.14159265358979323846)), Y, Real(0.8)), Y, Real(1));
     const Real sqT = T * rsqrt_(T);
-    const Real inv_tau = rhat * chi * sqT / (Real(a.tau_pref) * muf);
+    const Real inv_tau = rhat * chi * sqT * rcp_(Real(a.tau_pref) * muf);
     Real Pr = Real(a.pr_const);
     if (a.pr_mode) {
         const Real laf =
             fma_(fma_(Real(0.36 * (1.0 + 32.0 / (9.0 * 3.14159265358979323846))), Y, Real(1.2)), Y, Real(1));
-        Pr = Real(2.0 / 3.0) * muf / laf;
+        Pr = Real(2.0 / 3.0) * muf * rcp_(laf);
     }
-    const Real invT = Real(1) / T;
+    const Real invT = rcp_(T);
     // Shakhov: A = (1 - Pr) q / (5 P_i T), P_i = n T
-    const Real A = (Real(1) - Pr) * q * invT * invT / (Real(5) * n);
+    const Real A = (Real(1) - Pr) * q * invT * invT * (Real(0.2) * rcp_(n));
     const Real Yj = a.enskog ? Y : Real(0);
     // chi_SET: d ln chi = eta (3/(1-eta) - 1/(2-eta)) d ln rho (chi depends on the local eta only);
     // chi_RET-FM: 6th-order difference of ln chi(nbar)
     const Real dlnchi =
-        ret ? cd6_(s_lnchi, s) * inv_dx : eta * (Real(3) / ome - Real(1) / (Real(2) - eta)) * dlnn;
+        ret ? cd6_(s_lnchi, s) * inv_dx : eta * (Real(3) * rome - rcp_(Real(2) - eta)) * dlnn;
     const Real G = dlnchi + Real(2) * dlnn;
     // Targets over the equilibrium, cubic in xi = p_k - u:
     //   phi:   (1/tau)(1 + A xi (xi^2/T - 3)) - Y [xi G + 3/5 (xi^2/T - 1) du + 3/10 (xi^3/T + xi/3) dlnT]
@@ -550,11 +564,26 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     const Real a3 = (A * inv_tau - Real(0.3) * Yj * dlnT) * invT;
     const Real b0 = fma_(Real(0.2) * Yj, du, inv_tau);
     const Real b1 = -A * inv_tau - Yj * G - Real(0.7) * Yj * dlnT;
-    // Stages 1-3 fold dt into the targets (see the velocity loop).
-    const Real ndt = STAGE == 0 ? n : n * Real(a.dt);
+    // Stages 1-3 fold dt and the Runge-Kutta weight of v into the targets (see
+    // the velocity loop).
+    const Real ndt = STAGE == 0 ? n : n * (Real(a.dt) * rk_w);
     const Real nphi = ndt, nth = Real(2) * T * ndt;
     const V C0 = mk2(a0 * nphi, b0 * nth), C1 = mk2(a1 * nphi, b1 * nth);
     const V C2 = mk2(a2 * nphi, a2 * nth), C3 = mk2(a3 * nphi, a3 * nth);
+    // The same cubic as a polynomial in y = xi + u = +-p (Taylor shift by -u,
+    // Horner's scheme): P(+-p) = E(p^2) +- p O(p^2) with E = D0 + D2 p^2 and
+    // O = D1 + D3 p^2, so both velocities of a pair share E and O.
+    V D0 = C0, D1 = C1, D2 = C2;
+    const V D3 = C3;
+    {
+        const V mu = sp2(-u);
+        D2 = fma2(mu, D3, D2);
+        D1 = fma2(mu, D2, D1);
+        D0 = fma2(mu, D1, D0);
+        D2 = fma2(mu, D3, D2);
+        D1 = fma2(mu, D2, D1);
+        D2 = fma2(mu, D3, D2);
+    }
 
     // Normalised Hermite coefficients of the equilibrium, Eq. (g_alpha):
     // c^_0 = 1, c^_1 = u, c^_l = u c^_{l-1}/sqrt(l) + (T-1) c^_{l-2} sqrt((l-1)/l),
@@ -575,11 +604,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
     }
 
     // STAGE 0: L[psi] = target - psi / tau - advection.  Stages 1-3 form
-    // v = psi + dt L[psi] directly as (1 - dt/tau) psi + dt target - dt advection,
-    // the targets already scaled by dt: two packed operations fewer per velocity.
+    // w v = w (psi + dt L[psi]) directly as w (1 - dt/tau) psi + w dt target -
+    // w dt advection (targets and the advection table already scaled by w dt).
     const Real dt = Real(a.dt);
-    const V kpsi = sp2(STAGE == 0 ? -inv_tau : Real(1) - dt * inv_tau);
-    const Real adv_scale = STAGE == 0 ? inv_dx : dt * inv_dx;
+    const V kpsi = sp2(STAGE == 0 ? -inv_tau : rk_w * (Real(1) - dt * inv_tau));
     const V *__restrict__ base = static_cast<const V *>(a.base);
     V *out = static_cast<V *>(a.out);
     const int64_t col = kHalo + i;
@@ -610,7 +638,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             bp = base[ip];
             bm = base[im];
         }
-        const Real p = QL_TAB[TV.p + kp];
+        // (p, p), (p^2, p^2), (w dt p / dx, w dt p / dx) of this pair (p / dx for STAGE 0)
+        const V *pt = s_pt + 3 * j;
         const V *rp = s_psi + kp * SEG;
         const V *rm = s_psi + km * SEG;
         // WENO-5 values at the right face of s: upwind stencil for +p, mirrored for -p
@@ -619,7 +648,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
         const V hm = weno5_face2<Real>(rm[s + 3], rm[s + 2], rm[s + 1], fm0, rm[s - 1]);
         const V hpl = mk2(__shfl_up_sync(0xffffffffu, hp.x, 1), __shfl_up_sync(0xffffffffu, hp.y, 1));
         const V hml = mk2(__shfl_up_sync(0xffffffffu, hm.x, 1), __shfl_up_sync(0xffffffffu, hm.y, 1));
-        const Real pa = p * adv_scale;
 
         // g at +p and -p: even and odd Hermite parts, h_l(-p) = (-1)^l h_l(p)
         V eo = sp2(Real(0));
@@ -629,22 +657,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
         const Real gpv = eo.x + eo.y, gmv = eo.x - eo.y;
 
         // targets, Eq. (cast): L[psi] = target - psi / tau - (p/dx)(h - h_left) for
-        // STAGE 0, v = psi + dt L[psi] for stages 1-3 (targets and advection scaled by dt)
-        const Real xp = p - u, xm = -p - u;
-        const V Pp = fma2(fma2(fma2(C3, sp2(xp), C2), sp2(xp), C1), sp2(xp), C0);
-        const V Pm = fma2(fma2(fma2(C3, sp2(xm), C2), sp2(xm), C1), sp2(xm), C0);
-        const V vp = fma2(sp2(-pa), sub2(hp, hpl), fma2(fp0, kpsi, mul2(sp2(gpv), Pp)));
-        const V vm = fma2(sp2(pa), sub2(hm, hml), fma2(fm0, kpsi, mul2(sp2(gmv), Pm)));
+        // STAGE 0, w v = w (psi + dt L[psi]) for stages 1-3
+        const V E = fma2(D2, pt[1], D0);
+        const V O = mul2(fma2(D3, pt[1], D1), pt[0]);
+        const V Pp = add2(E, O), Pm = sub2(E, O);
+        const V vp = fma2(pt[2], sub2(hpl, hp), fma2(fp0, kpsi, mul2(sp2(gpv), Pp)));
+        const V vm = fma2(pt[2], sub2(hm, hml), fma2(fm0, kpsi, mul2(sp2(gmv), Pm)));
 
         if (owner) {
             V op = vp, om = vm;
             if (STAGE >= 2) {
-                // 3/4 psi^n + 1/4 v and 1/3 psi^n + 2/3 v, written as v + c (psi^n - v)
-                // so that the two weights sum to exactly one in any precision (1/3 and
-                // 2/3 rounded to FP32 sum to 1 + 4e-8, a per-step bias)
-                const V c = sp2(STAGE == 2 ? Real(0.75) : Real(1.0 / 3.0));
-                op = fma2(c, sub2(bp, vp), vp);
-                om = fma2(c, sub2(bm, vm), vm);
+                // c psi^n + w v with (c, w) = (3/4, 1/4) and (1 - fl(2/3), fl(2/3)):
+                // the two weights sum to exactly one in any precision (1/3 and 2/3
+                // both rounded to FP32 sum to 1 + 4e-8, a per-step bias)
+                const V c = sp2(Real(1) - rk_w);
+                op = fma2(c, bp, vp);
+                om = fma2(c, bm, vm);
             }
             out[ip] = op;
             out[im] = om;
