@@ -328,6 +328,20 @@ ql_status ql_closure_gradients(ql_closure *c, const float *x, const float *y, co
 ql_status ql_closure_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
                                 int64_t B, float lr, float *loss);
 
+/* nsteps Adam steps on mini-batches drawn on the device (the training loop of
+ * the learned closure without a host round trip per step).  x [n][positions]
+ * [in_channels], y [n][positions][out_channels] and periodic [n] hold the whole
+ * training set on the device; perm (device, nsteps * B int32) lists the samples
+ * of step s at perm[s B .. s B + B - 1]; lr (host, nsteps floats) the learning
+ * rate of each step; losses (device, nsteps floats, may be NULL) receives the
+ * mean squared error of each step's batch before its update.  The same
+ * arithmetic as nsteps calls of ql_closure_train_step on the gathered batches.
+ * Synchronises once at the end; an index of perm outside [0, n) returns
+ * QL_EINVAL (sample 0 is used in its place, nothing is read out of bounds). */
+ql_status ql_closure_train_steps(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
+                                 int64_t n, const int32_t *perm, int64_t nsteps, int64_t B, const float *lr,
+                                 float *losses);
+
 /* Parameter vector (f32, host): for each layer W[cout][ksize][cin] then
  * bias[cout], channels padded to 16 (padding stays zero).  get and set may be
  * NULL; count (may be NULL) receives the length.  Synchronises. */

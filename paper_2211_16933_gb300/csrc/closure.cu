@@ -372,6 +372,47 @@ __global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npo
     y[e] = pred[pos * coutp + c] * out_scale[c];
 }
 
+// Mini-batch b of a training run: sample idx[b] of the device data set (n
+// samples) copied into the contiguous batch buffers.  An index outside [0, n)
+// sets *bad and is replaced by 0, so that nothing is read out of bounds.
+__global__ void gather_batch_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                    const int32_t *__restrict__ per, const int32_t *__restrict__ idx, int64_t n,
+                                    int B, int64_t xrow, int64_t yrow, float *__restrict__ xb, float *__restrict__ yb,
+                                    int32_t *__restrict__ perb, unsigned *__restrict__ bad)
+{
+    const int64_t total = int64_t(B) * (xrow + yrow + 1);
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t per_sample = xrow + yrow + 1;
+        const int b = int(e / per_sample);
+        const int64_t r = e - int64_t(b) * per_sample;
+        int64_t k = idx[b];
+        if (k < 0 || k >= n) {
+            if (r == 0) atomicOr(bad, 1u);
+            k = 0;
+        }
+        if (r < xrow) xb[int64_t(b) * xrow + r] = x[k * xrow + r];
+        else if (r < xrow + yrow) yb[int64_t(b) * yrow + (r - xrow)] = y[k * yrow + (r - xrow)];
+        else perb[b] = per[k];
+    }
+}
+
+// Mean loss of one batch from the per-block partial sums of mse_kernel, summed
+// in a fixed order by one block.
+__global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, float scale, float *__restrict__ out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += double(partial[i]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (int(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = float(red[0] * double(scale));
+}
+
 // Adam on FP32 master parameters; refreshes the bf16 weight copies, the
 // tap-flipped transposed copies used by the backward pass, and the f32 biases.
 struct AdamArgs {
@@ -488,6 +529,10 @@ struct ql_closure {
     float *loss_partial = nullptr;
     float *edge = nullptr;  // [max_batch][2][64] end-position gradient terms of replicate padding
     float *norm = nullptr;  // in_shift[8], in_inv_scale[8], out_scale[8], inv_out_scale[8]
+    // mini-batch buffers of ql_closure_train_steps and its out-of-range index flag
+    float *xb = nullptr, *yb = nullptr;
+    int32_t *perb = nullptr;
+    unsigned *bad = nullptr;
     int wgrid = 0;
     int64_t step = 0;
     std::string err;
@@ -519,7 +564,7 @@ static void closure_release(ql_closure *c)
 {
     for (void *p : {(void *)c->param, (void *)c->grad, (void *)c->m, (void *)c->v, (void *)c->w16, (void *)c->wt16,
                     (void *)c->pred, (void *)c->partial, (void *)c->loss_partial, (void *)c->edge,
-                    (void *)c->norm})
+                    (void *)c->norm, (void *)c->xb, (void *)c->yb, (void *)c->perb, (void *)c->bad})
         cfree_dev(c, p);
     for (bf16 *p : c->act) cfree_dev(c, p);
     for (bf16 *p : c->dz) cfree_dev(c, p);
@@ -574,6 +619,8 @@ static ql_status pack(ql_closure *c, const float *x, int B)
     QC_CUDA(c, cudaGetLastError());
     return QL_OK;
 }
+
+static ql_status adam_step(ql_closure *c, float lr);
 
 // Loss, gradients of all parameters into c->grad; loss (host) if not null.
 static ql_status backward(ql_closure *c, const float *y, const int *per, int B, float *loss)
@@ -672,8 +719,12 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
     c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(c->wgrid) * (64 * kTaps * 64 + 64)));
     c->loss_partial = static_cast<float *>(calloc_dev(c, sizeof(float) * ((npos * 16 + 255) / 256)));
     c->edge = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(B) * 2 * 64));
+    c->xb = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * d->in_channels));
+    c->yb = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * d->out_channels));
+    c->perb = static_cast<int32_t *>(calloc_dev(c, sizeof(int32_t) * size_t(B)));
+    c->bad = static_cast<unsigned *>(calloc_dev(c, sizeof(unsigned)));
     bool ok = c->param && c->grad && c->m && c->v && c->w16 && c->wt16 && c->pred && c->norm && c->partial &&
-              c->loss_partial && c->edge;
+              c->loss_partial && c->edge && c->xb && c->yb && c->perb && c->bad;
     for (int l = 0; l < d->layers; ++l) ok = ok && c->act[l] && c->dz[l];
     if (!ok) return bail(QL_ENOMEM, "closure allocation failed");
 
@@ -745,6 +796,47 @@ ql_status ql_closure_train_step(ql_closure *c, const float *x, const float *y, c
 {
     ql_status st = ql_closure_gradients(c, x, y, periodic, B, loss, nullptr);
     if (st != QL_OK) return st;
+    return adam_step(c, lr);
+}
+
+ql_status ql_closure_train_steps(ql_closure *c, const float *x, const float *y, const int32_t *periodic, int64_t n,
+                                 const int32_t *perm, int64_t nsteps, int64_t B, const float *lr, float *losses)
+{
+    if (!c || !x || !y || !periodic || !perm || n < 1 || nsteps < 0 || B < 1 || B > c->d.max_batch ||
+        (nsteps > 0 && !lr))
+        return cfail(c, QL_EINVAL, "bad arguments");
+    const int X = c->d.positions;
+    const int64_t xrow = int64_t(X) * c->d.in_channels, yrow = int64_t(X) * c->d.out_channels;
+    const int64_t npos = B * X;
+    const unsigned nb = unsigned((npos * c->layers.back().cout + 255) / 256);
+    const float lscale = float(1.0 / double(npos * c->d.out_channels));
+    QC_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(unsigned), c->stream));
+    for (int64_t s = 0; s < nsteps; ++s) {
+        gather_batch_kernel<<<unsigned((B * (xrow + yrow + 1) + 255) / 256), 256, 0, c->stream>>>(
+            x, y, periodic, perm + s * B, n, int(B), xrow, yrow, c->xb, c->yb, c->perb, c->bad);
+        QC_CUDA(c, cudaGetLastError());
+        ql_status st = pack(c, c->xb, int(B));
+        if (st == QL_OK) st = forward(c, c->perb, int(B));
+        if (st == QL_OK) st = backward(c, c->yb, c->perb, int(B), nullptr);
+        if (st != QL_OK) return st;
+        if (losses) {
+            loss_sum_kernel<<<1, 256, 0, c->stream>>>(c->loss_partial, int(nb), lscale, losses + s);
+            QC_CUDA(c, cudaGetLastError());
+        }
+        st = adam_step(c, lr[s]);
+        if (st != QL_OK) return st;
+    }
+    unsigned bad = 0;
+    QC_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    QC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) return cfail(c, QL_EINVAL, "perm holds a sample index outside [0, n); sample 0 was used in its place");
+    return QL_OK;
+}
+
+}  // extern "C"
+
+static ql_status adam_step(ql_closure *c, float lr)
+{
     c->step += 1;
     AdamArgs a;
     a.param = c->param;
@@ -762,6 +854,8 @@ ql_status ql_closure_train_step(ql_closure *c, const float *x, const float *y, c
     QC_CUDA(c, cudaGetLastError());
     return refresh_weights(c);
 }
+
+extern "C" {
 
 ql_status ql_closure_params(ql_closure *c, float *get_host, const float *set_host, int64_t *count)
 {

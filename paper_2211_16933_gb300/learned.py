@@ -120,8 +120,10 @@ def norm_stats(x, y):
 
 
 def train(x, y, periodic, epochs=10, batch=256, lr=1e-3, seed=0, log=None, lr_final=None):
-    """Trains a closure on device tensors; returns it and the per-epoch mean losses (sampled every
-    16th step).  The learning rate follows a cosine from lr down to lr_final (default lr / 20)."""
+    """Trains a closure on device tensors; returns it and the per-epoch mean losses (each step's loss
+    before its update).  The learning rate follows a cosine from lr down to lr_final (default lr / 20).
+    Each epoch is one ql_closure_train_steps call: the mini-batches of a seeded permutation are gathered
+    on the device, with no host round trip per step."""
     import torch
     xm, xsd, ysd = norm_stats(x, y)
     net = q.Closure(x.shape[2], y.shape[2], x.shape[1], batch, seed=seed, in_shift=xm, in_scale=xsd,
@@ -130,23 +132,18 @@ def train(x, y, periodic, epochs=10, batch=256, lr=1e-3, seed=0, log=None, lr_fi
     g.manual_seed(seed)
     losses = []
     n = x.shape[0]
+    per_epoch = n // batch
     lr_final = lr / 20.0 if lr_final is None else lr_final
-    total = max(1, epochs * (n // batch))
-    step = 0
+    total = max(1, epochs * per_epoch)
+    x, y = x.contiguous(), y.contiguous()
+    per32 = periodic.to(torch.int32).contiguous()
+    step_loss = torch.empty(per_epoch, dtype=torch.float32, device=x.device)
     for ep in range(epochs):
-        perm = torch.randperm(n, device=x.device, generator=g)
-        tot, cnt = 0.0, 0
-        for s in range(0, n - batch + 1, batch):
-            idx = perm[s:s + batch]
-            want = (s // batch) % 16 == 0
-            cur = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / total))
-            step += 1
-            l = net.train_step(x[idx].contiguous(), y[idx].contiguous(), periodic[idx].contiguous(), cur,
-                               want_loss=want)
-            if want:
-                tot += l
-                cnt += 1
-        losses.append(tot / max(cnt, 1))
+        perm = torch.randperm(n, device=x.device, generator=g)[:per_epoch * batch].to(torch.int32).contiguous()
+        steps = np.arange(ep * per_epoch, (ep + 1) * per_epoch)
+        rates = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * steps / total))
+        net.train_steps(x, y, per32, perm, rates, step_loss)
+        losses.append(float(step_loss.mean().item()) if per_epoch > 0 else 0.0)
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.4e}")
     return net, losses

@@ -31,7 +31,8 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
             "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc",
             "ql_batch_fields", "ql_batch_project", "ql_sound_modes", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
-            "ql_closure_train_step", "ql_closure_params", "ql_closure_destroy", "ql_closure_last_error")
+            "ql_closure_train_step", "ql_closure_train_steps", "ql_closure_params", "ql_closure_destroy",
+            "ql_closure_last_error")
 
 
 class QLError(RuntimeError):
@@ -134,6 +135,8 @@ def lib():
         L.ql_closure_forward.argtypes = [V, V, V, C.c_int64, V]
         L.ql_closure_gradients.argtypes = [V, V, V, V, C.c_int64, F, F]
         L.ql_closure_train_step.argtypes = [V, V, V, V, C.c_int64, C.c_float, F]
+        L.ql_closure_train_steps.argtypes = [V, V, V, V, C.c_int64, V, C.c_int64, C.c_int64,
+                                             C.POINTER(C.c_float), V]
         L.ql_closure_params.argtypes = [V, F, F, C.POINTER(C.c_int64)]
         L.ql_closure_destroy.argtypes = [V]
         L.ql_closure_last_error.argtypes = [V]
@@ -438,6 +441,22 @@ class Closure:
                                             C.c_void_p(periodic.data_ptr()), x.shape[0], lr,
                                             C.byref(loss) if want_loss else None), self.c)
         return loss.value if want_loss else None
+
+    def train_steps(self, x, y, periodic, perm, lr, losses=None):
+        """len(lr) Adam steps on batches gathered on the device: step s takes the samples
+        perm[s B:(s + 1) B] of the device tensors x, y, periodic (B = len(perm) // len(lr)); losses (device
+        float32 tensor of len(lr), optional) receives each step's loss.  Synchronises once."""
+        lr = np.ascontiguousarray(lr, dtype=np.float32)
+        nsteps = len(lr)
+        if nsteps == 0:
+            return
+        B = perm.numel() // nsteps
+        _ccheck(lib().ql_closure_train_steps(self.c, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                             C.c_void_p(periodic.data_ptr()), x.shape[0],
+                                             C.c_void_p(perm.data_ptr()), nsteps, B,
+                                             lr.ctypes.data_as(C.POINTER(C.c_float)),
+                                             C.c_void_p(losses.data_ptr()) if losses is not None else None),
+                self.c)
 
     def nparams(self):
         n = C.c_int64()

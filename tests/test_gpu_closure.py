@@ -137,6 +137,39 @@ def test_training_reduces_a_regression_loss(gpu):
     assert l < 0.2 * first, (first, l)
 
 
+def test_device_training_loop_equals_single_steps(gpu):
+    """ql_closure_train_steps (mini-batches gathered on the device from a permutation, one call for many
+    steps) gives bitwise the parameters and losses of ql_closure_train_step on the same batches gathered by
+    the caller, with a ragged data set (n not a multiple of B) and mixed padding kinds."""
+    import torch
+    q = gpu
+    rng = np.random.default_rng(11)
+    n, B, X, steps = 45, 8, 96, 5
+    dev = torch.device("cuda", 0)
+    xd = torch.tensor(rng.normal(0, 1, (n, X, 7)).astype(np.float32), device=dev)
+    yd = torch.tensor(rng.normal(0, 0.5, (n, X, 5)).astype(np.float32), device=dev)
+    pd = torch.tensor(rng.integers(0, 2, n).astype(np.int32), device=dev)
+    perm = torch.tensor(rng.permutation(n)[:steps * B].astype(np.int32), device=dev)
+    rates = np.linspace(2e-3, 1e-3, steps).astype(np.float32)
+    a = q.Closure(7, 5, X, B, seed=9)
+    b = q.Closure(7, 5, X, B, seed=9)
+    losses = torch.zeros(steps, dtype=torch.float32, device=dev)
+    a.train_steps(xd, yd, pd, perm, rates, losses)
+    ref = []
+    for s in range(steps):
+        idx = perm[s * B:(s + 1) * B].long()
+        ref.append(b.train_step(xd[idx].contiguous(), yd[idx].contiguous(), pd[idx].contiguous(), float(rates[s]),
+                                want_loss=True))
+    np.testing.assert_array_equal(a.get_params(), b.get_params())
+    np.testing.assert_allclose(losses.cpu().numpy(), np.array(ref, dtype=np.float32), rtol=1e-6)
+    # an index outside the data set is reported, not read
+    bad = perm.clone()
+    bad[3] = n
+    with pytest.raises(q.QLError) as e:
+        a.train_steps(xd, yd, pd, bad[:B].contiguous(), rates[:1])
+    assert e.value.status == q.QL_EINVAL
+
+
 def test_trained_closure_improves_held_out_coarse_fields(gpu):
     from paper_2211_16933_gb300 import learned as L
     train_specs = L.pair_specs(48, 0)
