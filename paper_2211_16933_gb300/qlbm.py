@@ -159,10 +159,18 @@ def _check(st, ctx=None):
 
 
 # ---------------------------------------------------------------- host-only helpers
+_VELSET_CACHE = {}
+
+
 def ql_velocity_set(Q: int):
-    p, w = np.zeros(Q), np.zeros(Q)
-    _check(lib().ql_velocity_set(Q, _ptr(p), _ptr(w)))
-    return p, w
+    """Nodes and weights of the Q-point set (computed by the library once per Q, about a millisecond at
+    Q = 32; copies are returned)."""
+    if Q not in _VELSET_CACHE:
+        p, w = np.zeros(Q), np.zeros(Q)
+        _check(lib().ql_velocity_set(Q, _ptr(p), _ptr(w)))
+        _VELSET_CACHE[Q] = (p, w)
+    p, w = _VELSET_CACHE[Q]
+    return p.copy(), w.copy()
 
 
 def ql_eta_of_denseness(El: float) -> float:
