@@ -961,24 +961,36 @@ __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a,
 }
 
 // FP32 mode, domain totals only (ql_totals): mass, momentum and energy of every
-// cell as double-FP32 sums of exact products, a non-physical check on their
+// cell as double-FP32 sums of exact products (two packed accumulations per
+// velocity: (phi, theta) and (p phi, p^2 phi)), a non-physical check on their
 // leading parts, and block sums reduced in double-FP32 by warp shuffles, so
 // that no FP64 arithmetic runs per cell.
-__device__ __forceinline__ void ff_acc(FF &F, float x)
-{
-    const FF t = two_sum(F.h, x);
-    F = {t.h, F.l + t.l};
-}
-__device__ __forceinline__ void ff_acc_prod(FF &F, float ph, float pl, float x)
-{
-    const float prod = ph * x;
-    const float perr = fmaf(pl, x, fmaf(ph, x, -prod));
-    const FF t = two_sum(F.h, prod);
-    F = {t.h, F.l + (t.l + perr)};
-}
 __device__ __forceinline__ FF ff_shfl_down(FF v, int off)
 {
     return {__shfl_down_sync(0xffffffffu, v.h, off), __shfl_down_sync(0xffffffffu, v.l, off)};
+}
+
+// Packed double-FP32 accumulation of two independent sums (the two components
+// of a pair): error-free two-sum of the leading parts, errors gathered in l.
+struct FF2 {
+    float2 h, l;
+};
+__device__ __forceinline__ void ff2_acc(FF2 &F, float2 x)
+{
+    const float2 s = add2(F.h, x);
+    const float2 bb = sub2(s, F.h);
+    const float2 err = add2(sub2(F.h, sub2(s, bb)), sub2(x, bb));
+    F = {s, add2(F.l, err)};
+}
+// F += (ph + pl) x with the product's rounding error kept: nph = -ph.
+__device__ __forceinline__ void ff2_acc_prod(FF2 &F, float2 nph, float2 ph, float2 pl, float2 x)
+{
+    const float2 nprod = mul2(nph, x);                         // -fl(ph x)
+    const float2 perr = fma2(pl, x, fma2(ph, x, nprod));       // ph x - fl(ph x) + pl x
+    const float2 s = sub2(F.h, nprod);
+    const float2 bb = sub2(s, F.h);
+    const float2 err = sub2(sub2(F.h, sub2(s, bb)), add2(nprod, bb));
+    F = {s, add2(F.l, add2(err, perr))};
 }
 
 template <int Q>
@@ -986,31 +998,32 @@ __global__ void __launch_bounds__(kMomThreads) fdlb_totals_f32_kernel(MomentArgs
 {
     constexpr TabView TV = tab_view(Q);
     constexpr int NW = kMomThreads / 32;
-    __shared__ float s_pw[4][Q];  // p and p^2 as (hi, lo)
+    // per velocity: (p, p^2) leading parts, their negatives, and trailing parts
+    __shared__ float2 s_ph[Q], s_nph[Q], s_pl[Q];
     __shared__ FF s_red[3][NW];
     if (threadIdx.x < Q) {
         const double p = tab[TV.p + threadIdx.x], p2 = p * p;
-        s_pw[0][threadIdx.x] = float(p);
-        s_pw[1][threadIdx.x] = float(p - double(float(p)));
-        s_pw[2][threadIdx.x] = float(p2);
-        s_pw[3][threadIdx.x] = float(p2 - double(float(p2)));
+        const float2 h = make_float2(float(p), float(p2));
+        s_ph[threadIdx.x] = h;
+        s_nph[threadIdx.x] = make_float2(-h.x, -h.y);
+        s_pl[threadIdx.x] = make_float2(float(p - double(h.x)), float(p2 - double(h.y)));
     }
     __syncthreads();
     const P2<float> *__restrict__ psi = static_cast<const P2<float> *>(a.psi);
     const int64_t i = int64_t(blockIdx.x) * kMomThreads + threadIdx.x;
     FF tot[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (i < a.nx) {
-        FF S0{0.f, 0.f}, S1{0.f, 0.f}, S2{0.f, 0.f}, R0{0.f, 0.f};
+        // (S0, R0) = (sum phi, sum theta), (S1, S2) = (sum p phi, sum p^2 phi)
+        FF2 A{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, B = A;
+#pragma unroll 8
         for (int k = 0; k < Q; ++k) {
-            const P2<float> v = psi[int64_t(k) * a.stride + kHalo + i];
-            ff_acc(S0, v.x);
-            ff_acc_prod(S1, s_pw[0][k], s_pw[1][k], v.x);
-            ff_acc_prod(S2, s_pw[2][k], s_pw[3][k], v.x);
-            ff_acc(R0, v.y);
+            const float2 v = psi[int64_t(k) * a.stride + kHalo + i];
+            ff2_acc(A, v);
+            ff2_acc_prod(B, s_nph[k], s_ph[k], s_pl[k], make_float2(v.x, v.x));
         }
-        S0 = fast_two_sum(S0.h, S0.l);
-        S1 = fast_two_sum(S1.h, S1.l);
-        const FF E2 = ff_add(fast_two_sum(S2.h, S2.l), fast_two_sum(R0.h, R0.l));  // 2 x energy
+        const FF S0 = fast_two_sum(A.h.x, A.l.x), R0 = fast_two_sum(A.h.y, A.l.y);
+        const FF S1 = fast_two_sum(B.h.x, B.l.x), S2 = fast_two_sum(B.h.y, B.l.y);
+        const FF E2 = ff_add(S2, R0);  // 2 x energy
         // 3 n T = S2 + R0 - u S1 with u = S1 / n
         const float n = S0.h, u = S1.h / n, e3 = E2.h - u * S1.h;
         if (!(n > 0.f) || !(e3 > 0.f) || !isfinite(u) || !isfinite(e3)) atomicOr(a.err, 1u);
