@@ -278,44 +278,85 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz,
 // transposed convolution lacks:
 //   left  (x = 0):     sum_co (W0 + W1)[co][ci] dz[0][co] + W0[co][ci] dz[1][co]
 //   right (x = X - 1): sum_co (W3 + W4)[co][ci] dz[X-1][co] + W4[co][ci] dz[X-2][co]
-// w is the forward layer's W[co][j][ci]; one block per (sample, side), thread ci.
-__global__ void edge_grad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ w,
-                                 const int *__restrict__ periodic, int X, int cout, int cin, float *__restrict__ edge)
+// w is the forward layer's W[co][j][ci].  One block per side, kEdgeSamples
+// samples and kEdgeChannels input channels: the two weight combinations of
+// that side and channel range (the same for every sample) and the samples' end
+// gradients are staged in shared memory once.
+constexpr int kEdgeSamples = 16, kEdgeChannels = 16;
+__global__ void __launch_bounds__(256) edge_grad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ w,
+                                                        const int *__restrict__ periodic, int B, int X, int cout,
+                                                        int cin, float *__restrict__ edge)
 {
-    const int b = blockIdx.x, side = blockIdx.y, ci = threadIdx.x;
-    if (ci >= cin) return;
-    float s = 0.f;
-    if (periodic[b] == 0) {
-        const bf16 *d0 = dz + (size_t(b) * X + (side ? X - 1 : 0)) * cout;
-        const bf16 *d1 = dz + (size_t(b) * X + (side ? X - 2 : 1)) * cout;
-        const int ja = side ? 3 : 0, jb = side ? 4 : 1, jn = side ? 4 : 0;
-        // independent iterations: keep 16 in flight (the loads are L2 hits)
-#pragma unroll 16
-        for (int co = 0; co < cout; ++co) {
-            const float wa = __bfloat162float(w[(co * kTaps + ja) * cin + ci]);
-            const float wb = __bfloat162float(w[(co * kTaps + jb) * cin + ci]);
-            const float wn = __bfloat162float(w[(co * kTaps + jn) * cin + ci]);
-            s = fmaf(wa + wb, __bfloat162float(d0[co]), s);
-            s = fmaf(wn, __bfloat162float(d1[co]), s);
+    __shared__ float s_a[64][kEdgeChannels], s_n[64][kEdgeChannels];  // [co][ci - c0], cout <= 64
+    __shared__ float s_d0[kEdgeSamples][64], s_d1[kEdgeSamples][64];
+    const int side = blockIdx.y, b0 = blockIdx.x * kEdgeSamples, c0 = blockIdx.z * kEdgeChannels, t = threadIdx.x;
+    const int ja = side ? 3 : 0, jb = side ? 4 : 1, jn = side ? 4 : 0;
+    for (int e = t; e < cout * kEdgeChannels; e += blockDim.x) {
+        const int co = e / kEdgeChannels, cc = e - co * kEdgeChannels, ci = c0 + cc;
+        float a = 0.f, n = 0.f;
+        if (ci < cin) {
+            a = __bfloat162float(w[(co * kTaps + ja) * cin + ci]) + __bfloat162float(w[(co * kTaps + jb) * cin + ci]);
+            n = __bfloat162float(w[(co * kTaps + jn) * cin + ci]);
         }
+        s_a[co][cc] = a;
+        s_n[co][cc] = n;
     }
-    edge[(size_t(b) * 2 + side) * cin + ci] = s;
+    for (int e = t; e < kEdgeSamples * cout; e += blockDim.x) {
+        const int sm = e / cout, co = e - sm * cout, b = b0 + sm;
+        float d0 = 0.f, d1 = 0.f;
+        if (b < B) {
+            d0 = __bfloat162float(dz[(size_t(b) * X + (side ? X - 1 : 0)) * cout + co]);
+            d1 = __bfloat162float(dz[(size_t(b) * X + (side ? X - 2 : 1)) * cout + co]);
+        }
+        s_d0[sm][co] = d0;
+        s_d1[sm][co] = d1;
+    }
+    __syncthreads();
+    const int sm = t / kEdgeChannels, cc = t - sm * kEdgeChannels, b = b0 + sm, ci = c0 + cc;
+    if (sm < kEdgeSamples && b < B && ci < cin) {
+        float acc = 0.f;
+        if (periodic[b] == 0)
+            for (int co = 0; co < cout; ++co) {
+                acc = fmaf(s_a[co][cc], s_d0[sm][co], acc);
+                acc = fmaf(s_n[co][cc], s_d1[sm][co], acc);
+            }
+        edge[(size_t(b) * 2 + side) * cin + ci] = acc;
+    }
 }
 
-// out[i] = sum_c partial[c][i] in a fixed order: four interleaved running sums
-// (c mod 4), combined pairwise, so that loads overlap and results stay
-// deterministic.
-__global__ void reduce_partials_kernel(const float *__restrict__ partial, int nparts, int len, float *__restrict__ out)
+// out[i] = sum_c partial[c][i] in a fixed order.  A block of 16 warps takes 128
+// consecutive i (four per lane, 16-byte loads); warp w sums the parts c = w,
+// w + 16, ... in four interleaved running sums (independent loads in flight),
+// and the warp sums are added in warp order, so the result does not depend on
+// scheduling.  len is a multiple of 4.
+constexpr int kReduceWarps = 16;
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(const float *__restrict__ partial,
+                                                                           int nparts, int len,
+                                                                           float *__restrict__ out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= len) return;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    int c = 0;
-    for (; c + 4 <= nparts; c += 4)
+    __shared__ float4 s_w[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i4 = blockIdx.x * 32 + lane;  // float4 index
+    const bool ok = 4 * i4 < len;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 s[4] = {z, z, z, z};
+    if (ok) {
+        const float4 *p = reinterpret_cast<const float4 *>(partial) + i4;
+        const size_t row = size_t(len) / 4;
+        int c = warp;
+        for (; c + 3 * kReduceWarps < nparts; c += 4 * kReduceWarps)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) s[r] += partial[size_t(c + r) * len + i];
-    for (int r = 0; c < nparts; ++c, ++r) s[r] += partial[size_t(c) * len + i];
-    out[i] = (s[0] + s[1]) + (s[2] + s[3]);
+            for (int r = 0; r < 4; ++r) s[r] = add4(s[r], p[size_t(c + r * kReduceWarps) * row]);
+        for (int r = 0; c < nparts; c += kReduceWarps, ++r) s[r] = add4(s[r], p[size_t(c) * row]);
+    }
+    s_w[warp][lane] = add4(add4(s[0], s[1]), add4(s[2], s[3]));
+    __syncthreads();
+    if (warp == 0 && ok) {
+        float4 r = s_w[0][lane];
+        for (int k = 1; k < kReduceWarps; ++k) r = add4(r, s_w[k][lane]);
+        reinterpret_cast<float4 *>(out)[i4] = r;
+    }
 }
 
 // Input features (f32 [B][X][cin_real]) -> normalised bf16 [B][X][CINP].
@@ -398,13 +439,19 @@ __global__ void gather_batch_kernel(const float *__restrict__ x, const float *__
 }
 
 // Mean loss of one batch from the per-block partial sums of mse_kernel, summed
-// in a fixed order by one block.
+// in a fixed order by one block of 256 threads: each thread adds its strided
+// share in FP32, the thread sums are combined in FP64.
 __global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, float scale, float *__restrict__ out)
 {
     __shared__ double red[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += double(partial[i]);
-    red[threadIdx.x] = s;
+    // four independent running sums per thread (loads in flight), combined in order
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+    int i = threadIdx.x;
+    for (; i + 3 * int(blockDim.x) < nparts; i += 4 * blockDim.x)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s4[r] += partial[i + r * blockDim.x];
+    for (int r = 0; i < nparts; i += blockDim.x, ++r) s4[r] += partial[i];
+    red[threadIdx.x] = double(s4[0]) + double(s4[1]) + double(s4[2]) + double(s4[3]);
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (int(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -636,15 +683,20 @@ static ql_status backward(ql_closure *c, const float *y, const int *per, int B, 
     QC_CUDA(c, cudaGetLastError());
     for (int l = nl - 1; l >= 0; --l) {
         const Layer &L = c->layers[l];
-        const int len = L.cout * kTaps * L.cin + L.cout;
+        const int len = L.cout * kTaps * L.cin + L.cout;  // a multiple of 4 (channels are padded to 16)
+        if (len % 4 != 0) return cfail(c, QL_EUNSUPPORTED, "channel padding");
         QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->wgrid, c->partial, c->stream));
         // partial layout per CTA: [cout][5 cin] then [cout]; W and b are contiguous in the parameter vector
-        reduce_partials_kernel<<<(len + 255) / 256, 256, 0, c->stream>>>(c->partial, c->wgrid, len, c->grad + L.woff);
+        reduce_partials_kernel<<<(len + 127) / 128, 32 * kReduceWarps, 0, c->stream>>>(c->partial, c->wgrid, len,
+                                                                                     c->grad + L.woff);
         QC_CUDA(c, cudaGetLastError());
         if (l > 0) {
             // dz[l-1] = (W^T * dz[l] + end terms of replicate padding) masked by act[l] > 0
             // (act[l] is the output of layer l-1)
-            edge_grad_kernel<<<dim3(B, 2), L.cin, 0, c->stream>>>(c->dz[l], c->w16 + L.woff, per, X, L.cout, L.cin,
+            static_assert(kEdgeSamples * kEdgeChannels == 256, "one output per thread");
+            edge_grad_kernel<<<dim3((B + kEdgeSamples - 1) / kEdgeSamples, 2, (L.cin + kEdgeChannels - 1) / kEdgeChannels),
+                               256, 0, c->stream>>>(
+                c->dz[l], c->w16 + L.woff, per, B, X, L.cout, L.cin,
                                                                  c->edge);
             QC_CUDA(c, cudaGetLastError());
             QC_CUDA(c, conv_any(L.cout, L.cin, EPI_MASK_BF16, c->dz[l], c->wt16 + L.woff, nullptr, per, B, X,
