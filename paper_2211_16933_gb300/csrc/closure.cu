@@ -25,6 +25,10 @@ namespace {
 
 constexpr int kTaps = 5;
 constexpr int kTM = 64;  // positions per CTA tile
+// Resident weight-gradient CTAs per SM the kernel is compiled for.
+#ifndef QL_WGRAD_MINBLOCKS
+#define QL_WGRAD_MINBLOCKS 2
+#endif
 typedef __nv_bfloat16 bf16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -66,6 +70,20 @@ __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, const uint
 // Padding of a position outside [0, X): periodic image, copy of the nearest end
 // value, or zero (the transposed convolution of the backward pass).
 enum { PAD_ZERO = 0, PAD_PERIODIC = 1, PAD_REPLICATE = 2 };
+// 16-byte asynchronous copy global -> shared; src_bytes 0 writes zeros and
+// reads nothing.  Completion per thread by commit / wait groups.
+__device__ __forceinline__ void cp_async16_zfill(void *smem_dst, const void *src, unsigned src_bytes)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ int wrap_pos(int p, int X, int mode, bool *inside)
 {
     *inside = true;
@@ -86,7 +104,8 @@ enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
 //     replicate-padded sample edge[b][side][co] is added (edge_grad_kernel);
 //     then times (mask[b][x][co] > 0), stored bf16 (ReLU backward).
 // Persistent CTAs: the layer's weights are loaded into shared memory once, then
-// each CTA walks (sample, 64-position tile) items with a grid stride; per item
+// each CTA walks (sample, 64-position tile) items with a grid stride, the next
+// item's input window copied in by cp.async while the current one is used; per item
 // 4 warps x 16 positions, all COUT channels, as an implicit GEMM (M = positions,
 // N = COUT, K = 5 CIN) on mma.sync m16n8k16 with ldmatrix fragments.
 template <int CIN, int COUT, int EPI>
@@ -99,7 +118,8 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
     constexpr int WS = CIN + 8;  // smem row stride (bf16): 16-byte rows, no ldmatrix bank conflicts
     extern __shared__ __align__(16) unsigned char smem[];
     bf16 *ws = reinterpret_cast<bf16 *>(smem);  // [COUT * 5][WS]
-    bf16 *win = ws + COUT * kTaps * WS;         // [kTM + 4][WS]
+    bf16 *const win_base = ws + COUT * kTaps * WS;  // two stages of [kTM + 4][WS]
+    constexpr int kWin = (kTM + 4) * WS;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
     constexpr int VPR = CIN / 8;  // 16-byte vectors per row
     for (int e = t; e < COUT * kTaps * VPR; e += blockDim.x) {
@@ -110,20 +130,33 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
     const int m0 = warp * 16;
     // ldmatrix row of this lane: matrix mat = lane / 8, row t8 = lane % 8
     const int t8 = lane & 7, mat = lane >> 3;
-    for (int item = blockIdx.x; item < B * tiles; item += gridDim.x) {
+    // cp.async of the input window of `item` into stage `st` (positions beyond the
+    // padding are zero-filled: source size 0, nothing is read); the next item's
+    // window is copied in while the current one is multiplied
+    auto stage_win = [&](int item, int st) {
+        bf16 *win = win_base + st * kWin;
         const int b = item / tiles, x0 = (item % tiles) * kTM;
-        const bool per = periodic[b] != 0;
-        const int mode = per ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
-        __syncthreads();  // the previous item's window is no longer read
+        const int mode = periodic[b] != 0 ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
         for (int e = t; e < (kTM + 4) * VPR; e += blockDim.x) {
             const int r = e / VPR, v = e % VPR;
             bool inside;
             const int p = wrap_pos(x0 - 2 + r, X, mode, &inside);
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (inside) val = *reinterpret_cast<const uint4 *>(in + (size_t(b) * X + p) * CIN + v * 8);
-            *reinterpret_cast<uint4 *>(win + r * WS + v * 8) = val;
+            const bf16 *src = inside ? in + (size_t(b) * X + p) * CIN + v * 8 : in;
+            cp_async16_zfill(win + r * WS + v * 8, src, inside ? 16u : 0u);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    int st = 0;
+    if (blockIdx.x < B * tiles) stage_win(blockIdx.x, 0);
+    for (int item = blockIdx.x; item < B * tiles; item += gridDim.x, st ^= 1) {
+        const int b = item / tiles, x0 = (item % tiles) * kTM;
+        const bool per = periodic[b] != 0;
+        const bool more = item + int(gridDim.x) < B * tiles;
+        if (more) stage_win(item + gridDim.x, st ^ 1);
+        if (more) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();  // this item's window (and, first time, the weights) visible
+        const bf16 *win = win_base + st * kWin;
 
         float acc[COUT / 8][4];
 #pragma unroll
@@ -145,6 +178,7 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
                 }
             }
         }
+        __syncthreads();  // every warp is done with this window: it is refilled two items later
 #pragma unroll
         for (int n = 0; n < COUT / 8; ++n) {
             const int co = n * 8 + 2 * tg;
@@ -184,12 +218,13 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
 // a GEMM with M = COUT, N = 5 CIN, K = positions.  Each CTA accumulates over
 // its share of the (sample, tile) items and writes a partial;
 // reduce_partials_kernel sums the partials in a fixed order.  The dz tile and
-// the input window are staged channels-last with 16-byte copies; the
-// transposed operands (K = positions contiguous) come from ldmatrix .trans.
+// the input window are staged channels-last by 16-byte cp.async copies, two
+// items deep; the transposed operands (K = positions contiguous) come from
+// ldmatrix .trans.
 // 8 warps: warp (mw, nw) holds couts [16 mw, 16 mw + 16) and NTW of the N/8
 // column tiles.
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ in,
+__global__ void __launch_bounds__(256, QL_WGRAD_MINBLOCKS) wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ in,
                                                     const int *__restrict__ periodic, int X, int ntiles,
                                                     float *__restrict__ partial)
 {
@@ -201,8 +236,11 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz,
     constexpr int NTW = (NT + NW - 1) / NW;  // n tiles per warp
     constexpr int DS = COUT + 8, IS = CIN + 8;  // smem row strides (bf16)
     extern __shared__ __align__(16) unsigned char smem[];
-    bf16 *sdz = reinterpret_cast<bf16 *>(smem);  // [kTM][DS]     dz tile, positions x couts
-    bf16 *sin = sdz + kTM * DS;                  // [kTM + 4][IS] input window, positions x cins
+    // two stages of [kTM][DS] dz tile (positions x couts) and [kTM + 4][IS]
+    // input window (positions x cins): the next item is copied in while the
+    // current one is multiplied
+    constexpr int kStage = kTM * DS + (kTM + 4) * IS;
+    bf16 *const stage_base = reinterpret_cast<bf16 *>(smem);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
     const int t8 = lane & 7, mat = lane >> 3;
     const int mw = warp % MT, nw = warp / MT;
@@ -211,26 +249,36 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz,
     for (int n = 0; n < NTW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
     float db = 0.f;
     const int tiles = (X + kTM - 1) / kTM;
-    for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
+    // cp.async of item `item` into stage `st`: positions outside the sample (and
+    // outside the padding) are zero-filled (source size 0, nothing is read)
+    auto stage_item = [&](int item, int st) {
+        bf16 *sdz = stage_base + st * kStage, *sin = sdz + kTM * DS;
         const int b = item / tiles, x0 = (item % tiles) * kTM;
         const int mode = periodic[b] != 0 ? PAD_PERIODIC : PAD_REPLICATE;
-        __syncthreads();
         for (int e = t; e < kTM * (COUT / 8); e += blockDim.x) {
             const int p = e / (COUT / 8), v = e % (COUT / 8);
             const int x = x0 + p;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (x < X) val = *reinterpret_cast<const uint4 *>(dz + (size_t(b) * X + x) * COUT + v * 8);
-            *reinterpret_cast<uint4 *>(sdz + p * DS + v * 8) = val;
+            const bf16 *src = x < X ? dz + (size_t(b) * X + x) * COUT + v * 8 : dz;
+            cp_async16_zfill(sdz + p * DS + v * 8, src, x < X ? 16u : 0u);
         }
         for (int e = t; e < (kTM + 4) * (CIN / 8); e += blockDim.x) {
             const int p = e / (CIN / 8), v = e % (CIN / 8);
             bool inside;
             const int x = wrap_pos(x0 - 2 + p, X, mode, &inside);
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (inside) val = *reinterpret_cast<const uint4 *>(in + (size_t(b) * X + x) * CIN + v * 8);
-            *reinterpret_cast<uint4 *>(sin + p * IS + v * 8) = val;
+            const bf16 *src = inside ? in + (size_t(b) * X + x) * CIN + v * 8 : in;
+            cp_async16_zfill(sin + p * IS + v * 8, src, inside ? 16u : 0u);
         }
+        cp_async_commit();
+    };
+    int st = 0;
+    if (blockIdx.x < ntiles) stage_item(blockIdx.x, 0);
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, st ^= 1) {
+        const bool more = item + int(gridDim.x) < ntiles;
+        if (more) stage_item(item + gridDim.x, st ^ 1);
+        if (more) cp_async_wait<1>();
+        else cp_async_wait<0>();
         __syncthreads();
+        const bf16 *sdz = stage_base + st * kStage, *sin = sdz + kTM * DS;
         // bias gradient: thread t < COUT sums column t of the dz tile
         if (t < COUT) {
             float s = 0.f;
@@ -255,6 +303,7 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dz,
                 mma16816(acc[n], a, bb);
             }
         }
+        __syncthreads();  // this stage is refilled two items later
     }
     // partial[cta][co][col] with col = j CIN + ci, then the bias partials
     float *P = partial + size_t(blockIdx.x) * (COUT * N + COUT);
@@ -503,7 +552,7 @@ template <int CIN, int COUT, int EPI>
 cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const int *per, int B, int X, void *out,
                         const bf16 *mask, const float *edge, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(bf16) * ((kTM + 4) * (CIN + 8) + COUT * kTaps * (CIN + 8));
+    constexpr size_t smem = sizeof(bf16) * (2 * (kTM + 4) * (CIN + 8) + COUT * kTaps * (CIN + 8));
     auto k = conv_kernel<CIN, COUT, EPI>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -537,7 +586,7 @@ template <int CIN, int COUT>
 cudaError_t wgrad_launch(const bf16 *dz, const bf16 *in, const int *per, int B, int X, int grid, float *partial,
                          cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(bf16) * (kTM * (COUT + 8) + (kTM + 4) * (CIN + 8));
+    constexpr size_t smem = 2 * sizeof(bf16) * (kTM * (COUT + 8) + (kTM + 4) * (CIN + 8));
     auto k = wgrad_kernel<CIN, COUT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
