@@ -3,6 +3,7 @@
 // and declares `static __constant__ QL_REAL QL_TAB[kTabTotal]`.
 #pragma once
 #include "fdlb_kernels.cuh"
+#include "fdlb_aux.cuh"
 
 #define QL_CAT2(a, b) a##b
 #define QL_CAT(a, b) QL_CAT2(a, b)
