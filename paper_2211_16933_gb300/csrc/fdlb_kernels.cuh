@@ -334,7 +334,7 @@ constexpr int kVelocityLoopUnroll = QL_VLOOP_UNROLL;
 // Resident CTAs per SM the FP32 stage kernels are compiled for (8-warp tiles;
 // the register budget follows from it).
 #ifndef QL_STAGE_MINBLOCKS_F32
-#define QL_STAGE_MINBLOCKS_F32 (QL_STAGE_WARPS == 6 ? 4 : 3)
+#define QL_STAGE_MINBLOCKS_F32 3
 #endif
 
 // ---------------------------------------------------------------------------

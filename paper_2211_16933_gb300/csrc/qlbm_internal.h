@@ -32,15 +32,12 @@ constexpr int kBatchMaxQ = 32;
 // plus kHalo cells on each side (the WENO-5 and 6th-order stencils reach 3).
 // Each warp updates 31 cells; its lane 0 computes the flux on the warp's
 // left face.
-#ifndef QL_STAGE_WARPS
-#define QL_STAGE_WARPS 8
-#endif
-constexpr int kWarps = QL_STAGE_WARPS;
+constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kTile = 31 * kWarps;
 constexpr int kHalo = 4;
 constexpr int kSeg = kTile + 2 * kHalo;
-static_assert(kTile % 2 == 0 && kSeg <= 256, "even tile starts (16-byte aligned FP32 segments); strides leave 256 columns");
+static_assert(kSeg == kThreads, "one staged cell per thread in the moment phase");
 
 // Row layout of a state buffer: Q rows, one per velocity k, each of `stride`
 // pairs (phi_k, theta_k) of the working precision; cell i (-kHalo <= i <
