@@ -422,12 +422,40 @@ __global__ void pack_input_kernel(const float *__restrict__ x, int64_t n, int ci
     out[e] = __float2bfloat16(v);
 }
 
+// The same for the mini-batch idx[0..B) of a data set of n samples (X positions
+// each), with the samples' padding kinds gathered into perb.  An index outside
+// [0, n) sets *bad and reads sample 0 instead, so nothing is read out of bounds.
+__global__ void pack_gather_kernel(const float *__restrict__ x, const int32_t *__restrict__ per,
+                                   const int32_t *__restrict__ idx, int64_t n, int B, int X, int cin, int cinp,
+                                   const float *__restrict__ shift, const float *__restrict__ inv_scale,
+                                   bf16 *__restrict__ out, int32_t *__restrict__ perb, unsigned *__restrict__ bad)
+{
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < B) {
+        const int64_t k = idx[e];
+        const bool ok = k >= 0 && k < n;
+        if (!ok) atomicOr(bad, 1u);
+        perb[e] = per[ok ? k : 0];
+    }
+    if (e >= int64_t(B) * X * cinp) return;
+    const int64_t pos = e / cinp;
+    const int c = int(e % cinp);
+    const int64_t b = pos / X;
+    int64_t k = idx[b];
+    if (k < 0 || k >= n) k = 0;
+    float v = 0.f;
+    if (c < cin) v = (x[(k * X + (pos - b * X)) * cin + c] - shift[c]) * inv_scale[c];
+    out[e] = __float2bfloat16(v);
+}
+
 // Mean squared error between prediction (f32 [B][X][COUTP], first cout used) and
 // target / out_scale; writes dL/dpred (bf16, padded channels zero) and
 // per-block partial sums of the squared error.
-__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ y, int64_t npos, int cout,
-                           int coutp, const float *__restrict__ inv_out_scale, float grad_scale,
-                           bf16 *__restrict__ dpred, float *__restrict__ partial)
+// y rows of the batch: y[b] directly, or y[idx[b]] of the whole data set
+// (idx already checked by pack_gather_kernel; X positions per sample).
+__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ y, const int32_t *__restrict__ idx,
+                           int X, int64_t npos, int cout, int coutp, const float *__restrict__ inv_out_scale,
+                           float grad_scale, bf16 *__restrict__ dpred, float *__restrict__ partial)
 {
     __shared__ float red[256];
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -437,7 +465,12 @@ __global__ void mse_kernel(const float *__restrict__ pred, const float *__restri
         const int c = int(e % coutp);
         float d = 0.f;
         if (c < cout) {
-            d = pred[e] - y[pos * cout + c] * inv_out_scale[c];
+            int64_t row = pos;
+            if (idx) {
+                const int64_t b = pos / X;
+                row = int64_t(idx[b]) * X + (pos - b * X);
+            }
+            d = pred[e] - y[row * cout + c] * inv_out_scale[c];
             se = d * d;
         }
         dpred[e] = __float2bfloat16(grad_scale * d);
@@ -460,31 +493,6 @@ __global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npo
     const int64_t pos = e / cout;
     const int c = int(e % cout);
     y[e] = pred[pos * coutp + c] * out_scale[c];
-}
-
-// Mini-batch b of a training run: sample idx[b] of the device data set (n
-// samples) copied into the contiguous batch buffers.  An index outside [0, n)
-// sets *bad and is replaced by 0, so that nothing is read out of bounds.
-__global__ void gather_batch_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                    const int32_t *__restrict__ per, const int32_t *__restrict__ idx, int64_t n,
-                                    int B, int64_t xrow, int64_t yrow, float *__restrict__ xb, float *__restrict__ yb,
-                                    int32_t *__restrict__ perb, unsigned *__restrict__ bad)
-{
-    const int64_t total = int64_t(B) * (xrow + yrow + 1);
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t per_sample = xrow + yrow + 1;
-        const int b = int(e / per_sample);
-        const int64_t r = e - int64_t(b) * per_sample;
-        int64_t k = idx[b];
-        if (k < 0 || k >= n) {
-            if (r == 0) atomicOr(bad, 1u);
-            k = 0;
-        }
-        if (r < xrow) xb[int64_t(b) * xrow + r] = x[k * xrow + r];
-        else if (r < xrow + yrow) yb[int64_t(b) * yrow + (r - xrow)] = y[k * yrow + (r - xrow)];
-        else perb[b] = per[k];
-    }
 }
 
 // Mean loss of one batch from the per-block partial sums of mse_kernel, summed
@@ -511,11 +519,19 @@ __global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, f
 
 // Adam on FP32 master parameters; refreshes the bf16 weight copies, the
 // tap-flipped transposed copies used by the backward pass, and the f32 biases.
+constexpr int kAdamLayers = 8;  // layers whose bf16 copies the Adam pass refreshes itself
 struct AdamArgs {
     float *param, *m, *v;
     const float *grad;
     int64_t n;
     float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+    // bf16 copies written in the same pass (nl = 0: none): layer l's W[co][j][ci]
+    // at woff[l] (cout[l] x 5 x cin[l]) into w16 and, tap-flipped and
+    // transposed, into wt16 at the same offset
+    bf16 *w16, *wt16;
+    int nl;
+    int64_t woff[kAdamLayers];
+    int cout[kAdamLayers], cin[kAdamLayers];
 };
 __global__ void adam_kernel(AdamArgs a)
 {
@@ -526,7 +542,19 @@ __global__ void adam_kernel(AdamArgs a)
     const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
     a.m[i] = m;
     a.v[i] = v;
-    a.param[i] -= a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+    const float p = a.param[i] - a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+    a.param[i] = p;
+    for (int l = 0; l < a.nl; ++l) {
+        const int64_t e = i - a.woff[l];
+        const int ci_ = a.cin[l], cout_ = a.cout[l];
+        if (e >= 0 && e < int64_t(cout_) * kTaps * ci_) {
+            const int co = int(e / (kTaps * ci_)), j = int((e / ci_) % kTaps), ci = int(e % ci_);
+            const bf16 b = __float2bfloat16(p);
+            a.w16[i] = b;
+            a.wt16[a.woff[l] + (int64_t(ci) * kTaps + (kTaps - 1 - j)) * cout_ + co] = b;
+            break;
+        }
+    }
 }
 
 // bf16 copies of one layer's weights: w[co][j][ci] and wt[ci][4 - j][co].
@@ -625,8 +653,7 @@ struct ql_closure {
     float *loss_partial = nullptr;
     float *edge = nullptr;  // [max_batch][2][64] end-position gradient terms of replicate padding
     float *norm = nullptr;  // in_shift[8], in_inv_scale[8], out_scale[8], inv_out_scale[8]
-    // mini-batch buffers of ql_closure_train_steps and its out-of-range index flag
-    float *xb = nullptr, *yb = nullptr;
+    // padding kinds of ql_closure_train_steps' mini-batch and its out-of-range index flag
     int32_t *perb = nullptr;
     unsigned *bad = nullptr;
     int wgrid = 0;
@@ -660,7 +687,7 @@ static void closure_release(ql_closure *c)
 {
     for (void *p : {(void *)c->param, (void *)c->grad, (void *)c->m, (void *)c->v, (void *)c->w16, (void *)c->wt16,
                     (void *)c->pred, (void *)c->partial, (void *)c->loss_partial, (void *)c->edge,
-                    (void *)c->norm, (void *)c->xb, (void *)c->yb, (void *)c->perb, (void *)c->bad})
+                    (void *)c->norm, (void *)c->perb, (void *)c->bad})
         cfree_dev(c, p);
     for (bf16 *p : c->act) cfree_dev(c, p);
     for (bf16 *p : c->dz) cfree_dev(c, p);
@@ -719,7 +746,7 @@ static ql_status pack(ql_closure *c, const float *x, int B)
 static ql_status adam_step(ql_closure *c, float lr);
 
 // Loss, gradients of all parameters into c->grad; loss (host) if not null.
-static ql_status backward(ql_closure *c, const float *y, const int *per, int B, float *loss)
+static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, const int *per, int B, float *loss)
 {
     const int X = c->d.positions, nl = int(c->layers.size());
     const int64_t npos = int64_t(B) * X;
@@ -727,7 +754,7 @@ static ql_status backward(ql_closure *c, const float *y, const int *per, int B, 
     const int64_t nel = npos * coutp;
     const unsigned nb = unsigned((nel + 255) / 256);
     const float gscale = 2.f / float(npos * c->d.out_channels);
-    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, npos, c->d.out_channels, coutp, c->norm + 24, gscale,
+    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, yidx, X, npos, c->d.out_channels, coutp, c->norm + 24, gscale,
                                           c->dz[nl - 1], c->loss_partial);
     QC_CUDA(c, cudaGetLastError());
     for (int l = nl - 1; l >= 0; --l) {
@@ -820,12 +847,10 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
     c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(c->wgrid) * (64 * kTaps * 64 + 64)));
     c->loss_partial = static_cast<float *>(calloc_dev(c, sizeof(float) * ((npos * 16 + 255) / 256)));
     c->edge = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(B) * 2 * 64));
-    c->xb = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * d->in_channels));
-    c->yb = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * d->out_channels));
     c->perb = static_cast<int32_t *>(calloc_dev(c, sizeof(int32_t) * size_t(B)));
     c->bad = static_cast<unsigned *>(calloc_dev(c, sizeof(unsigned)));
     bool ok = c->param && c->grad && c->m && c->v && c->w16 && c->wt16 && c->pred && c->norm && c->partial &&
-              c->loss_partial && c->edge && c->xb && c->yb && c->perb && c->bad;
+              c->loss_partial && c->edge && c->perb && c->bad;
     for (int l = 0; l < d->layers; ++l) ok = ok && c->act[l] && c->dz[l];
     if (!ok) return bail(QL_ENOMEM, "closure allocation failed");
 
@@ -883,7 +908,7 @@ ql_status ql_closure_gradients(ql_closure *c, const float *x, const float *y, co
     if (!c || !x || !y || !periodic || B < 1 || B > c->d.max_batch) return cfail(c, QL_EINVAL, "bad arguments");
     ql_status st = pack(c, x, int(B));
     if (st == QL_OK) st = forward(c, periodic, int(B));
-    if (st == QL_OK) st = backward(c, y, periodic, int(B), loss);
+    if (st == QL_OK) st = backward(c, y, nullptr, periodic, int(B), loss);
     if (st != QL_OK) return st;
     if (grad_host) {
         QC_CUDA(c, cudaMemcpyAsync(grad_host, c->grad, sizeof(float) * c->nparam, cudaMemcpyDeviceToHost, c->stream));
@@ -907,18 +932,18 @@ ql_status ql_closure_train_steps(ql_closure *c, const float *x, const float *y, 
         (nsteps > 0 && !lr))
         return cfail(c, QL_EINVAL, "bad arguments");
     const int X = c->d.positions;
-    const int64_t xrow = int64_t(X) * c->d.in_channels, yrow = int64_t(X) * c->d.out_channels;
     const int64_t npos = B * X;
     const unsigned nb = unsigned((npos * c->layers.back().cout + 255) / 256);
     const float lscale = float(1.0 / double(npos * c->d.out_channels));
     QC_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(unsigned), c->stream));
     for (int64_t s = 0; s < nsteps; ++s) {
-        gather_batch_kernel<<<unsigned((B * (xrow + yrow + 1) + 255) / 256), 256, 0, c->stream>>>(
-            x, y, periodic, perm + s * B, n, int(B), xrow, yrow, c->xb, c->yb, c->perb, c->bad);
+        const int32_t *idx = perm + s * B;
+        const int cinp = c->layers[0].cin;
+        pack_gather_kernel<<<unsigned((B * X * cinp + 255) / 256), 256, 0, c->stream>>>(
+            x, periodic, idx, n, int(B), X, c->d.in_channels, cinp, c->norm, c->norm + 8, c->act[0], c->perb, c->bad);
         QC_CUDA(c, cudaGetLastError());
-        ql_status st = pack(c, c->xb, int(B));
-        if (st == QL_OK) st = forward(c, c->perb, int(B));
-        if (st == QL_OK) st = backward(c, c->yb, c->perb, int(B), nullptr);
+        ql_status st = forward(c, c->perb, int(B));
+        if (st == QL_OK) st = backward(c, y, idx, c->perb, int(B), nullptr);
         if (st != QL_OK) return st;
         if (losses) {
             loss_sum_kernel<<<1, 256, 0, c->stream>>>(c->loss_partial, int(nb), lscale, losses + s);
@@ -951,9 +976,18 @@ static ql_status adam_step(ql_closure *c, float lr)
     a.eps = 1e-8f;
     a.c1 = float(1.0 / (1.0 - pow(0.9, double(c->step))));
     a.c2 = float(1.0 / (1.0 - pow(0.999, double(c->step))));
+    const bool fused = c->layers.size() <= size_t(kAdamLayers);
+    a.w16 = c->w16;
+    a.wt16 = c->wt16;
+    a.nl = fused ? int(c->layers.size()) : 0;
+    for (int l = 0; l < a.nl; ++l) {
+        a.woff[l] = c->layers[l].woff;
+        a.cout[l] = c->layers[l].cout;
+        a.cin[l] = c->layers[l].cin;
+    }
     adam_kernel<<<unsigned((c->nparam + 255) / 256), 256, 0, c->stream>>>(a);
     QC_CUDA(c, cudaGetLastError());
-    return refresh_weights(c);
+    return fused ? QL_OK : refresh_weights(c);
 }
 
 extern "C" {
