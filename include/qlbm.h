@@ -137,6 +137,12 @@ typedef void (*ql_free_fn)(void *ptr, void *user);
  *              The output pressure keeps chi_SET of the local density.
  *   rho_ref    density at which the denseness E_l is given; the local reduced
  *              density is eta = eta0 rho / rho_ref.
+ *   fault      0 normally.  1 (for failure-detection tests of the caller's
+ *              error handling, tiled velocity sets only): the stage kernels
+ *              arm their tile-staging barrier but issue no copies, so each
+ *              CTA's bounded wait gives up (no copy is in flight, nothing
+ *              faults) and the next synchronising call returns QL_ECUDA
+ *              ("gave up waiting"); the state is left as it was.
  *   stream     cudaStream_t for all work, NULL for the legacy default stream. */
 typedef struct {
     int32_t precision;
@@ -144,7 +150,7 @@ typedef struct {
     int32_t enskog;
     int32_t device;
     int32_t chi_mode;
-    int32_t pad_;
+    int32_t fault;
     double pr_const;
     double rho_ref;
     void *stream;

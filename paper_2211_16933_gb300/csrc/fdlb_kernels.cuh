@@ -278,9 +278,10 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 }
 
 // Polls of the staging mbarrier before a CTA gives up (each try_wait may
-// itself suspend the thread for a while); a give-up sets bit 1 of the error
-// word and the tile is skipped.
-constexpr uint32_t kMbarPolls = 1u << 22;
+// itself suspend the thread, measured at about 3.7 us, so the limit is about
+// 0.25 s, against microseconds for a tile's copies); a give-up sets bit 1 of
+// the error word and the tile is skipped.
+constexpr uint32_t kMbarPolls = 1u << 16;
 
 // 1: stage the tile's rows with TMA bulk copies; 0: with 16-byte loads.
 #ifndef QL_STAGE_TMA
@@ -384,8 +385,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
             if (t == 0) {
                 fence_proxy_async_smem();  // the previous tile's reads of s_psi come first
                 mbar_arrive_expect_tx(mbar, uint32_t(Q * SEG * sizeof(V)));
-                for (int r = 0; r < Q; ++r)
-                    bulk_copy_g2s(s_psi + r * SEG, in + r * stride + i0, uint32_t(SEG * sizeof(V)), mbar);
+                if (!a.fault)  // failure-detection tests: no copy is issued, the wait below gives up
+                    for (int r = 0; r < Q; ++r)
+                        bulk_copy_g2s(s_psi + r * SEG, in + r * stride + i0, uint32_t(SEG * sizeof(V)), mbar);
             }
         } else {
             constexpr int PPV = 16 / sizeof(V);  // pairs per vector
@@ -753,7 +755,7 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
         a.pr_mode = I.pr_mode;
         a.enskog = I.enskog;
         a.periodic = I.periodic;
-        a.pad_ = 0;
+        a.fault = 0;
         a.err = b.err + it.x;
         a.nbar = nullptr;  // instances use chi_SET
         a.nout = nullptr;

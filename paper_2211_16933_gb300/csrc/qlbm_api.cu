@@ -15,7 +15,7 @@
 using namespace qlbm;
 
 struct ql_ctx {
-    int Q = 0, precision = 0, pr_mode = 0, enskog = 1, periodic = 1, device = 0;
+    int Q = 0, precision = 0, pr_mode = 0, enskog = 1, periodic = 1, device = 0, fault = 0;
     int64_t nx = 0, stride = 0;
     double L = 0, dx = 0, dt = 0, El = 0, kn = 0, pr_const = 2.0 / 3.0, rho_ref = 1.0;
     double eta0 = 0, chi0 = 1, sigma = 0, tau_pref = 0;
@@ -128,7 +128,7 @@ static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, voi
     a.pr_mode = c->pr_mode;
     a.enskog = c->enskog;
     a.periodic = c->periodic;
-    a.pad_ = 0;
+    a.fault = c->fault;
     a.err = c->d_err;
     const bool ret = c->chi_mode == QL_CHI_RET_FM;
     a.nbar = ret ? c->d_nbar : nullptr;
@@ -236,9 +236,11 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     if (!(opts->rho_ref > 0)) return fail(nullptr, QL_EINVAL, "rho_ref must be > 0");
     if (opts->pr_mode == QL_PR_CONST && !(opts->pr_const > 0)) return fail(nullptr, QL_EINVAL, "pr_const must be > 0");
     if (opts->chi_mode != QL_CHI_SET && opts->chi_mode != QL_CHI_RET_FM) return fail(nullptr, QL_EINVAL, "bad chi_mode");
+    if (opts->fault != 0 && opts->fault != 1) return fail(nullptr, QL_EINVAL, "bad fault (0 or 1)");
 
     ql_ctx *c = new ql_ctx();
     c->chi_mode = opts->chi_mode;
+    c->fault = opts->fault;
     c->lq = lq;
     c->Q = vs->Q;
     c->precision = opts->precision;

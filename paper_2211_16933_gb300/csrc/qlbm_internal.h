@@ -79,7 +79,8 @@ struct StageArgs {
     int64_t stride;
     double inv_dx, dt;
     double eta0, inv_rho_ref, tau_pref, pr_const;
-    int pr_mode, enskog, periodic, pad_;
+    int pr_mode, enskog, periodic;
+    int fault;      // 1: arm the staging barrier without issuing the copies (failure-detection tests)
     unsigned *err;  // device error word; bit 0: non-physical cell, bit 1: a TMA staging wait gave up
     // chi_RET-FM only (else null): nbar of every column of the stage input
     // (nx + 2 kHalo values of the working precision), and the density of

@@ -140,7 +140,7 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     a.pr_mode = opts->pr_mode;
     a.enskog = opts->enskog ? 1 : 0;
     a.periodic = bc->kind == QL_BC_PERIODIC;
-    a.pad_ = 0;
+    a.fault = 0;
     a.err = err;
     a.nbar = nullptr;
     a.nout = nullptr;

@@ -67,7 +67,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class ql_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("pr_mode", C.c_int32), ("enskog", C.c_int32), ("device", C.c_int32),
-                ("chi_mode", C.c_int32), ("pad_", C.c_int32), ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
+                ("chi_mode", C.c_int32), ("fault", C.c_int32), ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -500,7 +500,9 @@ class Solver:
     def __init__(self, Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND,
                  prm=(1.0, 1.0, 1e-3), rho=None, u=None, T=None, ghost=None, precision=QL_FP64,
                  pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, device=0, use_torch=True,
-                 chi_mode=None):
+                 chi_mode=None, fault=0):
+        """fault = 1 is for failure-detection tests (ql_opts.fault): the stage kernels give up waiting for
+        copies that are never issued and the next synchronising call raises QLError(QL_ECUDA)."""
         self.Q, self.nx, self.precision = Q, nx, precision
         vs = ql_velset(Q, 0)
         grid = ql_grid(nx, length, dt)
@@ -519,6 +521,7 @@ class Solver:
         o.precision, o.pr_mode, o.enskog, o.device = precision, pr_mode, enskog, device
         o.pr_const, o.rho_ref = pr_const, rho_ref
         o.chi_mode = QL_CHI_SET if chi_mode is None else chi_mode
+        o.fault = fault
         self._torch_blocks = {}
         if use_torch:
             import torch
