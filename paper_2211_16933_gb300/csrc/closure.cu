@@ -157,6 +157,20 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
         else cp_async_wait<0>();
         __syncthreads();  // this item's window (and, first time, the weights) visible
         const bf16 *win = win_base + st * kWin;
+        // ReLU-backward mask of this thread's outputs, loaded before the products so
+        // that its latency is hidden behind them
+        __nv_bfloat162 mk[EPI == EPI_MASK_BF16 ? COUT / 8 : 1][2];
+        if constexpr (EPI == EPI_MASK_BF16) {
+#pragma unroll
+            for (int n = 0; n < COUT / 8; ++n)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int x = x0 + m0 + g + 8 * h;
+                    mk[n][h] = x < X ? *reinterpret_cast<const __nv_bfloat162 *>(
+                                           mask + (size_t(b) * X + x) * COUT + n * 8 + 2 * tg)
+                                     : __floats2bfloat162_rn(0.f, 0.f);
+                }
+        }
 
         float acc[COUT / 8][4];
 #pragma unroll
@@ -203,9 +217,9 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
                         v0 += eg[0];
                         v1 += eg[1];
                     }
-                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + o);
-                    v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
-                    v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+                    const __nv_bfloat162 mv = mk[n][h];
+                    v0 = __bfloat162float(mv.x) > 0.f ? v0 : 0.f;
+                    v1 = __bfloat162float(mv.y) > 0.f ? v1 : 0.f;
                     *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) = __floats2bfloat162_rn(v0, v1);
                 }
             }
