@@ -69,13 +69,13 @@ def _kernel_hash(precision_name="fp32"):
     return h.hexdigest()[:16]
 
 
-def _flops_per_update(precision_name):
+def _flops_per_update(precision_name, Q=32):
     """Floating-point operations per cell-velocity update (all three stages) from the committed ncu counts,
-    if they were taken on this kernel source."""
+    if they were taken on this kernel source and velocity set (the Hermite sum makes them grow with Q)."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_flops.json")))
         e = t.get(precision_name)
-        if e and e.get("kernel_hash") == _kernel_hash(precision_name):
+        if e and e.get("kernel_hash") == _kernel_hash(precision_name) and e.get("Q") == Q:
             return float(sum(e["flop_per_update_per_stage"]))
     except Exception:
         pass
@@ -87,8 +87,8 @@ def _flops_per_update(precision_name):
 ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12}
 
 
-def _alu_roofline(precision_name, updates_per_s):
-    f = _flops_per_update(precision_name)
+def _alu_roofline(precision_name, updates_per_s, Q=32):
+    f = _flops_per_update(precision_name, Q)
     if f is None:
         return None
     achieved = f * updates_per_s / 1e12
@@ -98,12 +98,14 @@ def _alu_roofline(precision_name, updates_per_s):
             "flop_per_update": f, "kernel": "fdlb_stage_kernel"}
 
 
-def _traffic(precision_name):
-    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on this kernel source."""
+def _traffic(precision_name, Q=32, nx=1 << 22):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on this kernel source and
+    scaled to this workload's size."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
         e = t.get(precision_name)
-        if e and e.get("kernel_hash") == _kernel_hash(precision_name):
+        if (e and e.get("kernel_hash") == _kernel_hash(precision_name) and e.get("Q") == Q
+                and e.get("scaled_to_nx") == nx):
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -290,11 +292,11 @@ def run_ours(args, w):
     else:
         peak, peak_src = 6800.0, "fallback"
     hbm_roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": _traffic(args.precision), "peak_source": peak_src,
+                    "traffic": _traffic(args.precision, Q, nx), "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": bytes_per_step / 3, "launches_per_step": 3,
                     "kernel": "fdlb_stage_kernel"}
     # the per-launch update rate is the step's (three launches of the same cells)
-    alu_roofline = _alu_roofline(args.precision, nx * Q * args.steps / (total_ms * 1e-3))
+    alu_roofline = _alu_roofline(args.precision, nx * Q * args.steps / (total_ms * 1e-3), Q)
     # FP32: the metric's HBM roofline, the FP32-pipe view beside it; FP64: bound by GB300's FP64 rate
     if args.precision == "fp64" and alu_roofline is not None:
         roofline, other_roofline = alu_roofline, hbm_roofline

@@ -179,3 +179,15 @@ def test_python_binding_has_no_cpu_path():
     src = open(os.path.join(ROOT, "paper_2211_16933_gb300", "qlbm.py")).read()
     assert "oracle" not in src
     assert "import torch" in src  # allocator and stream only
+
+
+def test_bench_records_apply_only_to_their_workload():
+    """The committed DRAM-traffic and operation-count records are for Q = 32 at 2^22 cells: other velocity sets or
+    sizes report null rather than a borrowed figure; the ALU peaks follow from the unit counts and clocks."""
+    import bench
+    assert bench._traffic("fp32", 16, 1 << 22) is None
+    assert bench._traffic("fp32", 32, 1 << 20) is None
+    assert bench._flops_per_update("fp32", 24) is None
+    assert bench._alu_roofline("fp64", 1e9, 40) is None
+    assert abs(bench.ALU_PEAK_TFLOPS["fp32"] - 80.54784) < 1e-9
+    assert abs(bench.ALU_PEAK_TFLOPS["fp64"] - 1.25856) < 1e-12
