@@ -667,3 +667,18 @@ def test_sound_modes_are_the_small_k_roots_of_the_linear_hydrodynamic_equations(
     # the thermodynamic identity c_s^2 = gamma (dP/drho)_T with c_P - c_V = T PT^2 / (rho^2 Prho)
     assert gamma * cV - cV == pytest.approx(T * PT ** 2 / (rho ** 2 * Prho), rel=1e-12)
     assert aa >= aa0 and (aa - aa0) / aa < (0.5 if El > 1 else 0.05)
+
+
+def test_hermite_equilibrium_conditioning_bounded_only_below_twice_the_reference_temperature():
+    """READINGS c17, c24: the weighted L2 norm of the Maxwellian against the Gauss-Hermite weight is finite only for
+    T < 2, so the conditioning kappa = sum_k |g_k| / n of the discrete equilibrium stays near 1 for every Q below
+    it and grows without bound with Q above it (the Mach 2.0 downstream state u = 1.19, T = 2.08; T = 2.5 at rest)."""
+    def kappa(Q, u, T):
+        p, w = O.quadrature(Q)
+        return float(np.abs(O.equilibrium(p, w, 1.0, u, T)).sum())
+
+    for u, T in ((0.0, 1.5), (1.19, 1.8), (2.64, 1.0)):
+        assert max(kappa(Q, u, T) for Q in (16, 32, 48, 64)) < 2.0, (u, T)
+    for u, T in ((1.19, 2.08), (0.0, 2.5)):
+        k = [kappa(Q, u, T) for Q in (16, 32, 48, 64)]
+        assert all(b > 3.0 * a for a, b in zip(k[1:], k[2:])) and k[-1] > 1e3, (u, T, k)
