@@ -682,3 +682,23 @@ def test_hermite_equilibrium_conditioning_bounded_only_below_twice_the_reference
     for u, T in ((1.19, 2.08), (0.0, 2.5)):
         k = [kappa(Q, u, T) for Q in (16, 32, 48, 64)]
         assert all(b > 3.0 * a for a, b in zip(k[1:], k[2:])) and k[-1] > 1e3, (u, T, k)
+
+
+def test_rhs_is_the_sum_of_its_pinned_terms():
+    """The oracle's right-hand side equals relaxation + J1 - advection rebuilt cell by cell from the separately
+    pinned moments, Shakhov targets, J1, CD6 and WENO-5 faces (periodic, off-equilibrium state)."""
+    from rhs_terms import rhs_terms
+    from paper_2211_16933_gb300 import inputs
+    nx, Q = 24, 16
+    p, _ = O.quadrature(Q)
+    m = O.make_model(Q, nx, 1.0, 1e-3, 0.4, 0.05, bc=O.BC_PERIODIC)
+    r, u, T = inputs.smooth_periodic_fields(nx, seed=3, amp=(0.1, 0.2, 0.1))
+    ph, th = O.equilibrium_state(m, r, u, T)
+    ph = ph * inputs.state_noise(ph.shape, seed=4, scale=2e-2)
+    th = th * inputs.state_noise(th.shape, seed=5, scale=2e-2)
+    Lp, Lt = O.rhs(m, ph, th)
+    relax, j1, adv = rhs_terms(m, ph, th)
+    for c, L in enumerate((Lp, Lt)):
+        np.testing.assert_allclose(relax[c] + j1[c] - adv[c], L, rtol=0, atol=1e-12 * np.abs(L).max())
+    assert np.abs(j1[0]).max() > 1e-3 * np.abs(Lp).max()  # every term matters here
+    assert np.abs(adv[0]).max() > 1e-3 * np.abs(Lp).max()
