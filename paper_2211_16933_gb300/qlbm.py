@@ -458,6 +458,8 @@ class Closure:
         nsteps = len(lr)
         if nsteps == 0:
             return
+        if perm.numel() % nsteps != 0:
+            raise ValueError("perm must hold the same number of samples for every step")
         B = perm.numel() // nsteps
         _ccheck(lib().ql_closure_train_steps(self.c, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                              C.c_void_p(periodic.data_ptr()), x.shape[0],
