@@ -215,7 +215,36 @@ def _oracle_sample(w, steps, warmup):
     ups = ns * Q * steps / el
     sample = (f"{steps} oracle RK3 steps (FP64, 1 thread) on {ns} cells around the membrane of the "
               f"Nx={nx}, Q={Q} Sod tube, same dx and dt")
-    return ups, el, sample
+    # the window problem and its oracle result, for the error statement of the GPU run
+    window = dict(Q=Q, nx=ns, length=ns * dx, dt=dt, denseness=w["denseness"], kn=w["kn"] * w["length"] / (ns * dx),
+                  fields=(r, u, T), ghost=[tuple(c) for c in np.stack(gl, 1)] + [tuple(c) for c in np.stack(gr, 1)],
+                  steps=warmup + steps, model=m, phi=ph, theta=th)
+    return ups, el, sample, window
+
+
+def _errors_vs_oracle(window, precision):
+    """L-inf and L2 errors of rho, u, T, P, q of the library's run of the oracle's window problem (same cells,
+    ghosts, dx, dt and steps), each normalised by its reference scale: rho_ref, sqrt(T_ref), T_ref,
+    rho_ref T_ref (1 + Y0), rho_ref T_ref^(3/2) with rho_ref = T_ref = 1."""
+    import oracle as O
+    from paper_2211_16933_gb300 import qlbm as q
+    r, u, T = window["fields"]
+    s = q.Solver(window["Q"], window["nx"], window["length"], window["dt"], window["denseness"], window["kn"],
+                 bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_FIELDS, rho=r, u=u, T=T,
+                 ghost=np.asarray(window["ghost"], dtype=float).ravel(), precision=precision, pr_mode=q.QL_PR_DENSE)
+    s.step(window["steps"])
+    f_gpu = s.moments()
+    s.close()
+    m = window["model"]
+    f_or = O.fields(m, window["phi"], window["theta"])
+    Y0 = 4.0 * m.eta0 * O.chi_set(m.eta0)
+    scale = dict(rho=1.0, u=1.0, T=1.0, P=1.0 + Y0, q=1.0)
+    out = {"steps": window["steps"], "cells": window["nx"], "reference": "FP64 oracle, same window",
+           "normalisation": "rho_ref, sqrt(T_ref), T_ref, rho_ref T_ref (1 + Y0), rho_ref T_ref^1.5"}
+    for k, sc in scale.items():
+        d = (f_gpu[k] - f_or[k]) / sc
+        out[k] = {"linf": float(np.abs(d).max()), "l2": float(np.sqrt(np.mean(d * d)))}
+    return out
 
 
 def run_reference(args, w):
@@ -223,7 +252,7 @@ def run_reference(args, w):
     if rank != 0:
         return
     steps = max(1, args.steps)
-    ups, el, sample = _oracle_sample(w, steps, min(args.warmup, 1))
+    ups, el, sample, _ = _oracle_sample(w, steps, min(args.warmup, 1))
     line = {"impl": "reference", "metric": "cell-velocity updates/s", "value": ups, "unit": "updates/s",
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -330,9 +359,11 @@ def run_ours(args, w):
                "steps": ke, "pattern": "load fields (pinned) + K x (step, totals) + all fields"}
 
     cpu = None
+    errors = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        ups, el, sample = _oracle_sample(w, args.cpu_steps, 0)
+        ups, el, sample, window = _oracle_sample(w, args.cpu_steps, 0)
         cpu = {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+        errors = _errors_vs_oracle(window, prec)
 
     s.close()
     if rank == 0:
@@ -346,7 +377,8 @@ def run_ours(args, w):
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (3 state buffers of %.2f GiB)" % (
                                2 * Q * nx * elem / 2 ** 30)},
-                "roofline": roofline, "roofline_other": other_roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "roofline_other": other_roofline, "cpu_baseline": cpu,
+                "errors_vs_oracle": errors, "e2e": e2e,
                 "gpu_launches": 3 * args.steps,
                 "clocks": clocks, "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
         print(json.dumps(line), flush=True)
