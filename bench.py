@@ -563,9 +563,9 @@ def run_learned(args):
             "config": {"workload": "learned_closure_conv1d_5x64_k5", "pairs": args.pairs, "snapshots": 8,
                        "fine_cells": L.NF, "coarse_cells": L.NC, "fine_steps": S, "epochs": args.epochs,
                        "batch": args.train_batch, "lr": args.lr, "lr_schedule": "cosine to lr/20"},
-            # per training step: pack, 5 convs, mse, 5 wgrads + 5 partial sums, 4 edge terms + 4 transposed
-            # convs, adam, 5 weight casts
-            "gpu_launches": 27 * (nsamp // args.train_batch), "train_conv_tflops": train_tflops,
+            # per training step (graph nodes): gather + pack, 5 convs, mse, 5 wgrads + 5 partial sums,
+            # 4 edge terms + 4 transposed convs, loss sum, adam (with the weight casts), step counter
+            "gpu_launches": 28 * (nsamp // args.train_batch), "train_conv_tflops": train_tflops,
             "roofline": _tensor_roofline(train_tflops), "data_generation_s": t_gen,
             "train_s": t_train, "loss_per_epoch": losses, "held_out": held,
             "time_to_solution": {"pairs": n, "coarse_fp32_batch_plus_net_s": t_learned,

@@ -436,14 +436,17 @@ __global__ void pack_input_kernel(const float *__restrict__ x, int64_t n, int ci
     out[e] = __float2bfloat16(v);
 }
 
-// The same for the mini-batch idx[0..B) of a data set of n samples (X positions
-// each), with the samples' padding kinds gathered into perb.  An index outside
+// The same for the mini-batch idx[0..B) = perm[step B ..] (step read from the
+// device) of a data set of n samples (X positions each), with the samples'
+// padding kinds gathered into perb.  An index outside
 // [0, n) sets *bad and reads sample 0 instead, so nothing is read out of bounds.
 __global__ void pack_gather_kernel(const float *__restrict__ x, const int32_t *__restrict__ per,
-                                   const int32_t *__restrict__ idx, int64_t n, int B, int X, int cin, int cinp,
-                                   const float *__restrict__ shift, const float *__restrict__ inv_scale,
-                                   bf16 *__restrict__ out, int32_t *__restrict__ perb, unsigned *__restrict__ bad)
+                                   const int32_t *__restrict__ perm, const int *__restrict__ step, int64_t n, int B,
+                                   int X, int cin, int cinp, const float *__restrict__ shift,
+                                   const float *__restrict__ inv_scale, bf16 *__restrict__ out,
+                                   int32_t *__restrict__ perb, unsigned *__restrict__ bad)
 {
+    const int32_t *__restrict__ idx = perm + int64_t(*step) * B;  // this step's samples
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < B) {
         const int64_t k = idx[e];
@@ -468,9 +471,12 @@ __global__ void pack_gather_kernel(const float *__restrict__ x, const int32_t *_
 // y rows of the batch: y[b] directly, or y[idx[b]] of the whole data set
 // (idx already checked by pack_gather_kernel; X positions per sample).
 __global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ y, const int32_t *__restrict__ idx,
-                           int X, int64_t npos, int cout, int coutp, const float *__restrict__ inv_out_scale,
-                           float grad_scale, bf16 *__restrict__ dpred, float *__restrict__ partial)
+                           const int *__restrict__ step, int X, int64_t npos, int cout, int coutp,
+                           const float *__restrict__ inv_out_scale, float grad_scale, bf16 *__restrict__ dpred,
+                           float *__restrict__ partial)
 {
+    // step (device, may be null): the batch is idx[step * B ..] of a training run's permutation
+    if (idx && step) idx += int64_t(*step) * (npos / X);
     __shared__ float red[256];
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     float se = 0.f;
@@ -512,8 +518,10 @@ __global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npo
 // Mean loss of one batch from the per-block partial sums of mse_kernel, summed
 // in a fixed order by one block of 256 threads: each thread adds its strided
 // share in FP32, the thread sums are combined in FP64.
-__global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, float scale, float *__restrict__ out)
+__global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, float scale, float *__restrict__ out,
+                                const int *__restrict__ step)
 {
+    if (step) out += *step;
     __shared__ double red[256];
     // four independent running sums per thread (loads in flight), combined in order
     float s4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -531,6 +539,9 @@ __global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, f
     if (threadIdx.x == 0) *out = float(red[0] * double(scale));
 }
 
+// Advances the device step counter of a training run (last node of a step).
+__global__ void step_inc_kernel(int *step) { *step += 1; }
+
 // Adam on FP32 master parameters; refreshes the bf16 weight copies, the
 // tap-flipped transposed copies used by the backward pass, and the f32 biases.
 constexpr int kAdamLayers = 8;  // layers whose bf16 copies the Adam pass refreshes itself
@@ -539,6 +550,9 @@ struct AdamArgs {
     const float *grad;
     int64_t n;
     float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+    // training runs: lr, c1, c2 of step *step from device arrays (null: the scalars above)
+    const int *step;
+    const float *lr_arr, *c1_arr, *c2_arr;
     // bf16 copies written in the same pass (nl = 0: none): layer l's W[co][j][ci]
     // at woff[l] (cout[l] x 5 x cin[l]) into w16 and, tap-flipped and
     // transposed, into wt16 at the same offset
@@ -556,7 +570,14 @@ __global__ void adam_kernel(AdamArgs a)
     const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
     a.m[i] = m;
     a.v[i] = v;
-    const float p = a.param[i] - a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+    float lr = a.lr, c1 = a.c1, c2 = a.c2;
+    if (a.step) {
+        const int t = *a.step;
+        lr = a.lr_arr[t];
+        c1 = a.c1_arr[t];
+        c2 = a.c2_arr[t];
+    }
+    const float p = a.param[i] - lr * (m * c1) / (sqrtf(v * c2) + a.eps);
     a.param[i] = p;
     for (int l = 0; l < a.nl; ++l) {
         const int64_t e = i - a.woff[l];
@@ -670,6 +691,15 @@ struct ql_closure {
     // padding kinds of ql_closure_train_steps' mini-batch and its out-of-range index flag
     int32_t *perb = nullptr;
     unsigned *bad = nullptr;
+    // ql_closure_train_steps: one step captured as a graph (keyed by its pointers and sizes) and replayed;
+    // the device step counter and the per-step lr, 1/(1-b1^t), 1/(1-b2^t) tables it reads
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[5] = {};
+    int64_t gkey_n = 0, gkey_B = 0;
+    int *d_step = nullptr;
+    float *d_sched = nullptr;
+    int64_t sched_cap = 0;
     int wgrid = 0;
     int64_t step = 0;
     std::string err;
@@ -701,8 +731,10 @@ static void closure_release(ql_closure *c)
 {
     for (void *p : {(void *)c->param, (void *)c->grad, (void *)c->m, (void *)c->v, (void *)c->w16, (void *)c->wt16,
                     (void *)c->pred, (void *)c->partial, (void *)c->loss_partial, (void *)c->edge,
-                    (void *)c->norm, (void *)c->perb, (void *)c->bad})
+                    (void *)c->norm, (void *)c->perb, (void *)c->bad, (void *)c->d_step, (void *)c->d_sched})
         cfree_dev(c, p);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (bf16 *p : c->act) cfree_dev(c, p);
     for (bf16 *p : c->dz) cfree_dev(c, p);
 }
@@ -758,9 +790,12 @@ static ql_status pack(ql_closure *c, const float *x, int B)
 }
 
 static ql_status adam_step(ql_closure *c, float lr);
+static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
+                                    int64_t n, const int32_t *perm, int64_t B, float *losses);
 
 // Loss, gradients of all parameters into c->grad; loss (host) if not null.
-static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, const int *per, int B, float *loss)
+static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, const int *ystep, const int *per, int B,
+                          float *loss)
 {
     const int X = c->d.positions, nl = int(c->layers.size());
     const int64_t npos = int64_t(B) * X;
@@ -768,7 +803,8 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
     const int64_t nel = npos * coutp;
     const unsigned nb = unsigned((nel + 255) / 256);
     const float gscale = 2.f / float(npos * c->d.out_channels);
-    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, yidx, X, npos, c->d.out_channels, coutp, c->norm + 24, gscale,
+    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, yidx, ystep, X, npos, c->d.out_channels, coutp, c->norm + 24,
+                                          gscale,
                                           c->dz[nl - 1], c->loss_partial);
     QC_CUDA(c, cudaGetLastError());
     for (int l = nl - 1; l >= 0; --l) {
@@ -922,7 +958,7 @@ ql_status ql_closure_gradients(ql_closure *c, const float *x, const float *y, co
     if (!c || !x || !y || !periodic || B < 1 || B > c->d.max_batch) return cfail(c, QL_EINVAL, "bad arguments");
     ql_status st = pack(c, x, int(B));
     if (st == QL_OK) st = forward(c, periodic, int(B));
-    if (st == QL_OK) st = backward(c, y, nullptr, periodic, int(B), loss);
+    if (st == QL_OK) st = backward(c, y, nullptr, nullptr, periodic, int(B), loss);
     if (st != QL_OK) return st;
     if (grad_host) {
         QC_CUDA(c, cudaMemcpyAsync(grad_host, c->grad, sizeof(float) * c->nparam, cudaMemcpyDeviceToHost, c->stream));
@@ -945,26 +981,66 @@ ql_status ql_closure_train_steps(ql_closure *c, const float *x, const float *y, 
     if (!c || !x || !y || !periodic || !perm || n < 1 || nsteps < 0 || B < 1 || B > c->d.max_batch ||
         (nsteps > 0 && !lr))
         return cfail(c, QL_EINVAL, "bad arguments");
-    const int X = c->d.positions;
-    const int64_t npos = B * X;
-    const unsigned nb = unsigned((npos * c->layers.back().cout + 255) / 256);
-    const float lscale = float(1.0 / double(npos * c->d.out_channels));
     QC_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(unsigned), c->stream));
-    for (int64_t s = 0; s < nsteps; ++s) {
-        const int32_t *idx = perm + s * B;
-        const int cinp = c->layers[0].cin;
-        pack_gather_kernel<<<unsigned((B * X * cinp + 255) / 256), 256, 0, c->stream>>>(
-            x, periodic, idx, n, int(B), X, c->d.in_channels, cinp, c->norm, c->norm + 8, c->act[0], c->perb, c->bad);
-        QC_CUDA(c, cudaGetLastError());
-        ql_status st = forward(c, c->perb, int(B));
-        if (st == QL_OK) st = backward(c, y, idx, c->perb, int(B), nullptr);
-        if (st != QL_OK) return st;
-        if (losses) {
-            loss_sum_kernel<<<1, 256, 0, c->stream>>>(c->loss_partial, int(nb), lscale, losses + s);
-            QC_CUDA(c, cudaGetLastError());
+    if (nsteps > 0) {
+        if (!c->d_step) {
+            c->d_step = static_cast<int *>(calloc_dev(c, sizeof(int)));
+            if (!c->d_step) return cfail(c, QL_ENOMEM, "step counter allocation failed");
         }
-        st = adam_step(c, lr[s]);
-        if (st != QL_OK) return st;
+        if (nsteps > c->sched_cap) {
+            cfree_dev(c, c->d_sched);
+            c->sched_cap = 0;
+            c->d_sched = static_cast<float *>(calloc_dev(c, sizeof(float) * 3 * size_t(nsteps)));
+            if (!c->d_sched) return cfail(c, QL_ENOMEM, "schedule allocation failed");
+            c->sched_cap = nsteps;
+            if (c->gexec) cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        // the schedule of steps step+1 .. step+nsteps, in the arithmetic of the single-step path
+        const int64_t cap = c->sched_cap;
+        std::vector<float> h(size_t(3 * cap), 0.f);
+        for (int64_t s = 0; s < nsteps; ++s) {
+            const double t = double(c->step + s + 1);
+            h[size_t(s)] = lr[s];
+            h[size_t(cap + s)] = float(1.0 / (1.0 - pow(0.9, t)));
+            h[size_t(2 * cap + s)] = float(1.0 / (1.0 - pow(0.999, t)));
+        }
+        QC_CUDA(c, cudaMemcpyAsync(c->d_sched, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, c->stream));
+        QC_CUDA(c, cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
+
+        const void *key[5] = {x, y, periodic, perm, losses};
+        if (c->gexec && (!std::equal(key, key + 5, c->gkey) || c->gkey_n != n || c->gkey_B != B)) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        if (!c->gexec) {
+            // capture on a stream of our own (the caller's may be the legacy default stream)
+            if (!c->cap_stream) QC_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            cudaStream_t user = c->stream;
+            c->stream = c->cap_stream;
+            cudaGraph_t g = nullptr;
+            ql_status st = QL_ECUDA;
+            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+                st = enqueue_train_step(c, x, y, periodic, n, perm, B, losses);
+                if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess) st = QL_ECUDA;
+            }
+            c->stream = user;
+            if (st == QL_OK && cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) c->gexec = nullptr;
+            if (g) cudaGraphDestroy(g);
+            (void)cudaGetLastError();  // a capture that failed leaves the plain launches below
+            std::copy(key, key + 5, c->gkey);
+            c->gkey_n = n;
+            c->gkey_B = B;
+        }
+        for (int64_t s = 0; s < nsteps; ++s) {
+            if (c->gexec) {
+                QC_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+            } else {
+                ql_status st = enqueue_train_step(c, x, y, periodic, n, perm, B, losses);
+                if (st != QL_OK) return st;
+            }
+        }
+        c->step += nsteps;
     }
     unsigned bad = 0;
     QC_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
@@ -975,21 +1051,34 @@ ql_status ql_closure_train_steps(ql_closure *c, const float *x, const float *y, 
 
 }  // extern "C"
 
+static AdamArgs adam_args(ql_closure *c);
+
 static ql_status adam_step(ql_closure *c, float lr)
 {
     c->step += 1;
+    AdamArgs a = adam_args(c);
+    a.lr = lr;
+    a.c1 = float(1.0 / (1.0 - pow(0.9, double(c->step))));
+    a.c2 = float(1.0 / (1.0 - pow(0.999, double(c->step))));
+    adam_kernel<<<unsigned((c->nparam + 255) / 256), 256, 0, c->stream>>>(a);
+    QC_CUDA(c, cudaGetLastError());
+    return a.nl ? QL_OK : refresh_weights(c);
+}
+
+static AdamArgs adam_args(ql_closure *c)
+{
     AdamArgs a;
     a.param = c->param;
     a.m = c->m;
     a.v = c->v;
     a.grad = c->grad;
     a.n = c->nparam;
-    a.lr = lr;
+    a.lr = a.c1 = a.c2 = 0.f;
     a.b1 = 0.9f;
     a.b2 = 0.999f;
     a.eps = 1e-8f;
-    a.c1 = float(1.0 / (1.0 - pow(0.9, double(c->step))));
-    a.c2 = float(1.0 / (1.0 - pow(0.999, double(c->step))));
+    a.step = nullptr;
+    a.lr_arr = a.c1_arr = a.c2_arr = nullptr;
     const bool fused = c->layers.size() <= size_t(kAdamLayers);
     a.w16 = c->w16;
     a.wt16 = c->wt16;
@@ -999,9 +1088,45 @@ static ql_status adam_step(ql_closure *c, float lr)
         a.cout[l] = c->layers[l].cout;
         a.cin[l] = c->layers[l].cin;
     }
+    return a;
+}
+
+// One step of a training run on c->stream: the mini-batch perm[t B ..], the loss
+// slot losses[t] (losses may be null) and the schedule entries are those of the
+// device step counter t, which the last launch advances.
+static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
+                                    int64_t n, const int32_t *perm, int64_t B, float *losses)
+{
+    const int X = c->d.positions;
+    const int64_t npos = B * X;
+    const unsigned nb = unsigned((npos * c->layers.back().cout + 255) / 256);
+    const float lscale = float(1.0 / double(npos * c->d.out_channels));
+    const int cinp = c->layers[0].cin;
+    pack_gather_kernel<<<unsigned((B * X * cinp + 255) / 256), 256, 0, c->stream>>>(
+        x, periodic, perm, c->d_step, n, int(B), X, c->d.in_channels, cinp, c->norm, c->norm + 8, c->act[0], c->perb,
+        c->bad);
+    QC_CUDA(c, cudaGetLastError());
+    ql_status st = forward(c, c->perb, int(B));
+    if (st == QL_OK) st = backward(c, y, perm, c->d_step, c->perb, int(B), nullptr);
+    if (st != QL_OK) return st;
+    if (losses) {
+        loss_sum_kernel<<<1, 256, 0, c->stream>>>(c->loss_partial, int(nb), lscale, losses, c->d_step);
+        QC_CUDA(c, cudaGetLastError());
+    }
+    AdamArgs a = adam_args(c);
+    a.step = c->d_step;
+    a.lr_arr = c->d_sched;
+    a.c1_arr = c->d_sched + c->sched_cap;
+    a.c2_arr = c->d_sched + 2 * c->sched_cap;
     adam_kernel<<<unsigned((c->nparam + 255) / 256), 256, 0, c->stream>>>(a);
     QC_CUDA(c, cudaGetLastError());
-    return fused ? QL_OK : refresh_weights(c);
+    if (!a.nl) {
+        st = refresh_weights(c);
+        if (st != QL_OK) return st;
+    }
+    step_inc_kernel<<<1, 1, 0, c->stream>>>(c->d_step);
+    QC_CUDA(c, cudaGetLastError());
+    return QL_OK;
 }
 
 extern "C" {

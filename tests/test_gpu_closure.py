@@ -170,6 +170,33 @@ def test_device_training_loop_equals_single_steps(gpu):
     assert e.value.status == q.QL_EINVAL
 
 
+def test_device_training_loop_across_calls(gpu):
+    """Repeated ql_closure_train_steps calls on the same buffers (the recorded step replayed, the Adam step
+    count carried over), then a longer call without losses on new buffers, give bitwise the parameters of
+    ql_closure_train_step on the same batches."""
+    import torch
+    q = gpu
+    rng = np.random.default_rng(12)
+    n, B, X = 40, 8, 64
+    dev = torch.device("cuda", 0)
+    xd = torch.tensor(rng.normal(0, 1, (n, X, 7)).astype(np.float32), device=dev)
+    yd = torch.tensor(rng.normal(0, 0.5, (n, X, 5)).astype(np.float32), device=dev)
+    pd = torch.tensor(rng.integers(0, 2, n).astype(np.int32), device=dev)
+    a = q.Closure(7, 5, X, B, seed=4)
+    b = q.Closure(7, 5, X, B, seed=4)
+    perm = torch.tensor(rng.permutation(n)[:3 * B].astype(np.int32), device=dev)
+    losses = torch.zeros(3, dtype=torch.float32, device=dev)
+    longer = torch.tensor(rng.integers(0, n, 7 * B).astype(np.int32), device=dev)
+    calls = [(perm, np.float32([3e-3, 2e-3, 1e-3]), losses), (perm, np.float32([1e-3, 5e-4, 2e-3]), losses),
+             (longer, np.linspace(1e-3, 4e-3, 7).astype(np.float32), None)]
+    for pm, rates, ls in calls:
+        a.train_steps(xd, yd, pd, pm, rates, ls)
+        for s in range(len(rates)):
+            idx = pm[s * B:(s + 1) * B].long()
+            b.train_step(xd[idx].contiguous(), yd[idx].contiguous(), pd[idx].contiguous(), float(rates[s]))
+        np.testing.assert_array_equal(a.get_params(), b.get_params())
+
+
 def test_trained_closure_improves_held_out_coarse_fields(gpu):
     from paper_2211_16933_gb300 import learned as L
     train_specs = L.pair_specs(48, 0)
