@@ -15,9 +15,10 @@ pytestmark = pytest.mark.gpu
 def test_eta_sweep_matches_linear_theory(gpu):
     from paper_2211_16933_gb300 import dispersion as D
     rows, _ = D.study([0.01, 0.1, 0.4825, 1.917], t_end=5.0, samples=500)
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open(os.path.join("gpurun_out", "dispersion_rows.json"), "w") as f:
-        json.dump(rows, f, indent=1)
+    out = os.environ.get("QL_DISPERSION_ROWS")  # optional: keep the fitted rows as JSON
+    if out:
+        with open(out, "w") as f:
+            json.dump(rows, f, indent=1)
     for r in rows:
         assert r["fit_rms"] < 2e-2, r
         # the sound speed is thermodynamic: J1 must give the dense-gas value at every density
