@@ -56,9 +56,10 @@ _STAGE_SOURCES = {
     "fp32": ("paper_2211_16933_gb300/csrc/fdlb_f32.cu", "paper_2211_16933_gb300/csrc/fdlb_impl.cuh",
              "paper_2211_16933_gb300/csrc/fdlb_kernels.cuh", "paper_2211_16933_gb300/csrc/qlbm_internal.h",
              "include/qlbm.h"),
+    # the generic large-Q kernels (fdlb_lq.cuh) share the FP64 translation unit but not the tiled kernel's code
     "fp64": ("paper_2211_16933_gb300/csrc/fdlb_f64.cu", "paper_2211_16933_gb300/csrc/fdlb_impl.cuh",
-             "paper_2211_16933_gb300/csrc/fdlb_kernels.cuh", "paper_2211_16933_gb300/csrc/fdlb_lq.cuh",
-             "paper_2211_16933_gb300/csrc/qlbm_internal.h", "include/qlbm.h"),
+             "paper_2211_16933_gb300/csrc/fdlb_kernels.cuh", "paper_2211_16933_gb300/csrc/qlbm_internal.h",
+             "include/qlbm.h"),
 }
 
 
