@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -63,10 +64,19 @@ _STAGE_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/CUDA source without comments, trailing blanks and empty lines (the sources hold no comment markers
+    inside string literals), so that a comment edit leaves the fingerprint unchanged."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def _kernel_hash(precision_name="fp32"):
+    """Fingerprint of the code the stage kernel of this precision is compiled from."""
     h = hashlib.sha256()
     for f in _STAGE_SOURCES[precision_name]:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
