@@ -66,8 +66,8 @@ enum { QL_CHI_SET = 0, QL_CHI_RET_FM = 1 };
  * kind).  Tiled kernels exist for Q in {8, 16, 20, 24, 32, 40} (the batched
  * form: {8, 16, 24, 32}); any other even Q up to 200 (the paper's
  * near-ballistic runs use 200) runs on a generic FP64 path whose per-cell
- * work grows as Q^2: FP64 and chi_SET only, for domains of the paper's sizes
- * (hundreds to thousands of cells). */
+ * work grows as Q^2: FP64 only (chi_SET or chi_RET-FM), for domains of the
+ * paper's sizes (hundreds to thousands of cells). */
 typedef struct {
     int32_t Q;
     int32_t kind;

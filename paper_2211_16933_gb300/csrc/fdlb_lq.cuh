@@ -11,9 +11,13 @@
 //                      G[k][.] shared by the block), the update.
 // Large Q (the paper's near-ballistic runs use Q = 200) makes the per-cell work
 // O(Q^2), so this path is arithmetic bound; it serves problem sizes of the
-// paper's (a few hundred cells), not the tiled kernel's.  Included by the FP64
+// paper's (a few hundred cells), not the tiled kernel's.  With chi_RET-FM
+// (Eq. chi_ret) the densities of the moments kernel are averaged over the ball
+// by fdlb_fm_kernel between the first two kernels.  Included by the FP64
 // translation unit only.
 #pragma once
+
+#include "qlbm_lq.h"
 
 namespace qlbm {
 
@@ -62,8 +66,9 @@ __global__ void lq_moments_kernel(LqArgs a)
 // Collision coefficients of interior cell i (Secs. II.A-II.C, Eq. j1): the
 // targets over the equilibrium are a cubic in xi = p - u, held as (phi, theta)
 // pairs already multiplied by n and 2 T n; coef[9 i ..] = C0, C1, C2, C3 (pairs),
-// 1/tau.
-__global__ void lq_coef_kernel(LqArgs a)
+// 1/tau.  nbar (chi_RET-FM, else null): the ball-averaged density of every
+// column.
+__global__ void lq_coef_kernel(LqArgs a, const double *__restrict__ nbar)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= a.nx) return;
@@ -75,7 +80,22 @@ __global__ void lq_coef_kernel(LqArgs a)
     const double du = cd6_<double>(mu, int(col)) * a.inv_dx;
     const double dlnT = cd6_<double>(lnT, int(col)) * a.inv_dx;
     const double rhat = n * a.inv_rho_ref, eta = a.eta0 * rhat, ome = 1.0 - eta;
-    const double chi = 0.5 * (2.0 - eta) / (ome * ome * ome);
+    double chi, dlnchi;
+    if (nbar) {
+        // Eq. (chi_ret): chi_SET of the averaged density; d ln chi as the
+        // 6th-order difference of ln chi_SET(nbar) over the 7 columns around
+        double lc[7];
+        for (int d = 0; d < 7; ++d) {
+            const double eb = a.eta0 * nbar[col - 3 + d] * a.inv_rho_ref, omb = 1.0 - eb;
+            const double cb = 0.5 * (2.0 - eb) / (omb * omb * omb);
+            if (d == 3) chi = cb;
+            lc[d] = log(cb);
+        }
+        dlnchi = cd6_<double>(lc, 3) * a.inv_dx;
+    } else {
+        chi = 0.5 * (2.0 - eta) / (ome * ome * ome);
+        dlnchi = eta * (3.0 / ome - 1.0 / (2.0 - eta)) * dlnn;  // chi_SET
+    }
     const double Y = 4.0 * eta * chi;
     const double muf = fma(fma(0.16 * (1.0 + 12.0 / 3.14159265358979323846), Y, 0.8), Y, 1.0);
     const double inv_tau = rhat * chi * sqrt(T) / (a.tau_pref * muf);
@@ -87,7 +107,6 @@ __global__ void lq_coef_kernel(LqArgs a)
     const double invT = 1.0 / T;
     const double A = (1.0 - Pr) * q * invT * invT / (5.0 * n);
     const double Yj = a.enskog ? Y : 0.0;
-    const double dlnchi = eta * (3.0 / ome - 1.0 / (2.0 - eta)) * dlnn;  // chi_SET
     const double G = dlnchi + 2.0 * dlnn;
     const double a0 = fma(0.6 * Yj, du, inv_tau);
     const double a1 = -3.0 * A * inv_tau - Yj * G - 0.1 * Yj * dlnT;
@@ -241,11 +260,15 @@ __global__ void __launch_bounds__(kMomThreads) lq_fields_kernel(MomentArgs a, in
     if (threadIdx.x < 3) a.partial[blockIdx.x * 3 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-cudaError_t launch_lq_stage(int stage, const LqArgs &a, cudaStream_t s)
+static cudaError_t lq_stage(int stage, const LqArgs &a, const FmArgs *fm, cudaStream_t s)
 {
     const int64_t ncol = a.nx + 2 * kHalo;
     lq_moments_kernel<<<unsigned((ncol + 255) / 256), 256, 0, s>>>(a);
-    lq_coef_kernel<<<unsigned((a.nx + 255) / 256), 256, 0, s>>>(a);
+    if (fm) {
+        const cudaError_t e = launch_fm_f64(*fm, s);
+        if (e != cudaSuccess) return e;
+    }
+    lq_coef_kernel<<<unsigned((a.nx + 255) / 256), 256, 0, s>>>(a, fm ? static_cast<const double *>(fm->nbar) : nullptr);
     const dim3 grid(unsigned((a.nx + kLqThreads - 1) / kLqThreads), unsigned(a.Q));
     const size_t smem = sizeof(double) * size_t(a.Q);
     switch (stage) {
@@ -256,6 +279,14 @@ cudaError_t launch_lq_stage(int stage, const LqArgs &a, cudaStream_t s)
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_lq_stage(int stage, const LqArgs &a, cudaStream_t s) { return lq_stage(stage, a, nullptr, s); }
+
+cudaError_t launch_lq_stage_ret(int stage, const LqArgs &a, const FmArgs &f, cudaStream_t s)
+{
+    if (f.n != static_cast<const void *>(a.mom + kHalo) || !f.nbar) return cudaErrorInvalidValue;
+    return lq_stage(stage, a, &f, s);
 }
 
 cudaError_t launch_lq_init(int Q, const double *rho, const double *u, const double *T, void *psi, int64_t nx,

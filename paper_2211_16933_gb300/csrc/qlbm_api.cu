@@ -11,6 +11,7 @@
 #include "../../include/qlbm.h"
 #include "qlbm_host.h"
 #include "qlbm_internal.h"
+#include "qlbm_lq.h"
 
 using namespace qlbm;
 
@@ -88,6 +89,8 @@ static void dev_free(ql_ctx *c, void *p)
     else cudaFree(p);
 }
 
+static FmArgs fm_args(ql_ctx *c);
+
 static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, void *out)
 {
     if (c->lq) {
@@ -111,6 +114,12 @@ static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, voi
         l.mom = c->d_lqmom;
         l.coef = c->d_lqcoef;
         l.err = c->d_err;
+        if (c->chi_mode == QL_CHI_RET_FM) {
+            // each stage averages the densities of its own input (its moments kernel writes them)
+            FmArgs f = fm_args(c);
+            f.n = c->d_lqmom + kHalo;
+            return launch_lq_stage_ret(s, l, f, c->stream);
+        }
         return launch_lq_stage(s, l, c->stream);
     }
     StageArgs a;
@@ -137,8 +146,8 @@ static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, voi
                                    : launch_stage_f64(c->Q, s, a, c->stream);
 }
 
-// chi_RET-FM: nbar of every column from the densities in d_n.
-static cudaError_t fm_average(ql_ctx *c)
+// chi_RET-FM: ball-average arguments, densities from d_n.
+static FmArgs fm_args(ql_ctx *c)
 {
     FmArgs f;
     f.n = c->d_n;
@@ -153,13 +162,21 @@ static cudaError_t fm_average(ql_ctx *c)
             f.ghost[g] = c->ghost_state[3 * (g + 1)];      // cells -3..-1: columns 1..3
             f.ghost[3 + g] = c->ghost_state[3 * (kHalo + g)];  // cells nx..nx+2
         }
+    return f;
+}
+
+// chi_RET-FM: nbar of every column from the densities in d_n.
+static cudaError_t fm_average(ql_ctx *c)
+{
+    const FmArgs f = fm_args(c);
     return c->precision == QL_FP32 ? launch_fm_f32(f, c->stream) : launch_fm_f64(f, c->stream);
 }
 
-// chi_RET-FM: densities of the current state psi^n, then nbar.
+// chi_RET-FM: densities of the current state psi^n, then nbar (the generic
+// large-Q path forms nbar inside each stage instead).
 static cudaError_t refresh_nbar(ql_ctx *c)
 {
-    if (c->chi_mode != QL_CHI_RET_FM) return cudaSuccess;
+    if (c->chi_mode != QL_CHI_RET_FM || c->lq) return cudaSuccess;
     cudaError_t e = c->precision == QL_FP32 ? launch_density_f32(c->Q, c->buf[0], c->nx, c->stride, c->d_n, c->stream)
                                             : launch_density_f64(c->Q, c->buf[0], c->nx, c->stride, c->d_n, c->stream);
     return e == cudaSuccess ? fm_average(c) : e;
@@ -226,8 +243,6 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     if (!qok && !lq) return fail(nullptr, QL_EUNSUPPORTED, "Q must be even and at most 200");
     if (lq && opts->precision != QL_FP64)
         return fail(nullptr, QL_EUNSUPPORTED, "velocity sets other than 8, 16, 20, 24, 32, 40 run in FP64 only");
-    if (lq && opts->chi_mode != QL_CHI_SET)
-        return fail(nullptr, QL_EUNSUPPORTED, "velocity sets other than 8, 16, 20, 24, 32, 40 use chi_SET only");
     if (grid->nx < 8 || grid->nx > (int64_t(1) << 31)) return fail(nullptr, QL_EINVAL, "nx must be in [8, 2^31]");
     if (!(grid->length > 0) || !(grid->dt > 0)) return fail(nullptr, QL_EINVAL, "length and dt must be > 0");
     if (!(denseness > 0) || !(kn > 0)) return fail(nullptr, QL_EINVAL, "denseness and kn must be > 0");
@@ -392,10 +407,10 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
 ql_status ql_step(ql_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
-    const bool ret = c->chi_mode == QL_CHI_RET_FM;
+    const bool ret = c->chi_mode == QL_CHI_RET_FM && !c->lq;
     for (int64_t s = 0; s < nsteps; ++s) {
-        // with chi_RET-FM each stage also writes the densities of its output,
-        // from which nbar for the next stage is averaged
+        // with chi_RET-FM each tiled stage also writes the densities of its
+        // output, from which nbar for the next stage is averaged
         cudaError_t e = stage(c, 1, c->buf[0], c->buf[0], c->buf[1]);
         if (e == cudaSuccess && ret) e = fm_average(c);
         if (e == cudaSuccess) e = stage(c, 2, c->buf[1], c->buf[0], c->buf[2]);

@@ -285,6 +285,40 @@ def test_ret_fm_differs_from_set(gpu):
     assert np.abs(Lr - Lo).max() <= 1e-11 * np.abs(Lo).max()
 
 
+@pytest.mark.parametrize("Q,bc,reach", [(48, "fixed", 4), (200, "periodic", 2)])
+def test_large_q_ret_fm_matches_oracle(gpu, Q, bc, reach):
+    """chi_RET-FM on the generic FP64 path (the paper's sigma = 1 shock runs use it with Q = 200): each stage
+    averages the densities of its own input over the ball; the right-hand side and 3 steps against the oracle,
+    a ball reaching `reach` cells on each side, and the chi_SET right-hand side of the same state differs."""
+    nx = 40
+    w = _smooth_workload(Q, nx, bc)
+    w["kn"] = (reach - 0.3) / (nx * w["denseness"])  # sigma = E_l Kn L
+    f = inputs.smooth_periodic_fields(nx, seed=Q + 5, amp=(0.2, 0.2, 0.1))
+    ghost = None
+    if bc == "fixed":
+        ghost = [(f[0][0], f[1][0], f[2][0])] * 3 + [(f[0][-1] * 0.9, f[1][-1], f[2][-1])] * 3
+    m, ph, th, s = _setup(gpu, w, 0, fields=f, ghost=ghost, chi_mode=1)
+    assert O.fm_halfwidth(m.dx, m.sigma) == reach
+    noise = inputs.state_noise(ph.shape, seed=Q + 6, scale=1e-2)
+    ph = ph * noise
+    s.set_state(ph, th)
+    Lp_o, Lt_o = O.rhs(m, ph, th)
+    Lp_g, Lt_g = s.rhs()
+    for a, b in ((Lp_g, Lp_o), (Lt_g, Lt_o)):
+        assert float(np.abs(a - b).max() / np.abs(b).max()) <= 1e-11
+    _, _, _, s_set = _setup(gpu, w, 0, fields=f, ghost=ghost, chi_mode=0)
+    s_set.set_state(ph, th)
+    Ls, _ = s_set.rhs()
+    assert np.abs(Lp_g - Ls).max() > 1e-6 * np.abs(Ls).max()
+    ph, th = O.run(m, ph, th, 3)
+    s.step(3)
+    errs = _field_errors(m, ph, th, s)
+    assert max(errs.values()) <= 1e-10, errs
+    gp, gt = s.state()
+    for a, b in ((gp, ph), (gt, th)):
+        assert float(np.abs(a - b).max() / np.abs(b).max()) <= 1e-11
+
+
 @pytest.mark.parametrize("Q", [16, 32])
 def test_fp32_totals_kernel_matches_field_totals(gpu, Q):
     """The FP32 totals-only kernel (double-FP32 sums and reductions) gives the domain totals of the field

@@ -125,11 +125,11 @@ def test_batch_create_rejects_an_empty_batch(qlbm_lib):
 
 
 def test_large_q_requirements_are_checked_before_touching_the_gpu(qlbm_lib):
-    """Velocity sets without tiled kernels: even Q up to 200, FP64, chi_SET."""
+    """Velocity sets without tiled kernels: even Q up to 200, FP64 (chi_SET or chi_RET-FM)."""
     q = qlbm_lib
     kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-3), use_torch=False)
     for Q, prec, chi in ((201, q.QL_FP64, 0), (202, q.QL_FP64, 0), (51, q.QL_FP64, 0), (64, q.QL_FP32, 0),
-                         (64, q.QL_FP64, q.QL_CHI_RET_FM)):
+                         (64, q.QL_FP32, q.QL_CHI_RET_FM)):
         with pytest.raises(q.QLError) as e:
             q.Solver(Q, 64, 1.0, 1e-4, 0.1, 0.1, precision=prec, chi_mode=chi, **kw)
         assert e.value.status == q.QL_EUNSUPPORTED, (Q, prec, chi)
