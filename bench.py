@@ -611,6 +611,80 @@ def run_dispersion(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's timed shock-tube runs (Table comp_time): sigma, Q, N_x, and the LB wall time on one core of an
+# Intel Xeon Gold 6330.
+PAPER_SHOCK_TABLE = [(0.001, 8, 1600, 62.0), (0.01, 8, 800, 32.0), (0.1, 20, 640, 71.0), (1.0, 200, 160, 176.0)]
+
+
+def run_paper_table(args):
+    """The shock tubes the paper times on one CPU core (Sec. IV, Table comp_time), on the GPU: Sod initial
+    state with eta_i = 0.05 (E_l = 0.4825) on the left and eta_i / 8 on the right, T = 1, u = 0, L = 80,
+    dt = 1e-3, chi_RET-FM, FP64, dense Pr, fixed ends, to t = 9 (9000 steps: the paper states no final time;
+    t = 9 is the reading of its section label, and it gives every row about the same time per update on the
+    paper's core).  Per row: time to solution from solver creation to the fields on the host, and the step
+    loop alone on CUDA events."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import qlbm as q
+    torch.cuda.set_device(0)
+    B.build()
+    El, L, dt, nsteps = 0.4825, 80.0, 1e-3, args.table_steps
+    prm = (1.0, 0.0, 1.0, 0.125, 0.0, 1.0)
+
+    def make(sig, Q, nx, prec):
+        return q.Solver(Q, nx, L, dt, El, sig / (El * L), bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN, prm=prm,
+                        precision=prec, pr_mode=q.QL_PR_DENSE, chi_mode=q.QL_CHI_RET_FM, device=0)
+
+    stream = torch.cuda.current_stream()
+
+    def timed(sig, Q, nx, prec):
+        w = make(sig, Q, nx, prec)  # warm-up: loads this row's kernels
+        w.step(3)
+        w.sync()
+        del w
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = make(sig, Q, nx, prec)
+        m0 = s.totals()[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(nsteps)
+        e1.record(stream)
+        f = s.moments()  # raises QLError on a non-physical state
+        return f, time.perf_counter() - t0, e0.elapsed_time(e1) * 1e-3, abs(f["totals"][0] - m0) / m0
+
+    rows = []
+    for sig, Q, nx, t_paper in PAPER_SHOCK_TABLE:
+        try:
+            f, tts, steps_s, dm = timed(sig, Q, nx, q.QL_FP64)
+        except q.QLError as e:  # a non-physical state is reported, not timed
+            rows.append({"sigma": sig, "Q": Q, "nx": nx, "error": str(e)})
+            continue
+        tiled = Q in q.SUPPORTED_Q
+        row = {"sigma": sig, "Q": Q, "nx": nx, "steps": nsteps, "time_to_solution_s": tts,
+               "step_loop_s": steps_s, "updates_per_s": nx * Q * nsteps / steps_s,
+               "paper_single_core_s": t_paper, "paper_over_ours": t_paper / tts, "mass_rel_change": dm,
+               "path": "tiled" if tiled else "generic large-Q"}
+        if tiled:  # the FP32 form on the same run, its fields against the FP64 ones (max-normalised L-inf)
+            try:
+                f32, tts32, steps32, dm32 = timed(sig, Q, nx, q.QL_FP32)
+                err = {k: float(np.abs(f32[k] - f[k]).max() / np.abs(f[k]).max()) for k in ("rho", "u", "T", "P", "q")}
+                row["fp32"] = {"time_to_solution_s": tts32, "step_loop_s": steps32,
+                               "paper_over_ours": t_paper / tts32, "mass_rel_change": dm32, "linf_vs_fp64": err}
+            except q.QLError as e:
+                row["fp32"] = {"error": str(e)}
+        rows.append(row)
+    line = {"metric": "time to solution", "value": sum(r.get("time_to_solution_s", float("nan")) for r in rows),
+            "unit": "s",
+            "n_gpus": 1, "steps": nsteps, "warmup": 3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper_shock_table_chi_ret_fm", "length": L, "dt": dt, "denseness": El,
+                       "t_end": nsteps * dt, "reading": "t_end = 9 (not stated in the paper)",
+                       "paper_hardware": "1 core of an Intel Xeon Gold 6330"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -623,7 +697,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion"], default="sod")
+    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table"], default="sod")
+    ap.add_argument("--table-steps", type=int, default=9000)
     ap.add_argument("--sweep", type=int, default=16)
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--eval-pairs", type=int, default=1000)
@@ -646,6 +721,9 @@ def main():
         return
     if args.workload == "dispersion" and args.impl == "ours":
         run_dispersion(args)
+        return
+    if args.workload == "paper_table" and args.impl == "ours":
+        run_paper_table(args)
         return
     if args.impl == "reference":
         run_reference(args, w)

@@ -173,7 +173,10 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
 
 /* Queues nsteps >= 0 steps of Eq. (rk3): three fused stage kernels per step,
  * each computing moments, equilibrium, Shakhov targets, J1, WENO-5 fluxes and
- * the Runge-Kutta combination for every (cell, velocity).  Asynchronous. */
+ * the Runge-Kutta combination for every (cell, velocity).  Asynchronous.  With
+ * nsteps > 1 the first call records one step as a CUDA graph (on a stream the
+ * context creates) and every step replays it, with results bitwise those of
+ * single steps; if recording fails the launches are issued one by one. */
 ql_status ql_step(ql_ctx *ctx, int64_t nsteps);
 
 /* Waits for the context's stream and reports the device error word. */

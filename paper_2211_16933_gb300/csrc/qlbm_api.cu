@@ -43,6 +43,11 @@ struct ql_ctx {
     double *d_fmk = nullptr;  // 2 fm_w + 1
     void *d_n = nullptr;      // nx values of the working precision
     void *d_nbar = nullptr;   // stride values (columns -kHalo .. ; the tail past nx + kHalo unused)
+    // ql_step of more than one step replays one recorded step (its launches
+    // read only buffers fixed for the context's lifetime)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_graph = nullptr;
+    bool step_graph_failed = false;
     std::string err;
 };
 
@@ -214,6 +219,10 @@ static ql_status upload_fields_and_init(ql_ctx *c, const double *rho, const doub
 
 static void destroy_buffers(ql_ctx *c)
 {
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->step_graph = nullptr;
+    c->cap_stream = nullptr;
     for (int b = 0; b < 3; ++b) dev_free(c, c->buf[b]);
     dev_free(c, c->d_fields);
     dev_free(c, c->d_init);
@@ -404,19 +413,59 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     return QL_OK;
 }
 
+// One step of Eq. (rk3) on c->stream: three stages and, with chi_RET-FM on the
+// tiled path, the ball average after each (each tiled stage also writes the
+// densities of its output, from which nbar for the next stage is averaged).
+static cudaError_t enqueue_step(ql_ctx *c)
+{
+    const bool ret = c->chi_mode == QL_CHI_RET_FM && !c->lq;
+    cudaError_t e = stage(c, 1, c->buf[0], c->buf[0], c->buf[1]);
+    if (e == cudaSuccess && ret) e = fm_average(c);
+    if (e == cudaSuccess) e = stage(c, 2, c->buf[1], c->buf[0], c->buf[2]);
+    if (e == cudaSuccess && ret) e = fm_average(c);
+    if (e == cudaSuccess) e = stage(c, 3, c->buf[2], c->buf[0], c->buf[0]);
+    if (e == cudaSuccess && ret) e = fm_average(c);
+    return e;
+}
+
+// Records one step as a CUDA graph, on a stream of the context's own (the
+// caller's may be the legacy default stream, which cannot be recorded).  A
+// recording that fails leaves the step to plain launches.
+static void record_step_graph(ql_ctx *c)
+{
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->cap_stream = nullptr;
+        c->step_graph_failed = true;
+        (void)cudaGetLastError();
+        return;
+    }
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        e = enqueue_step(c);
+        const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->step_graph = nullptr;
+        c->step_graph_failed = true;
+        (void)cudaGetLastError();
+    }
+}
+
 ql_status ql_step(ql_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
-    const bool ret = c->chi_mode == QL_CHI_RET_FM && !c->lq;
+    // small domains are launch-bound: several steps replay one recorded step
+    if (nsteps > 1 && !c->step_graph && !c->step_graph_failed) record_step_graph(c);
+    const bool replay = nsteps > 1 && c->step_graph;
     for (int64_t s = 0; s < nsteps; ++s) {
-        // with chi_RET-FM each tiled stage also writes the densities of its
-        // output, from which nbar for the next stage is averaged
-        cudaError_t e = stage(c, 1, c->buf[0], c->buf[0], c->buf[1]);
-        if (e == cudaSuccess && ret) e = fm_average(c);
-        if (e == cudaSuccess) e = stage(c, 2, c->buf[1], c->buf[0], c->buf[2]);
-        if (e == cudaSuccess && ret) e = fm_average(c);
-        if (e == cudaSuccess) e = stage(c, 3, c->buf[2], c->buf[0], c->buf[0]);
-        if (e == cudaSuccess && ret) e = fm_average(c);
+        const cudaError_t e = replay ? cudaGraphLaunch(c->step_graph, c->stream) : enqueue_step(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
     }
     return QL_OK;
