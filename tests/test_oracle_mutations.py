@@ -44,6 +44,15 @@ MUTATIONS = {
     "sound_alpha_a_gamma": ("out[1] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + muv + (gamma - 1.0) * lambda / cP);", "out[1] = k * k / (2.0 * rho) * (4.0 * mu / 3.0 + muv + gamma * lambda / cP);"),
     "sound_alpha_t_cp": ("out[3] = lambda * k * k / (rho * cP);", "out[3] = lambda * k * k / (rho * cV);"),
     "ret_prandtl_local_chi": ("double Pr = m->pr_mode == 0 ? m->pr_const : oq_prandtl_dense(Y);", "double Pr = oq_prandtl(m, n);"),
+    "shakhov_theta_poly": ("thetaS[k] = 2.0 * T * fmb[k] * (1.0 + a * (xi * xi / T - 1.0) * xi * q);", "thetaS[k] = 2.0 * T * fmb[k] * (1.0 + a * (xi * xi / T - 3.0) * xi * q);"),
+    "rk3_stage3": ("phi[e] = phi[e] / 3.0 + 2.0 / 3.0 * p2[e] + 2.0 / 3.0 * dt * Lp[e];", "phi[e] = phi[e] / 3.0 + 2.0 / 3.0 * p2[e] + 1.0 / 3.0 * dt * Lp[e];"),
+    "rk3_theta_stage2_operand": ("t2[e] = 0.75 * theta[e] + 0.25 * t1[e] + 0.25 * dt * Lt[e];", "t2[e] = 0.75 * theta[e] + 0.25 * t1[e] + 0.25 * dt * Lp[e];"),
+    "moments_pressure_tensor": ("Pi += xi * xi * phi[k];", "Pi += xi * phi[k];"),
+    "moments_heat_flux": ("q += xi * ek;", "q += xi * xi * ek;"),
+    "upwind_direction": ("if (pk > 0.0)", "if (pk < 0.0)"),
+    "weno_zero_indicator_case": ("if (z3 && z1) { om[0] = 0.25; om[1] = 0.0; om[2] = 0.75; return; }", "if (z3 && z1) { om[0] = 0.75; om[1] = 0.0; om[2] = 0.25; return; }"),
+    "j1_theta_du_coeff": ("0.6 * (xi * xi / T - 1.0 / 3.0) * du", "0.6 * (xi * xi / T - 1.0) * du"),
+    "j1_phi_dlnT_coeff": ("0.3 * (xi * xi * xi / T + xi / 3.0) * dlnT", "0.3 * (xi * xi * xi / T + xi) * dlnT"),
 }
 
 
