@@ -1,14 +1,18 @@
 // C ABI of the solver (include/qlbm.h): context, buffers, launches, copies.
 #include <cuda_runtime.h>
+#include <errno.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/qlbm.h"
+#include "../../include/qlbm_io.h"
 #include "qlbm_host.h"
 #include "qlbm_internal.h"
 #include "qlbm_lq.h"
@@ -48,6 +52,7 @@ struct ql_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t step_graph = nullptr;
     bool step_graph_failed = false;
+    int64_t steps = 0;  // steps advanced (restart files carry it)
     std::string err;
 };
 
@@ -467,6 +472,7 @@ ql_status ql_step(ql_ctx *c, int64_t nsteps)
     for (int64_t s = 0; s < nsteps; ++s) {
         const cudaError_t e = replay ? cudaGraphLaunch(c->step_graph, c->stream) : enqueue_step(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+        c->steps += 1;
     }
     return QL_OK;
 }
@@ -709,6 +715,276 @@ ql_status ql_rankine_hugoniot(double eta0, double rho_ref, double rho1, double T
 {
     if (!out || !rankine_hugoniot(eta0, rho_ref, rho1, T1, mach, out))
         return fail(nullptr, QL_EINVAL, "no compressive Rankine-Hugoniot solution");
+    return QL_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Restart files: a text header (first line and one JSON line) and the state.
+
+static const char kCkptMagic[] = "qlbm-checkpoint 1";
+
+static bool host_little_endian()
+{
+    const uint32_t one = 1;
+    unsigned char b;
+    memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+// Value after "key": in a one-line JSON object written by ql_save.
+static const char *json_value(const std::string &h, const char *key)
+{
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t at = h.find(k);
+    if (at == std::string::npos) return nullptr;
+    const char *v = h.c_str() + at + k.size();
+    while (*v == ' ') ++v;
+    return v;
+}
+
+static bool json_double(const std::string &h, const char *key, double *out)
+{
+    const char *v = json_value(h, key);
+    if (!v) return false;
+    char *end = nullptr;
+    *out = strtod(v, &end);
+    return end != v && isfinite(*out);
+}
+
+static bool json_int(const std::string &h, const char *key, int64_t *out)
+{
+    const char *v = json_value(h, key);
+    if (!v) return false;
+    char *end = nullptr;
+    *out = strtoll(v, &end, 10);
+    return end != v && (*end == ',' || *end == '}' || *end == ' ');
+}
+
+static bool json_string(const std::string &h, const char *key, std::string *out)
+{
+    const char *v = json_value(h, key);
+    if (!v || *v != '"') return false;
+    const char *e = strchr(v + 1, '"');
+    if (!e) return false;
+    out->assign(v + 1, e);
+    return true;
+}
+
+// Parses the header of an open restart file; leaves f at the state.
+static ql_status read_header(FILE *f, ql_checkpoint_info *in, std::string *why)
+{
+    if (!host_little_endian()) {
+        *why = "restart files are little-endian; this host is not";
+        return QL_EUNSUPPORTED;
+    }
+    char line[64];
+    if (!fgets(line, sizeof line, f) || strncmp(line, kCkptMagic, strlen(kCkptMagic)) != 0 ||
+        line[strlen(kCkptMagic)] != '\n') {
+        *why = "not a restart file (first line)";
+        return QL_EINVAL;
+    }
+    std::string h;
+    for (int ch; (ch = fgetc(f)) != EOF && ch != '\n';) {
+        h.push_back(char(ch));
+        if (h.size() > (1u << 16)) break;
+    }
+    if (h.empty() || h.front() != '{' || h.back() != '}') {
+        *why = "malformed header line";
+        return QL_EINVAL;
+    }
+    memset(in, 0, sizeof *in);
+    int64_t Q = 0, prm = 0, ens = 0, chi = 0;
+    std::string bc, prec, order;
+    bool ok = json_int(h, "Q", &Q) && json_int(h, "nx", &in->nx) && json_double(h, "length", &in->length) &&
+              json_double(h, "dt", &in->dt) && json_double(h, "denseness", &in->denseness) &&
+              json_double(h, "kn", &in->kn) && json_string(h, "bc", &bc) && json_string(h, "precision", &prec) &&
+              json_int(h, "pr_mode", &prm) && json_double(h, "pr_const", &in->pr_const) &&
+              json_int(h, "enskog", &ens) && json_double(h, "rho_ref", &in->rho_ref) &&
+              json_int(h, "chi_mode", &chi) && json_int(h, "steps", &in->steps) &&
+              json_string(h, "byte_order", &order);
+    ok = ok && (bc == "periodic" || bc == "fixed") && (prec == "fp64" || prec == "fp32") && order == "little";
+    ok = ok && Q >= 2 && Q <= kLargeMaxQ && in->nx >= 1 && in->nx <= (int64_t(1) << 31) && in->steps >= 0;
+    const char *g = json_value(h, "ghost");
+    ok = ok && g && *g == '[';
+    if (ok) {
+        ++g;
+        for (int j = 0; j < 18 && ok; ++j) {
+            while (*g == ' ' || *g == ',') ++g;
+            char *end = nullptr;
+            in->ghost[j] = strtod(g, &end);
+            ok = end != g && isfinite(in->ghost[j]);
+            g = end;
+        }
+        while (ok && *g == ' ') ++g;
+        ok = ok && *g == ']';
+    }
+    if (!ok) {
+        *why = "missing or malformed header field";
+        return QL_EINVAL;
+    }
+    in->Q = int32_t(Q);
+    in->bc_kind = bc == "fixed" ? QL_BC_FIXED : QL_BC_PERIODIC;
+    in->precision = prec == "fp32" ? QL_FP32 : QL_FP64;
+    in->pr_mode = int32_t(prm);
+    in->enskog = int32_t(ens);
+    in->chi_mode = int32_t(chi);
+    // the rest of the file is exactly the two state arrays
+    const long at = ftell(f);
+    if (at < 0 || fseek(f, 0, SEEK_END) != 0) {
+        *why = "cannot seek in the file";
+        return QL_EINVAL;
+    }
+    const long end = ftell(f);
+    const double want = 2.0 * double(in->nx) * double(Q) * sizeof(double);
+    if (end < 0 || double(end - at) != want || fseek(f, at, SEEK_SET) != 0) {
+        *why = "state size does not match nx and Q";
+        return QL_EINVAL;
+    }
+    return QL_OK;
+}
+
+ql_status ql_step_count(const ql_ctx *c, int64_t *steps)
+{
+    if (!c || !steps) return fail(nullptr, QL_EINVAL, "null argument to ql_step_count");
+    *steps = c->steps;
+    return QL_OK;
+}
+
+ql_status ql_save(ql_ctx *c, const char *path)
+{
+    if (!c || !path) return fail(c, QL_EINVAL, "null argument to ql_save");
+    const size_t n = size_t(c->nx) * size_t(c->Q);
+    std::vector<double> phi, theta;
+    try {
+        phi.resize(n);
+        theta.resize(n);
+    } catch (...) {
+        return fail(c, QL_ENOMEM, "host buffers for ql_save");
+    }
+    ql_status st = ql_get_state(c, phi.data(), theta.data());
+    if (st != QL_OK) return st;
+    double ghost[18] = {};
+    if (!c->periodic && c->ghost_state.size() >= size_t(3 * 2 * kHalo))
+        for (int g = 0; g < 3; ++g)
+            for (int v = 0; v < 3; ++v) {
+                ghost[3 * g + v] = c->ghost_state[3 * (g + 1) + v];          // cells -3..-1
+                ghost[9 + 3 * g + v] = c->ghost_state[3 * (kHalo + g) + v];  // cells nx..nx+2
+            }
+    std::string h = "{";
+    char b[96];
+    auto num = [&](const char *k, double v, bool last = false) {
+        snprintf(b, sizeof b, "\"%s\": %.17g%s", k, v, last ? "" : ", ");
+        h += b;
+    };
+    auto integer = [&](const char *k, int64_t v) {
+        snprintf(b, sizeof b, "\"%s\": %lld, ", k, (long long)v);
+        h += b;
+    };
+    integer("Q", c->Q);
+    integer("nx", c->nx);
+    num("length", c->L);
+    num("dt", c->dt);
+    num("denseness", c->El);
+    num("kn", c->kn);
+    h += std::string("\"bc\": \"") + (c->periodic ? "periodic" : "fixed") + "\", ";
+    h += std::string("\"precision\": \"") + (c->precision == QL_FP32 ? "fp32" : "fp64") + "\", ";
+    integer("pr_mode", c->pr_mode);
+    num("pr_const", c->pr_const);
+    integer("enskog", c->enskog);
+    num("rho_ref", c->rho_ref);
+    integer("chi_mode", c->chi_mode);
+    integer("steps", c->steps);
+    num("time", double(c->steps) * c->dt);
+    h += "\"ghost\": [";
+    for (int j = 0; j < 18; ++j) {
+        snprintf(b, sizeof b, "%.17g%s", ghost[j], j < 17 ? ", " : "");
+        h += b;
+    }
+    h += "], \"byte_order\": \"little\"}";
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string(long(getpid()));
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(c, QL_EINVAL, std::string("cannot write ") + tmp + ": " + strerror(errno));
+    bool ok = fprintf(f, "%s\n%s\n", kCkptMagic, h.c_str()) > 0 && fwrite(phi.data(), sizeof(double), n, f) == n &&
+              fwrite(theta.data(), sizeof(double), n, f) == n;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        const std::string why = strerror(errno);
+        remove(tmp.c_str());
+        return fail(c, QL_EINVAL, std::string("cannot write ") + path + ": " + why);
+    }
+    return QL_OK;
+}
+
+ql_status ql_checkpoint_read_info(const char *path, ql_checkpoint_info *info)
+{
+    if (!path || !info) return fail(nullptr, QL_EINVAL, "null argument to ql_checkpoint_read_info");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(nullptr, QL_EINVAL, std::string("cannot open ") + path + ": " + strerror(errno));
+    std::string why;
+    const ql_status st = read_header(f, info, &why);
+    fclose(f);
+    return st == QL_OK ? QL_OK : fail(nullptr, st, std::string(path) + ": " + why);
+}
+
+ql_status ql_load(const char *path, const ql_opts *opts, ql_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!path || !out) return fail(nullptr, QL_EINVAL, "null argument to ql_load");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(nullptr, QL_EINVAL, std::string("cannot open ") + path + ": " + strerror(errno));
+    ql_checkpoint_info in;
+    std::string why;
+    ql_status st = read_header(f, &in, &why);
+    if (st != QL_OK) {
+        fclose(f);
+        return fail(nullptr, st, std::string(path) + ": " + why);
+    }
+    const size_t n = size_t(in.nx) * size_t(in.Q);
+    std::vector<double> phi, theta;
+    try {
+        phi.resize(n);
+        theta.resize(n);
+    } catch (...) {
+        fclose(f);
+        return fail(nullptr, QL_ENOMEM, "host buffers for ql_load");
+    }
+    const bool got = fread(phi.data(), sizeof(double), n, f) == n && fread(theta.data(), sizeof(double), n, f) == n;
+    fclose(f);
+    if (!got) return fail(nullptr, QL_EINVAL, std::string(path) + ": short state");
+    // re-create from uniform fields and the stored fixed states (which set the
+    // ghost cells exactly as at the original creation), then load the state
+    ql_velset vs = {in.Q, 0};
+    ql_grid grid = {in.nx, in.length, in.dt};
+    ql_bc bc = {in.bc_kind, 0};
+    std::vector<double> r(size_t(in.nx), in.rho_ref), u(size_t(in.nx), 0.0), T(size_t(in.nx), 1.0);
+    ql_init init;
+    memset(&init, 0, sizeof init);
+    init.kind = QL_INIT_FIELDS;
+    init.rho = r.data();
+    init.u = u.data();
+    init.T = T.data();
+    init.ghost = in.bc_kind == QL_BC_FIXED ? in.ghost : nullptr;
+    ql_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    o.precision = in.precision;
+    o.pr_mode = in.pr_mode;
+    o.enskog = in.enskog;
+    o.chi_mode = in.chi_mode;
+    o.pr_const = in.pr_const;
+    o.rho_ref = in.rho_ref;
+    ql_ctx *c = nullptr;
+    st = ql_create(&vs, &grid, in.denseness, in.kn, &bc, &init, &o, &c);
+    if (st != QL_OK) return st;
+    st = ql_set_state(c, phi.data(), theta.data());
+    if (st != QL_OK) {
+        const std::string m = c->err;
+        ql_destroy(c);
+        return fail(nullptr, st, m);
+    }
+    c->steps = in.steps;
+    *out = c;
     return QL_OK;
 }
 

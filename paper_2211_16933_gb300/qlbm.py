@@ -32,7 +32,7 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc",
             "ql_batch_fields", "ql_batch_project", "ql_sound_modes", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
             "ql_closure_train_step", "ql_closure_train_steps", "ql_closure_params", "ql_closure_destroy",
-            "ql_closure_last_error")
+            "ql_closure_last_error", "ql_step_count", "ql_save", "ql_checkpoint_read_info", "ql_load")
 
 
 class QLError(RuntimeError):
@@ -75,6 +75,13 @@ class ql_instance(C.Structure):
     _fields_ = [("vs", ql_velset), ("grid", ql_grid), ("denseness", C.c_double), ("kn", C.c_double),
                 ("bc", ql_bc), ("init", ql_init), ("pr_mode", C.c_int32), ("enskog", C.c_int32),
                 ("pr_const", C.c_double), ("rho_ref", C.c_double)]
+
+
+class ql_checkpoint_info(C.Structure):
+    _fields_ = [("Q", C.c_int32), ("bc_kind", C.c_int32), ("precision", C.c_int32), ("pr_mode", C.c_int32),
+                ("enskog", C.c_int32), ("chi_mode", C.c_int32), ("nx", C.c_int64), ("steps", C.c_int64),
+                ("length", C.c_double), ("dt", C.c_double), ("denseness", C.c_double), ("kn", C.c_double),
+                ("pr_const", C.c_double), ("rho_ref", C.c_double), ("ghost", C.c_double * 18)]
 
 
 class ql_closure_desc(C.Structure):
@@ -141,6 +148,10 @@ def lib():
         L.ql_closure_destroy.argtypes = [V]
         L.ql_closure_last_error.argtypes = [V]
         L.ql_closure_last_error.restype = C.c_char_p
+        L.ql_step_count.argtypes = [V, C.POINTER(C.c_int64)]
+        L.ql_save.argtypes = [V, C.c_char_p]
+        L.ql_checkpoint_read_info.argtypes = [C.c_char_p, C.POINTER(ql_checkpoint_info)]
+        L.ql_load.argtypes = [C.c_char_p, C.POINTER(ql_opts), C.POINTER(V)]
         _lib = L
     return _lib
 
@@ -243,6 +254,28 @@ def ql_info(ctx, Q):
 
 def ql_destroy(ctx):
     _check(lib().ql_destroy(ctx))
+
+
+def ql_step_count(ctx) -> int:
+    n = C.c_int64()
+    _check(lib().ql_step_count(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def ql_save(ctx, path):
+    _check(lib().ql_save(ctx, os.fsencode(path)), ctx)
+
+
+def ql_checkpoint_read_info(path) -> ql_checkpoint_info:
+    info = ql_checkpoint_info()
+    _check(lib().ql_checkpoint_read_info(os.fsencode(path), C.byref(info)))
+    return info
+
+
+def ql_load(path, opts):
+    ctx = C.c_void_p()
+    _check(lib().ql_load(os.fsencode(path), C.byref(opts) if opts is not None else None, C.byref(ctx)))
+    return ctx
 
 
 def ql_step_noalloc(vs, grid, denseness, kn, bc, opts, psi, row_stride, nsteps):
@@ -524,6 +557,12 @@ class Solver:
         o.pr_const, o.rho_ref = pr_const, rho_ref
         o.chi_mode = QL_CHI_SET if chi_mode is None else chi_mode
         o.fault = fault
+        self._attach_torch(o, device, use_torch)
+        self.ctx = ql_create(vs, grid, denseness, kn, b, ini, o)
+        self._read_info()
+
+    def _attach_torch(self, o, device, use_torch):
+        """Work on PyTorch's current stream and device memory from its caching allocator, when available."""
         self._torch_blocks = {}
         if use_torch:
             import torch
@@ -545,10 +584,33 @@ class Solver:
 
                 self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
                 o.alloc, o.free = self._alloc_cb, self._free_cb
-        self.ctx = ql_create(vs, grid, denseness, kn, b, ini, o)
+
+    def _read_info(self):
+        Q = self.Q
         info = ql_info(self.ctx, Q)
         self.eta0, self.chi0, self.sigma, self.dx, self.dt, self.pmax = info[:6]
         self.p, self.w = info[6:6 + Q], info[6 + Q:]
+
+    @classmethod
+    def load(cls, path, *, device=0, use_torch=True):
+        """A solver resumed from a restart file written by save(): the stored parameters, state and step count."""
+        info = ql_checkpoint_read_info(path)
+        self = cls.__new__(cls)
+        self.Q, self.nx, self.precision = info.Q, info.nx, info.precision
+        self._keep = []
+        o = ql_opts()
+        o.device = device
+        self._attach_torch(o, device, use_torch)
+        self.ctx = ql_load(path, o)
+        self._read_info()
+        return self
+
+    def save(self, path):
+        """Writes a restart file (parameters, step count and state)."""
+        ql_save(self.ctx, path)
+
+    def step_count(self):
+        return ql_step_count(self.ctx)
 
     def step(self, n=1):
         ql_step(self.ctx, n)

@@ -72,3 +72,44 @@ def test_replayed_steps_equal_single_steps(gpu, precision, Q, chi):
     b.step(1)
     b.step(1)
     np.testing.assert_array_equal(a.state()[0], b.state()[0])
+
+
+@pytest.mark.parametrize("precision,Q,chi,bc", [(0, 32, 0, "fixed"), (1, 16, 1, "fixed"), (0, 48, 1, "periodic")])
+def test_resume_from_restart_file_is_bitwise(gpu, tmp_path, precision, Q, chi, bc):
+    """ql_save after N steps, ql_load into a new context, M more steps: bitwise the state and moments of an
+    uninterrupted N + M step run, with the step count carried over; tiled FP64 and FP32 (chi_RET-FM) with
+    fixed ends and the generic path (chi_RET-FM) with periodic ones, a constant Prandtl number."""
+    q = gpu
+    nx, L, El = 611, 1.0, 0.4825
+    p, _ = q.ql_velocity_set(Q)
+    dt = inputs.cfl_dt(L / nx, float(np.abs(p).max()))
+    kn = 3.7 / (nx * El)
+    if bc == "fixed":
+        kw = dict(bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN, prm=(1.0, 0.0, 1.0, 0.125, 0.0, 1.0))
+    else:
+        kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-2))
+
+    def make():
+        return q.Solver(Q, nx, L, dt, El, kn, precision=precision, chi_mode=chi, pr_mode=q.QL_PR_CONST,
+                        pr_const=0.7, **kw)
+    N, M = 6, 5
+    a = make()
+    a.step(N + M)
+    b = make()
+    b.step(N)
+    path = tmp_path / "run.qlbm"
+    b.save(path)
+    info = q.ql_checkpoint_read_info(path)
+    assert (info.Q, info.nx, info.steps, info.precision, info.chi_mode) == (Q, nx, N, precision, chi)
+    c = q.Solver.load(path)
+    assert c.step_count() == N
+    assert (c.dt, c.sigma, c.eta0) == (a.dt, a.sigma, a.eta0)
+    c.step(M)
+    assert c.step_count() == a.step_count() == N + M
+    pa, ta = a.state()
+    pc, tc = c.state()
+    np.testing.assert_array_equal(pc, pa)
+    np.testing.assert_array_equal(tc, ta)
+    ma, mc = a.moments(), c.moments()
+    for f in ("rho", "u", "T", "P", "q", "Pxx"):
+        np.testing.assert_array_equal(mc[f], ma[f])

@@ -2,6 +2,7 @@
 entry point the header declares, and its host physics (velocity set, E_l -> eta,
 sound speed, Rankine-Hugoniot states) agrees with the oracle and closed forms."""
 import ctypes
+import glob
 import math
 import os
 import re
@@ -15,9 +16,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "qlbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ql_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(ql_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol(qlbm_lib):
@@ -191,3 +194,65 @@ def test_bench_records_apply_only_to_their_workload():
     assert bench._alu_roofline("fp64", 1e9, 40) is None
     assert abs(bench.ALU_PEAK_TFLOPS["fp32"] - 80.54784) < 1e-9
     assert abs(bench.ALU_PEAK_TFLOPS["fp64"] - 1.25856) < 1e-12
+
+
+def _write_checkpoint(path, hdr, nvals, magic="qlbm-checkpoint 1", extra=0):
+    import json
+    with open(path, "wb") as f:
+        f.write((magic + "\n" + json.dumps(hdr) + "\n").encode())
+        f.write(np.arange(2 * nvals + extra, dtype="<f8").tobytes())
+
+
+def _ckpt_header(Q=8, nx=16):
+    return {"Q": Q, "nx": nx, "length": 80.0, "dt": 1e-3, "denseness": 0.4825, "kn": 1.0 / 38.6, "bc": "fixed",
+            "precision": "fp32", "pr_mode": 1, "pr_const": 2.0 / 3.0, "enskog": 1, "rho_ref": 1.0, "chi_mode": 1,
+            "steps": 9000, "time": 9.0, "ghost": [0.1 * j + 0.7 for j in range(18)], "byte_order": "little"}
+
+
+def test_restart_file_header_reads_back_without_the_gpu(qlbm_lib, tmp_path):
+    """A restart file in the documented layout: every field reads back to the same value (numbers written
+    with full precision), with no GPU call."""
+    q = qlbm_lib
+    path = tmp_path / "a.qlbm"
+    h = _ckpt_header()
+    _write_checkpoint(path, h, h["nx"] * h["Q"])
+    info = q.ql_checkpoint_read_info(path)
+    assert (info.Q, info.nx, info.steps) == (8, 16, 9000)
+    assert (info.bc_kind, info.precision, info.pr_mode, info.enskog, info.chi_mode) == (
+        q.QL_BC_FIXED, q.QL_FP32, 1, 1, q.QL_CHI_RET_FM)
+    for k in ("length", "dt", "denseness", "kn", "pr_const", "rho_ref"):
+        assert getattr(info, k) == h[k], k
+    assert list(info.ghost) == h["ghost"]
+
+
+@pytest.mark.parametrize("case", ["magic", "missing_field", "bad_bc", "short_state", "long_state", "no_file",
+                                  "bad_ghost", "big_q"])
+def test_malformed_restart_files_are_rejected_before_the_gpu(qlbm_lib, tmp_path, case):
+    """ql_checkpoint_read_info and ql_load refuse a file that is not a complete restart file with QL_EINVAL,
+    before any GPU call."""
+    q = qlbm_lib
+    path = tmp_path / "b.qlbm"
+    h = _ckpt_header()
+    n = h["nx"] * h["Q"]
+    if case == "magic":
+        _write_checkpoint(path, h, n, magic="qlbm-checkpoint 2")
+    elif case == "missing_field":
+        del h["kn"]
+        _write_checkpoint(path, h, n)
+    elif case == "bad_bc":
+        h["bc"] = "open"
+        _write_checkpoint(path, h, n)
+    elif case == "short_state":
+        _write_checkpoint(path, h, n, extra=-1)
+    elif case == "long_state":
+        _write_checkpoint(path, h, n, extra=1)
+    elif case == "bad_ghost":
+        h["ghost"] = h["ghost"][:17]
+        _write_checkpoint(path, h, n)
+    elif case == "big_q":
+        h["Q"] = 202
+        _write_checkpoint(path, h, h["nx"] * 202)
+    for call in (lambda: q.ql_checkpoint_read_info(path), lambda: q.ql_load(path, None)):
+        with pytest.raises(q.QLError) as e:
+            call()
+        assert e.value.status == q.QL_EINVAL, case
