@@ -196,6 +196,17 @@ def test_bench_records_apply_only_to_their_workload():
     assert abs(bench.ALU_PEAK_TFLOPS["fp64"] - 1.25856) < 1e-12
 
 
+def test_kernel_fingerprint_follows_code_not_comments():
+    """The fingerprint that scopes the ncu records ignores comments and blank lines and changes with any code
+    token."""
+    import bench
+    a = "int f(int x) {\n  return x + 1; // one\n}\n"
+    b = "/* the successor */\nint f(int x) {\n\n  return x + 1;   /* still one */\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
+
+
 def _write_checkpoint(path, hdr, nvals, magic="qlbm-checkpoint 1", extra=0):
     import json
     with open(path, "wb") as f:
