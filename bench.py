@@ -674,8 +674,11 @@ def run_paper_table(args):
             except q.QLError as e:
                 row["fp32"] = {"error": str(e)}
         rows.append(row)
+    # stepping kernels per step (graph nodes): tiled, 3 stages + 3 ball averages; generic path, 4 per stage
+    launches = sum(r["steps"] * (6 if r["path"] == "tiled" else 12) * (2 if "fp32" in r else 1)
+                   for r in rows if "steps" in r)
     line = {"metric": "time to solution", "value": sum(r.get("time_to_solution_s", float("nan")) for r in rows),
-            "unit": "s",
+            "unit": "s", "gpu_launches": launches,
             "n_gpus": 1, "steps": nsteps, "warmup": 3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "paper_shock_table_chi_ret_fm", "length": L, "dt": dt, "denseness": El,
