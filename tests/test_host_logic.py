@@ -267,3 +267,33 @@ def test_malformed_restart_files_are_rejected_before_the_gpu(qlbm_lib, tmp_path,
         with pytest.raises(q.QLError) as e:
             call()
         assert e.value.status == q.QL_EINVAL, case
+
+
+def test_learned_closure_host_logic():
+    """Training-pair parameters are seeded and alternate sound waves (Q = 16, periodic) and shocks (Q = 32) in
+    the stated ranges; the normalisation statistics and the per-field error norms match numpy."""
+    import torch
+    from paper_2211_16933_gb300 import inputs, learned as L
+    a, b = L.pair_specs(40, 7), L.pair_specs(40, 7)
+    assert a == b and a != L.pair_specs(40, 8)
+    for j, s in enumerate(a):
+        assert 0.02 <= s["denseness"] <= 0.3
+        if j % 2 == 0:
+            assert s["kind"] == "sound" and s["Q"] == 16 and 5e-3 <= s["prm"][2] <= 5e-2
+        else:
+            assert s["kind"] == "shock" and s["Q"] == 32 and 1.2 <= s["prm"][2] <= 3.0
+            assert s["prm"][1] == inputs.SHOCK_T_UPSTREAM
+    # pair j depends on seed0 + j only
+    assert L.pair_specs(5, 7)[2] == a[2] and L.pair_specs(1, 9)[0] == a[2]
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.normal(2.0, 3.0, (6, 10, 7)), dtype=torch.float64)
+    y = torch.tensor(rng.normal(0.0, 0.5, (6, 10, 5)), dtype=torch.float64)
+    xm, xs, ys = L.norm_stats(x, y)
+    xn, yn = x.numpy().reshape(-1, 7), y.numpy().reshape(-1, 5)
+    np.testing.assert_allclose(xm, xn.mean(0), rtol=1e-12)
+    np.testing.assert_allclose(xs, xn.std(0, ddof=1), rtol=1e-12)
+    np.testing.assert_allclose(ys, yn.std(0, ddof=1), rtol=1e-12)
+    e = L.field_errors(y, torch.zeros_like(y))
+    for i, f in enumerate(L.FIELDS):
+        assert e[f]["linf"] == float(np.abs(yn[:, i]).max())
+        assert abs(e[f]["l2"] - float(np.sqrt((yn[:, i] ** 2).mean()))) <= 1e-15
