@@ -57,8 +57,8 @@ def run(specs, t_end, samples, precision=q.QL_FP64):
 
 
 def model(t, d0, gamma, k, cs, aa, at):
-    """Eq. (sw_solution) for a perturbation started with no pressure perturbation:
-    d0 [(1 - 1/gamma) exp(-alpha_t t) + (1/gamma) exp(-alpha_a t) cos(k c_s t)]."""
+    """Eq. (sw_solution), the density mode of an isothermal start (delta T = 0, u = 0: the initial state whose
+    acoustic share is 1/gamma): d0 [(1 - 1/gamma) exp(-alpha_t t) + (1/gamma) exp(-alpha_a t) cos(k c_s t)]."""
     return d0 * ((1.0 - 1.0 / gamma) * np.exp(-at * t) + np.exp(-aa * t) * np.cos(k * cs * t) / gamma)
 
 

@@ -297,3 +297,18 @@ def test_learned_closure_host_logic():
     for i, f in enumerate(L.FIELDS):
         assert e[f]["linf"] == float(np.abs(yn[:, i]).max())
         assert abs(e[f]["l2"] - float(np.sqrt((yn[:, i] ** 2).mean()))) <= 1e-15
+
+
+def test_dispersion_fit_recovers_known_modes():
+    """The Levenberg-Marquardt fit of Eq. (sw_solution) returns the c_s, alpha_a, alpha_t of a synthetic
+    density-mode signal from a guess 10-30 % off; the model starts at d0 (the two shares sum to one)."""
+    pytest.importorskip("scipy")
+    from paper_2211_16933_gb300 import dispersion as D
+    t = np.linspace(0.0, 5.0, 501)
+    gamma, k = 1.9, 2.0 * np.pi
+    true = (1.43, 0.061, 0.17)
+    y = D.model(t, 1e-3, gamma, k, *true)
+    assert y[0] == 1e-3
+    est, rms = D.fit(t, y, gamma, k, (1.3, 0.08, 0.13))
+    np.testing.assert_allclose(est, true, rtol=1e-8)
+    assert rms < 1e-10
