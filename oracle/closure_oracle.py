@@ -2,10 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY: used by tests/ to check the GPU training kernels.  It
 restates the network from its definition with numpy in double precision: 1D
-convolutions of kernel 5 (tap j reads position x + j - 2, periodic or zero
-padding), ReLU between layers, mean squared error, and the gradients of that
-loss written out by the chain rule.  Its gradient is pinned by central finite
-differences (tests/test_closure_oracle.py); parity unpinned beyond that.
+convolutions of kernel 5 (tap j reads position x + j - 2; beyond the ends,
+periodic images or the end values repeated), ReLU between layers and none on
+the output, mean squared error, and the gradients of that loss written out by
+the chain rule.  Pinned (tests/test_closure_oracle.py): each tap against a
+shift by hand under both paddings, the layer structure and the loss against an
+identity network whose output is -ReLU of its input, and the gradient against
+central finite differences of the loss.
 
 Parameter vector layout (as ql_closure_params): for each layer W[cout][5][cin]
 then bias[cout], channel counts padded to 16 (padding zero).

@@ -54,3 +54,28 @@ def test_gradient_matches_finite_differences():
     # padded channels carry no gradient
     W0 = C.unpack(g, shapes)[0][0]
     assert np.all(W0[:, :, 7:] == 0)
+
+
+def test_identity_network_pins_the_layer_structure_and_the_loss():
+    """Centre taps set to the identity (the output layer to minus the identity), zero biases: the hidden ReLUs
+    clear the negative inputs and the output layer has none, so the network gives -ReLU(x) on the real
+    channels; with y = 0 the loss is the mean of ReLU(x)^2 over samples, positions and output channels."""
+    shapes = C.layer_shapes(7, 5)
+    n = sum(co * 5 * ci + co for ci, co in shapes)
+    params = np.zeros(n)
+    layers = C.unpack(params, shapes)
+    for l, (W, b) in enumerate(layers):
+        cout, cin = W.shape[0], W.shape[2]
+        m = min(cout, cin)
+        W[:m, 2, :m] = -np.eye(m) if l == len(layers) - 1 else np.eye(m)
+    rng = np.random.default_rng(5)
+    B, X = 3, 12
+    xs = np.zeros((B, X, 16))
+    xs[:, :, :7] = rng.normal(0, 1, (B, X, 7))
+    for s in range(B):
+        zs, acts = C.forward(params, shapes, xs[s], periodic=bool(s % 2))
+        np.testing.assert_array_equal(zs[-1][:, :5], -np.maximum(xs[s, :, :5], 0.0))
+        np.testing.assert_array_equal(acts[-1], zs[-1])
+        assert (zs[-1][:, :5] < 0).any()
+    loss, _ = C.loss_and_grad(params, shapes, xs, np.zeros((B, X, 5)), np.arange(B) % 2, 5)
+    assert abs(loss - float(np.mean(np.maximum(xs[:, :, :5], 0.0) ** 2))) <= 1e-15
