@@ -466,7 +466,8 @@ static void record_step_graph(ql_ctx *c)
 ql_status ql_step(ql_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
-    // small domains are launch-bound: several steps replay one recorded step
+    // several steps replay one recorded step: one graph launch per step instead
+    // of three to six kernel launches, which matters where launches are slow
     if (nsteps > 1 && !c->step_graph && !c->step_graph_failed) record_step_graph(c);
     const bool replay = nsteps > 1 && c->step_graph;
     for (int64_t s = 0; s < nsteps; ++s) {
