@@ -71,3 +71,47 @@ def test_planted_mistake_is_caught(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+RIEMANN = os.path.join(ROOT, "oracle", "riemann.py")
+RIEMANN_MUTATIONS = {
+    "chi_sign": ("return 0.5 * (2.0 - eta) / (1.0 - eta) ** 3", "return 0.5 * (2.0 + eta) / (1.0 - eta) ** 3"),
+    "eos_coeff": ("return 1.0 + 4.0 * eta * chi_set(eta)", "return 1.0 + 3.0 * eta * chi_set(eta)"),
+    "rarefaction_velocity_sign": ("return c2, -math.sqrt(c2) / r", "return c2, math.sqrt(c2) / r"),
+    "hugoniot_energy_factor": ("return 1.5 * (gas.temperature(r2, Pc) - TR)", "return 2.5 * (gas.temperature(r2, Pc) - TR)"),
+    "shock_speed": ("xi_s = math.sqrt((Pc - PR) / (rhoR * (1.0 - rhoR / rho2)))", "xi_s = math.sqrt((Pc - PR) / (rhoR * (1.0 + rhoR / rho2)))"),
+}
+
+
+def _run_riemann_pins(tmp_path, old=None, new=None):
+    """Runs tests/test_riemann_oracle.py against a copy of oracle/ (riemann.py optionally mutated)."""
+    import shutil
+    src = open(RIEMANN).read()
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so"))
+    if old is not None:
+        (tmp_path / "oracle" / "riemann.py").write_text(src.replace(old, new))
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests", ignore=shutil.ignore_patterns("__pycache__"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path)
+    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           "tests/test_riemann_oracle.py"], cwd=tmp_path, env=env, capture_output=True, text=True,
+                          timeout=600)
+
+
+@pytest.mark.slow
+def test_riemann_unmutated_copy_passes(tmp_path):
+    """Control: the copied, unmutated oracle passes, so a failure below is the planted mistake's."""
+    r = _run_riemann_pins(tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(RIEMANN_MUTATIONS))
+def test_riemann_planted_mistake_is_caught(name, tmp_path):
+    """The same for the exact dense-gas Riemann solution: a mutated copy of oracle/riemann.py, imported in
+    place of the original, fails tests/test_riemann_oracle.py."""
+    old, new = RIEMANN_MUTATIONS[name]
+    assert open(RIEMANN).read().count(old) == 1, f"mutation anchor not unique/found: {name}"
+    r = _run_riemann_pins(tmp_path, old, new)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
