@@ -57,6 +57,19 @@ MUTATIONS = {
 
 
 @pytest.mark.slow
+def test_unmutated_oracle_copy_passes(tmp_path):
+    """Control: the oracle rebuilt the same way, unmutated, passes its pins, so a failure below is the
+    planted mistake's and not the build's."""
+    so = tmp_path / "liboracle_copy.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), SRC, "-lm"])
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=dict(os.environ, ORACLE_LIB=str(so)), capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.slow
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(name, tmp_path):
     old, new = MUTATIONS[name]
