@@ -128,3 +128,49 @@ def test_riemann_planted_mistake_is_caught(name, tmp_path):
     assert open(RIEMANN).read().count(old) == 1, f"mutation anchor not unique/found: {name}"
     r = _run_riemann_pins(tmp_path, old, new)
     assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+CLOSURE = os.path.join(ROOT, "oracle", "closure_oracle.py")
+CLOSURE_MUTATIONS = {
+    "zero_padding": ("return a[np.clip(idx, 0, X - 1)]", "return np.where(((idx >= 0) & (idx < X))[:, None], a[np.clip(idx, 0, X - 1)], 0.0)"),
+    "tap_offset": ("z += w[j:j + X] @ W[:, j, :].T", "z += w[TAPS - 1 - j:TAPS - 1 - j + X] @ W[:, j, :].T"),
+    "relu_on_output": ("a = np.maximum(z, 0.0) if l < len(layers) - 1 else z", "a = np.maximum(z, 0.0)"),
+    "loss_gradient_scale": ("dz = 2.0 * d / nel", "dz = d / nel"),
+    "periodic_fold": ("da[X - 2:] += dw[0:2]", "da[:2] += dw[0:2]"),
+    "replicate_fold": ("da[0] += dw[0] + dw[1]", "da[0] += dw[0]"),
+    "relu_gradient_mask": ("dz = da * (zs[l - 1] > 0.0)", "dz = da"),
+}
+
+
+def _run_closure_pins(tmp_path, old=None, new=None):
+    """Runs tests/test_closure_oracle.py against a copy of oracle/ (closure_oracle.py optionally mutated)."""
+    import shutil
+    src = open(CLOSURE).read()
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so"))
+    if old is not None:
+        (tmp_path / "oracle" / "closure_oracle.py").write_text(src.replace(old, new))
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests", ignore=shutil.ignore_patterns("__pycache__"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path)
+    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           "tests/test_closure_oracle.py"], cwd=tmp_path, env=env, capture_output=True, text=True,
+                          timeout=600)
+
+
+@pytest.mark.slow
+def test_closure_unmutated_copy_passes(tmp_path):
+    """Control for the closure network oracle's planted mistakes."""
+    r = _run_closure_pins(tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(CLOSURE_MUTATIONS))
+def test_closure_planted_mistake_is_caught(name, tmp_path):
+    """A mutated copy of oracle/closure_oracle.py (padding, tap order, output ReLU, loss scale, the fold of
+    the window gradient at the ends, the ReLU mask) fails tests/test_closure_oracle.py."""
+    old, new = CLOSURE_MUTATIONS[name]
+    assert open(CLOSURE).read().count(old) == 1, f"mutation anchor not unique/found: {name}"
+    r = _run_closure_pins(tmp_path, old, new)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
