@@ -312,3 +312,24 @@ def test_dispersion_fit_recovers_known_modes():
     est, rms = D.fit(t, y, gamma, k, (1.3, 0.08, 0.13))
     np.testing.assert_allclose(est, true, rtol=1e-8)
     assert rms < 1e-10
+
+
+def test_bench_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the oracle on the host and prints one JSON line with the keys of the
+    bench contract (the metric and unit of the GPU arm, a cpu_baseline, an e2e with no copies)."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "cell-velocity updates/s" and d["unit"] == "updates/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 1, 0)
+    assert d["config"]["workload"] == "sod_nx4194304_Q32"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
