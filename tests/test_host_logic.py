@@ -333,3 +333,30 @@ def test_bench_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_and_product_share_no_code():
+    """Independence: no product module imports the oracle, the oracle imports nothing of the product (its C
+    source includes no product header), and the shared input generators import neither."""
+    import ast
+
+    def imports(path):
+        tree = ast.parse(open(path).read())
+        out = set()
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                out |= {a.name.split(".")[0] for a in node.names}
+            elif isinstance(node, ast.ImportFrom):
+                out.add((node.module or "").split(".")[0] if node.level == 0 else "." + (node.module or ""))
+        return out
+
+    pkg = os.path.join(ROOT, "paper_2211_16933_gb300")
+    for f in glob.glob(os.path.join(pkg, "*.py")):
+        assert "oracle" not in imports(f), f
+    for f in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        assert not ({"paper_2211_16933_gb300", "bench"} & imports(f)), f
+    assert imports(os.path.join(pkg, "inputs.py")) <= {"__future__", "numpy", "math"}
+    csrc = open(os.path.join(ROOT, "oracle", "fdlb_oracle.c")).read()
+    assert "qlbm" not in csrc and "csrc" not in csrc
+    for f in glob.glob(os.path.join(pkg, "csrc", "*")):
+        assert "oracle" not in open(f).read().lower() or f.endswith(".md"), f
