@@ -233,7 +233,7 @@ def _oracle_sample(w, steps, warmup):
     return ups, el, sample, window
 
 
-def _errors_vs_oracle(window, precision):
+def _errors_vs_oracle(window, precision, sums=0):
     """L-inf and L2 errors of rho, u, T, P, q of the library's run of the oracle's window problem (same cells,
     ghosts, dx, dt and steps), each normalised by its reference scale: rho_ref, sqrt(T_ref), T_ref,
     rho_ref T_ref (1 + Y0), rho_ref T_ref^(3/2) with rho_ref = T_ref = 1."""
@@ -242,7 +242,8 @@ def _errors_vs_oracle(window, precision):
     r, u, T = window["fields"]
     s = q.Solver(window["Q"], window["nx"], window["length"], window["dt"], window["denseness"], window["kn"],
                  bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_FIELDS, rho=r, u=u, T=T,
-                 ghost=np.asarray(window["ghost"], dtype=float).ravel(), precision=precision, pr_mode=q.QL_PR_DENSE)
+                 ghost=np.asarray(window["ghost"], dtype=float).ravel(), precision=precision, pr_mode=q.QL_PR_DENSE,
+                 sums=sums)
     s.step(window["steps"])
     f_gpu = s.moments()
     s.close()
@@ -271,6 +272,91 @@ def run_reference(args, w):
             "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": ups, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _hbm_roofline(elem, nx, Q, step_s, precision_name):
+    """Stage kernel against the measured copy bandwidth: 16 words of phi and theta per update per step
+    (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2), per launch = a third of the step."""
+    bytes_per_step = 16 * elem * nx * Q
+    achieved = bytes_per_step / 3 / (step_s / 3) / 1e9
+    peaks = _peaks()
+    if peaks and "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic(precision_name, Q, nx), "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": bytes_per_step / 3, "launches_per_step": 3, "kernel": "fdlb_stage_kernel"}
+
+
+def _timed_steps(s, steps, warmup, stream):
+    """Per-step times (ms) of `steps` single steps after `warmup`, CUDA events on the solver's stream."""
+    import torch
+    for _ in range(warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        s.step(1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+
+
+def _forms(args, w, window, q, inputs, dev, stream):
+    """The other forms of the precision study and the batched form, each timed on the same GPU (sub-records
+    of the bench line): FP32 with FP64 per-cell conserved sums, FP64, and the 4096-instance batch."""
+    import torch
+    Q, nx = w["Q"], w["nx"]
+    pmax = float(np.abs(q.ql_velocity_set(Q)[0]).max())
+    dt = inputs.cfl_dt(w["length"] / nx, pmax)
+    out = {}
+    for name, prec, sums, steps in (("fp32_sums_fp64", q.QL_FP32, q.QL_SUMS_FP64, args.steps),
+                                    ("fp64", q.QL_FP64, q.QL_SUMS_DFP32, min(args.steps, args.fp64_steps))):
+        s = q.Solver(Q, nx, w["length"], dt, w["denseness"], w["kn"], bc=q.QL_BC_FIXED,
+                     init_kind=q.QL_INIT_RIEMANN, prm=w["prm"], precision=prec, pr_mode=q.QL_PR_DENSE, device=dev,
+                     sums=sums)
+        ms = _timed_steps(s, steps, min(args.warmup, 3), stream)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        step_s = sum(ms) * 1e-3 / steps
+        elem = 4 if prec == q.QL_FP32 else 8
+        pname = "fp32" if prec == q.QL_FP32 else "fp64"
+        rec = {"value": nx * Q / step_s, "unit": "updates/s", "steps": steps, "ms_per_step": step_s * 1e3,
+               "dtype": "f32" if prec == q.QL_FP32 else "f64",
+               "sums": "f64 per-cell conserved sums" if sums == q.QL_SUMS_FP64 or prec == q.QL_FP64 else "double-f32",
+               "roofline_hbm": _hbm_roofline(elem, nx, Q, step_s, pname),
+               "roofline_alu": _alu_roofline(pname, nx * Q / step_s, Q)}
+        if window is not None:
+            rec["errors_vs_oracle"] = _errors_vs_oracle(window, prec, sums)
+        out[name] = rec
+    if args.batch_n > 0:
+        insts, keep, spec = _batch_instances(q, inputs, args.batch_n, 20221130)
+        for name, sums in (("batch_fp32", q.QL_SUMS_DFP32), ("batch_fp32_sums_fp64", q.QL_SUMS_FP64)):
+            b = q.Batch(insts, precision=q.QL_FP32, sums=sums)
+            warps, ctas = b.tune(3)
+            upd = b.info()[1]
+            b.run(min(args.warmup, 3))
+            b.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ks = min(args.steps, 20)
+            e0.record(b._stream)
+            b.run(ks)
+            e1.record(b._stream)
+            e1.synchronize()
+            flags = b.sync()
+            bms = e0.elapsed_time(e1)
+            b.close()
+            out[name] = {"value": upd * ks / (bms * 1e-3), "unit": "updates/s", "steps": ks, "ms_per_step": bms / ks,
+                         "instances": args.batch_n, "updates_per_step": upd, "tuned_warps_per_cta": warps,
+                         "tuned_ctas_per_sm": ctas, "nonphysical_instances": int((flags & 1).sum()),
+                         "sums": "f64 per-cell conserved sums" if sums == q.QL_SUMS_FP64 else "double-f32",
+                         "graph": "one CUDA graph launch of 3 x steps persistent stage kernels per velocity set"}
+        del keep
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, w):
@@ -322,19 +408,7 @@ def run_ours(args, w):
     value = whole_job_rate(nx * Q * args.steps, ws, max_ms * 1e-3)
 
     # roofline of the stage kernel: algorithmic bytes = 16 words per update per step
-    # (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2, words of phi and theta)
-    bytes_per_step = 16 * elem * nx * Q
-    launch_s = (total_ms * 1e-3) / (3 * args.steps)
-    achieved = bytes_per_step / 3 / launch_s / 1e9
-    peaks = _peaks()
-    if peaks and "hbm_gbs" in peaks:
-        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
-    else:
-        peak, peak_src = 6800.0, "fallback"
-    hbm_roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": _traffic(args.precision, Q, nx), "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": bytes_per_step / 3, "launches_per_step": 3,
-                    "kernel": "fdlb_stage_kernel"}
+    hbm_roofline = _hbm_roofline(elem, nx, Q, total_ms * 1e-3 / args.steps, args.precision)
     # the per-launch update rate is the step's (three launches of the same cells)
     alu_roofline = _alu_roofline(args.precision, nx * Q * args.steps / (total_ms * 1e-3), Q)
     # FP32: the metric's HBM roofline, the FP32-pipe view beside it; FP64: bound by GB300's FP64 rate
@@ -371,10 +445,16 @@ def run_ours(args, w):
 
     cpu = None
     errors = None
+    window = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ups, el, sample, window = _oracle_sample(w, args.cpu_steps, 0)
         cpu = {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
         errors = _errors_vs_oracle(window, prec)
+    forms = None
+    if rank == 0 and ws == 1 and not args.no_forms and prec == q.QL_FP32:
+        s.close()
+        torch.cuda.empty_cache()
+        forms = _forms(args, w, window, q, inputs, dev, stream)
 
     s.close()
     if rank == 0:
@@ -389,7 +469,7 @@ def run_ours(args, w):
                            "l2": "inputs larger than L2 (3 state buffers of %.2f GiB)" % (
                                2 * Q * nx * elem / 2 ** 30)},
                 "roofline": roofline, "roofline_other": other_roofline, "cpu_baseline": cpu,
-                "errors_vs_oracle": errors, "e2e": e2e,
+                "errors_vs_oracle": errors, "e2e": e2e, "forms": forms,
                 "gpu_launches": 3 * args.steps,
                 "clocks": clocks, "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
         print(json.dumps(line), flush=True)
@@ -589,7 +669,7 @@ def run_learned(args):
 
 
 def run_dispersion(args):
-    """Sound-wave dispersion study (Sec. III.A): a batch of sound waves over a sweep of E_l, the density-mode
+    """Sound-wave dispersion study (Sec. IV.A): a batch of sound waves over a sweep of E_l, the density-mode
     amplitude sampled in time, a Levenberg-Marquardt fit of c_s, alpha_a, alpha_t against linear theory."""
     import torch
     from paper_2211_16933_gb300 import build as B
@@ -700,6 +780,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32-with-FP64-sums, FP64 and batch sub-records")
+    ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table"], default="sod")
     ap.add_argument("--table-steps", type=int, default=9000)
     ap.add_argument("--sweep", type=int, default=16)

@@ -50,6 +50,7 @@ typedef enum {
 } ql_status;
 
 enum { QL_FP64 = 0, QL_FP32 = 1 };              /* arithmetic of the state and its update */
+enum { QL_SUMS_DFP32 = 0, QL_SUMS_FP64 = 1 };   /* FP32 mode: per-cell conserved sums */
 enum { QL_BC_PERIODIC = 0, QL_BC_FIXED = 1 };   /* boundary of the 1D domain */
 enum { QL_INIT_SOUND = 0, QL_INIT_RIEMANN = 1, QL_INIT_SHOCK = 2, QL_INIT_FIELDS = 3 };
 enum { QL_PR_CONST = 0, QL_PR_DENSE = 1 };
@@ -119,9 +120,15 @@ typedef void (*ql_free_fn)(void *ptr, void *user);
 
 /* Options.
  *   precision  QL_FP64: state, update and sums in FP64.
- *              QL_FP32: state and update in FP32; per-cell conserved-moment
- *              sums combined, and u and T derived, in double-FP32 (about 48
- *              significant bits); the domain totals in FP64.
+ *              QL_FP32: state and update in FP32; the per-cell
+ *              conserved-moment sums (mass, momentum, energy) as `sums` says;
+ *              the domain totals in FP64.
+ *   sums       FP32 only.  QL_SUMS_DFP32 (0, default): the per-cell conserved
+ *              sums are combined, and u and T derived, in double-FP32 (about
+ *              48 significant bits).  QL_SUMS_FP64: in FP64, as are the
+ *              per-cell sums behind the domain totals of ql_totals and
+ *              ql_moments.  FP32 products are summed over groups of 8 velocity
+ *              pairs in FP32 first in either mode.
  *   pr_mode    QL_PR_CONST uses pr_const; QL_PR_DENSE the Prandtl number of
  *              the dense gas as a function of b rho chi (Sec. II.B).
  *   enskog     1 adds the simplified-Enskog term J1 of Eq. (j1_expanded);
@@ -151,6 +158,8 @@ typedef struct {
     int32_t device;
     int32_t chi_mode;
     int32_t fault;
+    int32_t sums;
+    int32_t pad_;
     double pr_const;
     double rho_ref;
     void *stream;
@@ -249,16 +258,23 @@ typedef struct {
 
 /* Creates a batch of n >= 1 instances (host array inst; the initial-field
  * arrays it points to are read before return).  Instances use chi_SET.  From
- * opts only precision, device, stream and the allocator hooks are used; with stream NULL the batch
+ * opts only precision, sums, device, stream and the allocator hooks are used; with stream NULL the batch
  * creates its own stream (a CUDA graph cannot be captured on the legacy
  * default stream).  Errors as for ql_create, naming the first bad instance. */
 ql_status ql_batch_create(const ql_instance *inst, int64_t n, const ql_opts *opts, ql_batch **out);
 
-/* Picks the CTA shape (warps per CTA, 8 or 4) and the number of persistent
- * CTAs per SM by timing trial_launches >= 1 launches of the first stage for
- * each candidate (the first stage leaves the state unchanged).  Outputs may be
- * NULL.  Synchronises. */
+/* Picks the CTA shape (warps per CTA, 8 or 4) and the grid by timing
+ * trial_launches >= 1 launches of the first stage for each candidate (the
+ * first stage leaves the state unchanged): one CTA per work item, which the
+ * batch starts with (*ctas_per_sm = 0), or a persistent grid of ctas_per_sm
+ * CTAs per SM walking the work list.  Every choice gives the same results.
+ * Outputs may be NULL.  Synchronises. */
 ql_status ql_batch_tune(ql_batch *b, int32_t trial_launches, int32_t *warps, int32_t *ctas_per_sm);
+
+/* Sets the CTA shape and grid that ql_batch_tune would pick: warps per CTA (8
+ * or 4) and ctas_per_sm (0: one CTA per work item; else a persistent grid of
+ * that many CTAs per SM, at most what an SM holds).  QL_EINVAL otherwise. */
+ql_status ql_batch_set_shape(ql_batch *b, int32_t warps, int32_t ctas_per_sm);
 
 /* Queues nsteps steps of Eq. (rk3) for every instance as one CUDA graph
  * launch (3 nsteps persistent stage kernels; the graph is rebuilt only when
@@ -273,7 +289,7 @@ ql_status ql_batch_sync(ql_batch *b, uint32_t *flags);
 ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, double *T, double *P, double *q,
                            double *Pxx, double *totals);
 
-/* Amplitude of density mode m of every instance (Sec. III.A: the projection
+/* Amplitude of density mode m of every instance (Sec. IV.A: the projection
  * (2/nx) sum_j rho_j cos(2 pi m x_j / L) used to follow a sound wave), written
  * as n doubles to the device array out (caller-owned).  Asynchronous on the
  * batch's stream.  QL_EINVAL for a null batch or out, or m < 0. */
@@ -364,8 +380,8 @@ const char *ql_closure_last_error(const ql_closure *c);
 /* Largest scratch ql_step_noalloc uses, in bytes. */
 #define QL_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)
 
-/* Advances a caller-owned state by nsteps steps of Eq. (rk3), like ql_step,
- * without allocating any device memory.  The paper has no counterpart: this
+/* Advances a caller-owned state by nsteps steps, like ql_step, without
+ * allocating any device memory.  The paper has no counterpart: this
  * entry point exists for callers that must not call cudaMalloc, for example
  * code that runs under a memory budget another framework has already reserved
  * (where an allocation can fail) or inside a latency-critical loop (where
@@ -380,8 +396,8 @@ const char *ql_closure_last_error(const ql_closure *c);
  *               ql_state_device reports for a context of the same nx); rows
  *               start 16-byte aligned, so in FP32 it must be even.
  *   The other arguments are those of ql_create; from opts only precision,
- *   pr_mode, enskog, device, pr_const, rho_ref, stream and chi_mode are used,
- *   and chi_mode must be QL_CHI_SET (QL_EUNSUPPORTED otherwise: chi_RET-FM
+ *   sums, pr_mode, enskog, device, pr_const, rho_ref, stream and chi_mode are
+ *   used, and chi_mode must be QL_CHI_SET (QL_EUNSUPPORTED otherwise: chi_RET-FM
  *   needs per-cell density buffers).
  * The two intermediate stage buffers and the error word live in one fixed
  * scratch array of QL_NOALLOC_MAX_BYTES that every GPU loading this library
@@ -392,7 +408,8 @@ const char *ql_closure_last_error(const ql_closure *c);
  * (other threads, other streams) race and must be serialised by the caller.
  * The first call on a device also uploads the kernel tables and looks up the
  * scratch address on that device; make that first call before any stream
- * capture.  The call returns after the stream has run the steps.  Errors:
+ * capture.  Every call synchronises the stream: it returns after the stream
+ * has run the steps and the error word has been read back.  Errors:
  * QL_EINVAL, QL_EUNSUPPORTED, QL_ECUDA, QL_ENONPHYSICAL; ql_last_error(NULL)
  * describes them. */
 ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double denseness, double kn,
@@ -415,7 +432,7 @@ ql_status ql_eta_of_denseness(double denseness, double *eta0);
 double ql_sound_speed2(double eta0, double rho_ref, double rho, double T);
 
 /* Linear modes of a sound wave of wave number k on the uniform state
- * (rho, T) of a model with these parameters (Sec. III.A, Eqs. sw_cs and
+ * (rho, T) of a model with these parameters (Sec. IV.A, Eqs. sw_cs and
  * sw_coeff), from the transport coefficients the kinetic model carries:
  * mu = tau P_i (Sec. II.B), lambda = (5/2) mu / Pr, the bulk viscosity of Eq.
  * (bulk_viscosity) as a fraction of Eq. (viscosity), c_V = 3/2 and the

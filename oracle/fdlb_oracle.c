@@ -722,7 +722,7 @@ double oq_sound_speed2(double eta0, double rho_ref, double rho, double T)
 }
 
 /* ------------------------------------------------------------------------
- * Sec. III.A (sound waves), Eqs. (sw_cs), (sw_coeff); READING c21: linear
+ * Sec. IV.A (sound waves), Eqs. (sw_cs), (sw_coeff); READING c21: linear
  * modes of a wave of wave number k on the uniform state (rho, T) of the model.
  * The kinetic model carries
  *   mu     = tau rho T                        (tau = mu / P_i, Sec. II.B),

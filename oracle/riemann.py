@@ -1,5 +1,5 @@
 """Inviscid limit of the dense-gas shock tube: the exact Riemann solution of the
-Euler equations with the Carnahan-Starling equation of state (Sec. III.B,
+Euler equations with the Carnahan-Starling equation of state (Sec. IV.B,
 "Inviscid limit", Eqs. euler, euler_xi, sod_sol, rankine_hugoniot).
 
 TEST INFRASTRUCTURE ONLY: used by tests/ as an analytic reference for the
@@ -53,7 +53,7 @@ class DenseGas:
 
     def sound_speed2(self, rho, P):
         """c_s^2(rho, P) = P/rho + 2P(1 + b rho chi)/(3 rho) + b P (chi + rho d_rho chi)/(1 + b rho chi),
-        b rho = 4 eta, d chi / d eta = (5 - 2 eta) / (2 (1 - eta)^4) (Sec. III.B)."""
+        b rho = 4 eta, d chi / d eta = (5 - 2 eta) / (2 (1 - eta)^4) (Sec. IV.B)."""
         eta = self.eta(rho)
         chi = chi_set(eta)
         Y = 4.0 * eta * chi

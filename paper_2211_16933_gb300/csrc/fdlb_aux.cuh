@@ -113,7 +113,9 @@ __global__ void __launch_bounds__(kFmThreads) fdlb_fm_kernel(FmArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Output fields (FP64) and per-block totals of mass, momentum and energy.
+// Output fields (FP64) and per-block totals of mass, momentum and energy.  The
+// per-cell sums over velocities are FP64 in FP64 mode and in FP32 mode with
+// a.sums64, else double-FP32 sums of exact products.
 template <typename Real, int Q>
 __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a, const double *__restrict__ tab)
 {
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kMomThreads) fdlb_moments_kernel(MomentArgs a,
     }
     if (i < a.nx) {
         double S0 = 0, S1 = 0, S2 = 0, S3 = 0, R0 = 0, R1 = 0;
-        if constexpr (sizeof(Real) == 4) {
+        if (sizeof(Real) == 4 && !a.sums64) {
             // sums of exact products p^j phi (two_sum / fma error terms) in
             // double-FP32, converted to FP64 once per cell: FP64 runs at a small
             // fraction of the FP32 rate on this GPU

@@ -1,7 +1,8 @@
 // FP64 kernels: everything in FP64.
 #include "qlbm_internal.h"
 namespace qlbm {
-static __constant__ double QL_TAB[kTabTotal];
+// 16-byte aligned: the stage kernels read the table rows as pairs.
+static __constant__ __align__(16) double QL_TAB[kTabTotal];
 }
 #define QL_REAL double
 #define QL_SUFFIX f64

@@ -18,22 +18,38 @@ cudaError_t QL_FN(upload_tables_)(const double *all)
     return cudaMemcpyToSymbol(QL_TAB, host, sizeof(host));
 }
 
+// One CTA per tile; in FP64, a domain of fewer tiles than the GPU holds CTAs
+// splits each tile's velocity pairs over up to Q/2 CTAs (FP64 arithmetic, not
+// memory, bounds those small domains).  With chi_RET-FM the densities of the
+// output then come from a separate pass, in the order the stage sums them.
 template <int Q, int STAGE, bool RET>
 static cudaError_t stage_q(const StageArgs &a, cudaStream_t s)
 {
     constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, kWarps, RET>();
     auto kern = fdlb_stage_kernel<QL_REAL, Q, STAGE, RET>;
-    static bool configured[64] = {};
+    static int resident[64] = {};  // CTAs of this kernel the device holds at once
     int dev = 0;
     cudaGetDevice(&dev);
-    if (!configured[dev & 63]) {
+    if (!resident[dev & 63]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        int per_sm = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        configured[dev & 63] = true;
+        resident[dev & 63] = per_sm * sms > 0 ? per_sm * sms : 1;
     }
     const int64_t nt = num_tiles(a.nx);
-    kern<<<dim3(unsigned(nt)), dim3(kThreads), smem, s>>>(a);
-    return cudaGetLastError();
+    StageArgs b = a;
+    b.vsplit = 1;
+    if (sizeof(QL_REAL) == 8 && nt < resident[dev & 63]) {
+        const int64_t v = resident[dev & 63] / nt;
+        b.vsplit = int(v < Q / 2 ? v : Q / 2);
+    }
+    kern<<<dim3(unsigned(nt * b.vsplit)), dim3(kThreads), smem, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && RET && STAGE != 0 && b.vsplit > 1)
+        e = QL_FN(launch_density_)(Q, b.out, b.nx, b.stride, b.nout, s);
+    return e;
 }
 
 template <int Q, bool RET>
@@ -186,7 +202,7 @@ cudaError_t QL_FN(launch_moments_)(int Q, const MomentArgs &a, const double *tab
 {
     const unsigned blocks = unsigned(moment_blocks(a.nx));
     if constexpr (sizeof(QL_REAL) == 4) {
-        if (!(a.rho || a.u || a.T || a.P || a.q || a.Pxx)) {  // totals only
+        if (!a.sums64 && !(a.rho || a.u || a.T || a.P || a.q || a.Pxx)) {  // totals only, double-FP32 sums
             switch (Q) {
             case 8: fdlb_totals_f32_kernel<8><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;
             case 16: fdlb_totals_f32_kernel<16><<<blocks, kMomThreads, 0, s>>>(a, tab64); break;

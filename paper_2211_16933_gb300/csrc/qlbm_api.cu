@@ -21,6 +21,7 @@ using namespace qlbm;
 
 struct ql_ctx {
     int Q = 0, precision = 0, pr_mode = 0, enskog = 1, periodic = 1, device = 0, fault = 0;
+    int sums64 = 0;  // FP32: per-cell conserved sums in FP64 (QL_SUMS_FP64) instead of double-FP32
     int64_t nx = 0, stride = 0;
     double L = 0, dx = 0, dt = 0, El = 0, kn = 0, pr_const = 2.0 / 3.0, rho_ref = 1.0;
     double eta0 = 0, chi0 = 1, sigma = 0, tau_pref = 0;
@@ -64,6 +65,39 @@ static bool g_tab_built = false;
 
 namespace qlbm {
 void set_global_error(const std::string &msg) { g_create_error = msg; }
+
+// The kernel tables of every compiled velocity set: built on the host once per
+// process, uploaded once per device (the current one must be `device`).  All
+// entry points that launch tiled kernels share this one flag per device.
+static bool host_tables_locked(std::string &err)
+{
+    if (!g_tab_built) {
+        if (!build_tables(g_tab)) {
+            err = "velocity-set construction failed";
+            return false;
+        }
+        g_tab_built = true;
+    }
+    return true;
+}
+
+bool ensure_device_tables(int device, std::string &err)
+{
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (!host_tables_locked(err)) return false;
+    if (!g_tables_ready[device & 63]) {
+        cudaError_t e = upload_tables_f32(g_tab);
+        if (e == cudaSuccess) e = upload_tables_f64(g_tab);
+        if (e != cudaSuccess) {
+            err = std::string("table upload: ") + cudaGetErrorString(e);
+            return false;
+        }
+        g_tables_ready[device & 63] = true;
+    }
+    return true;
+}
+
+const double *host_tables() { return g_tab; }
 }  // namespace qlbm
 
 static ql_status fail(ql_ctx *c, ql_status st, const std::string &msg)
@@ -148,6 +182,8 @@ static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, voi
     a.enskog = c->enskog;
     a.periodic = c->periodic;
     a.fault = c->fault;
+    a.sums64 = c->sums64;
+    a.vsplit = 1;  // the launcher picks the FP64 split
     a.err = c->d_err;
     const bool ret = c->chi_mode == QL_CHI_RET_FM;
     a.nbar = ret ? c->d_nbar : nullptr;
@@ -266,10 +302,12 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     if (opts->pr_mode == QL_PR_CONST && !(opts->pr_const > 0)) return fail(nullptr, QL_EINVAL, "pr_const must be > 0");
     if (opts->chi_mode != QL_CHI_SET && opts->chi_mode != QL_CHI_RET_FM) return fail(nullptr, QL_EINVAL, "bad chi_mode");
     if (opts->fault != 0 && opts->fault != 1) return fail(nullptr, QL_EINVAL, "bad fault (0 or 1)");
+    if (opts->sums != QL_SUMS_DFP32 && opts->sums != QL_SUMS_FP64) return fail(nullptr, QL_EINVAL, "bad sums");
 
     ql_ctx *c = new ql_ctx();
     c->chi_mode = opts->chi_mode;
     c->fault = opts->fault;
+    c->sums64 = opts->precision == QL_FP32 && opts->sums == QL_SUMS_FP64;
     c->lq = lq;
     c->Q = vs->Q;
     c->precision = opts->precision;
@@ -308,13 +346,11 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
             return bail(QL_EUNSUPPORTED, "the chi_RET-FM ball reaches " + std::to_string(c->fm_w) +
                                              " cells on each side; at most QL_FM_MAX_HALFWIDTH are supported");
     }
-    c->tau_pref = 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * kn * grid->length * c->chi0;
+    c->tau_pref = tau_prefactor(kn, grid->length, c->eta0);
     {
         std::lock_guard<std::mutex> lk(g_mutex);
-        if (!g_tab_built) {
-            if (!build_tables(g_tab)) return bail(QL_EINVAL, "velocity-set construction failed");
-            g_tab_built = true;
-        }
+        std::string terr;
+        if (!host_tables_locked(terr)) return bail(QL_EINVAL, terr);
     }
     c->p.assign(c->Q, 0.0);
     c->w.assign(c->Q, 0.0);
@@ -345,13 +381,8 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return bail(QL_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     {
-        std::lock_guard<std::mutex> lk(g_mutex);
-        if (!g_tables_ready[c->device & 63]) {
-            e = upload_tables_f32(g_tab);
-            if (e == cudaSuccess) e = upload_tables_f64(g_tab);
-            if (e != cudaSuccess) return bail(QL_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
-            g_tables_ready[c->device & 63] = true;
-        }
+        std::string terr;
+        if (!ensure_device_tables(c->device, terr)) return bail(QL_ECUDA, terr);
     }
     const size_t state_bytes = size_t(c->Q) * size_t(c->stride) * c->elem;
     for (int b = 0; b < 3; ++b) {
@@ -502,6 +533,7 @@ static ql_status run_moments(ql_ctx *c, bool fields)
     a.Pxx = fields ? f + 5 * c->nx : nullptr;
     a.partial = c->d_partial;
     a.err = c->d_err;
+    a.sums64 = c->sums64;
     cudaError_t e = c->lq                      ? launch_lq_moments(c->Q, a, c->d_lqtab, c->stream)
                     : c->precision == QL_FP32 ? launch_moments_f32(c->Q, a, c->d_tab64, c->stream)
                                               : launch_moments_f64(c->Q, a, c->d_tab64, c->stream);

@@ -18,6 +18,7 @@ using namespace qlbm;
 
 struct ql_batch {
     int precision = QL_FP32, device = 0;
+    int sums64 = 0;  // FP32: per-cell conserved sums in FP64 (QL_SUMS_FP64)
     int64_t n = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -92,21 +93,24 @@ static void batch_release(ql_batch *b)
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
-// One Runge-Kutta stage of every instance: a launch per velocity set present.
+// One Runge-Kutta stage of every instance: a launch per velocity set present,
+// of `grid` CTAs walking the set's work items, or (grid 0) one CTA per item.
 static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
 {
     const int wi = warps == kBatchWarps[0] ? 0 : 1;
     for (int g = 0; g < kNumBatchQ; ++g) {
         if (b->qcount[wi][g] == 0) continue;
+        const int gq = grid > 0 ? grid : int(std::min<int64_t>(b->qcount[wi][g], INT32_MAX));
         BatchArgs a;
         a.inst = b->d_inst;
         a.work = b->d_work[wi] + b->qstart[wi][g];
         a.nwork = b->qcount[wi][g];
         for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
         a.err = b->d_err;
+        a.sums64 = b->sums64;
         const cudaError_t e = b->precision == QL_FP32
-                                  ? launch_batch_stage_f32(kBatchQList[g], stage, warps, grid, a, b->stream)
-                                  : launch_batch_stage_f64(kBatchQList[g], stage, warps, grid, a, b->stream);
+                                  ? launch_batch_stage_f32(kBatchQList[g], stage, warps, gq, a, b->stream)
+                                  : launch_batch_stage_f64(kBatchQList[g], stage, warps, gq, a, b->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -158,7 +162,7 @@ __global__ void batch_fields_kernel(const BatchInstance *__restrict__ inst, cons
     for (int q = 0; q < 5; ++q) out[(int64_t(i) * 5 + q) * ncoarse + c] = acc[q] / double(f);
 }
 
-// Sec. III.A: amplitude of density mode m of every instance,
+// Sec. IV.A: amplitude of density mode m of every instance,
 //   out[i] = (2 / nx) sum_j rho_j cos(2 pi m x_j / L),  x_j = (j + 1/2) L / nx,
 // with rho_j = sum_k phi_k.  One block per instance, FP64 sums, fixed-order
 // tree reduction.
@@ -206,8 +210,10 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
     if (out) *out = nullptr;
     if (!in || n <= 0 || !opts || !out) return bfail(nullptr, QL_EINVAL, "bad arguments to ql_batch_create");
     if (opts->precision != QL_FP32 && opts->precision != QL_FP64) return bfail(nullptr, QL_EINVAL, "bad precision");
+    if (opts->sums != QL_SUMS_DFP32 && opts->sums != QL_SUMS_FP64) return bfail(nullptr, QL_EINVAL, "bad sums");
     ql_batch *b = new ql_batch();
     b->precision = opts->precision;
+    b->sums64 = opts->precision == QL_FP32 && opts->sums == QL_SUMS_FP64;
     b->device = opts->device;
     b->n = n;
     b->alloc = opts->alloc;
@@ -247,7 +253,7 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
         D.dt = I.grid.dt;
         D.eta0 = eta0;
         D.inv_rho_ref = 1.0 / I.rho_ref;
-        D.tau_pref = 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * I.kn * I.grid.length * chi_set(eta0);
+        D.tau_pref = tau_prefactor(I.kn, I.grid.length, eta0);
         D.pr_const = I.pr_const;
         D.Q = I.vs.Q;
         D.pr_mode = I.pr_mode;
@@ -289,11 +295,11 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
         if (e != cudaSuccess) return bail(QL_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
         b->own_stream = true;
     }
-    static double tab[kTabTotal];
-    if (!build_tables(tab)) return bail(QL_EINVAL, "velocity-set construction failed");
-    e = upload_tables_f32(tab);
-    if (e == cudaSuccess) e = upload_tables_f64(tab);
-    if (e != cudaSuccess) return bail(QL_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    {
+        std::string terr;
+        if (!ensure_device_tables(b->device, terr)) return bail(QL_ECUDA, terr);
+    }
+    const double *tab = host_tables();
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
 
     b->arena_bytes = size_t(off) * b->elem;
@@ -338,7 +344,7 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(QL_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
     b->warps = kBatchWarps[0];
-    b->grid = b->sms * std::max(1, ctas_per_sm(b, b->warps));
+    b->grid = 0;  // one CTA per work item until ql_batch_tune picks otherwise
     *out = b;
     return QL_OK;
 }
@@ -354,7 +360,8 @@ ql_status ql_batch_tune(ql_batch *b, int32_t trial_launches, int32_t *warps_out,
     for (int wi = 0; wi < 2; ++wi) {
         const int w = kBatchWarps[wi];
         const int cmax = ctas_per_sm(b, w);
-        for (int c = 1; c <= cmax; ++c) {
+        // c = 0: one CTA per work item, the block scheduler filling the SMs
+        for (int c = 0; c <= cmax; ++c) {
             const int grid = b->sms * c;
             // stage 1 reads psi^n and writes psi^(1) only, so timing it leaves the state unchanged
             QB_CUDA(b, launch_stage(b, 1, w, grid));
@@ -376,7 +383,19 @@ ql_status ql_batch_tune(ql_batch *b, int32_t trial_launches, int32_t *warps_out,
     b->warps = bw;
     b->grid = bg;
     if (warps_out) *warps_out = bw;
-    if (ctas_per_sm_out) *ctas_per_sm_out = bg / std::max(1, b->sms);
+    if (ctas_per_sm_out) *ctas_per_sm_out = bg / std::max(1, b->sms);  // 0: one CTA per work item
+    return QL_OK;
+}
+
+ql_status ql_batch_set_shape(ql_batch *b, int32_t warps, int32_t per_sm)
+{
+    if (!b || (warps != kBatchWarps[0] && warps != kBatchWarps[1]) || per_sm < 0)
+        return bfail(b, QL_EINVAL, "bad arguments to ql_batch_set_shape (warps 8 or 4, ctas_per_sm >= 0)");
+    const int cmax = ctas_per_sm(b, warps);
+    if (per_sm > cmax)
+        return bfail(b, QL_EINVAL, "ctas_per_sm above the " + std::to_string(cmax) + " CTAs an SM holds");
+    b->warps = warps;
+    b->grid = b->sms * per_sm;
     return QL_OK;
 }
 
@@ -448,6 +467,7 @@ ql_status ql_batch_moments(ql_batch *b, int64_t i, double *rho, double *u, doubl
     a.Pxx = f + 5 * D.nx;
     a.partial = b->d_partial;
     a.err = b->d_err + i;
+    a.sums64 = b->sums64;
     cudaError_t e = b->precision == QL_FP32 ? launch_moments_f32(D.Q, a, b->d_tab64, b->stream)
                                             : launch_moments_f64(D.Q, a, b->d_tab64, b->stream);
     if (e == cudaSuccess) e = launch_reduce_totals(b->d_partial, moment_blocks(D.nx), b->d_totals, b->stream);

@@ -92,6 +92,11 @@ double cs_dz(double eta) { return 4.0 * (chi_set(eta) + eta * dchi_deta(eta)); }
 
 double denseness_of_eta(double eta) { return 6.0 * sqrt(2.0) * eta * chi_set(eta); }
 
+double tau_prefactor(double kn, double length, double eta0)
+{
+    return 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * kn * length * chi_set(eta0);
+}
+
 // The part of a ball of radius sigma at x < t (|t| <= sigma) is a spherical cap
 // of height h = sigma + t and volume pi h^2 (3 sigma - h) / 3; divided by the
 // ball's volume 4 pi sigma^3 / 3.

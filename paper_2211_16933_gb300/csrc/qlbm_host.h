@@ -19,11 +19,19 @@ double cs_dz(double eta);  // dZ/deta
 double denseness_of_eta(double eta);
 bool eta_of_denseness(double El, double *eta);
 
+// Secs. II.B-C, Eqs. (viscosity), (tau_sigma): the factor tau_pref of the
+// relaxation time
+//   tau = tau_pref / (rho^ chi sqrt T) [1 + 0.8 Y + (4/25)(1 + 12/pi) Y^2],
+// tau_pref = (5 sqrt(2 pi) / 16) Kn L chi(eta0), Y = b rho chi, with Kn = l0 / L
+// and l0 the Enskog mean free path at the reference density.  Every solver
+// form (single domain, batch, allocation-free) takes it from here.
+double tau_prefactor(double kn, double length, double eta0);
+
 // Adiabatic sound speed squared of the dense gas, Eq. (sw_cs) with c_V = 3/2:
 // c_s^2 = T (Z + eta Z') + (2/3) T Z^2, eta = eta0 rho / rho_ref.
 double sound_speed2(double eta0, double rho_ref, double rho, double T);
 
-// Sec. III.A, Eqs. (sw_cs), (sw_coeff): linear modes of a sound wave of wave
+// Sec. IV.A, Eqs. (sw_cs), (sw_coeff): linear modes of a sound wave of wave
 // number k on the uniform state (rho, T) of the model with these parameters.
 // out = {c_s, alpha_a, alpha_a without bulk viscosity, alpha_t, gamma}.
 bool sound_modes(double denseness, double kn, double length, double rho_ref, int pr_mode, double pr_const,

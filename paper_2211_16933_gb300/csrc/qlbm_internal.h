@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "qlbm.h"
 
 #ifdef __CUDACC__
@@ -81,6 +83,8 @@ struct StageArgs {
     double eta0, inv_rho_ref, tau_pref, pr_const;
     int pr_mode, enskog, periodic;
     int fault;      // 1: arm the staging barrier without issuing the copies (failure-detection tests)
+    int sums64;     // FP32: 1 combines the per-cell conserved sums in FP64, 0 in double-FP32
+    int vsplit;     // FP64: CTAs per tile, each updating a contiguous range of the velocity pairs (>= 1)
     unsigned *err;  // device error word; bit 0: non-physical cell, bit 1: a TMA staging wait gave up
     // chi_RET-FM only (else null): nbar of every column of the stage input
     // (nx + 2 kHalo values of the working precision), and the density of
@@ -116,6 +120,7 @@ struct BatchArgs {
     int64_t nwork;
     void *arena[3];
     unsigned *err;  // one error word per instance
+    int sums64;     // FP32: per-cell conserved sums in FP64 (else double-FP32)
 };
 // Tile shapes the batched kernels are compiled for (warps per CTA).
 constexpr int kBatchWarps[2] = {8, 4};
@@ -124,6 +129,14 @@ constexpr int kBatchWarps[2] = {8, 4};
 // current device, rounded to the precision of the translation unit.
 cudaError_t upload_tables_f32(const double *all);
 cudaError_t upload_tables_f64(const double *all);
+
+// The tables of every compiled velocity set (qlbm_api.cu): built on the host
+// once per process and uploaded once per device, under one lock, with that
+// device current.  Every entry point that launches tiled kernels calls it.
+// On failure returns false with a message in err.  host_tables() (kTabTotal
+// doubles) is valid after a successful call.
+bool ensure_device_tables(int device, std::string &err);
+const double *host_tables();
 
 // stage: 0 writes L[psi] into out, 1..3 are the stages of Eq. (rk3).
 cudaError_t launch_stage_f32(int Q, int stage, const StageArgs &a, cudaStream_t s);
@@ -155,6 +168,7 @@ struct MomentArgs {
     double *rho, *u, *T, *P, *q, *Pxx;  // each nx doubles (device), any may be null
     double *partial;                    // [nblocks][3] (device)
     unsigned *err;
+    int sums64;  // FP32 state: per-cell sums in FP64 (else double-FP32)
 };
 constexpr int kMomThreads = 256;
 inline int64_t moment_blocks(int64_t nx) { return (nx + kMomThreads - 1) / kMomThreads; }

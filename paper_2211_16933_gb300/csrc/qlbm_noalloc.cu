@@ -52,13 +52,10 @@ ql_status setup_device(int device, unsigned char **scratch)
     std::lock_guard<std::mutex> lk(g_setup_mutex);
     DeviceSetup &d = g_setup[device & 63];
     if (!d.ready) {
-        static double tab[kTabTotal];
-        if (!build_tables(tab)) return nfail(QL_EINVAL, "velocity-set construction failed");
-        cudaError_t e = upload_tables_f32(tab);
-        if (e == cudaSuccess) e = upload_tables_f64(tab);
-        if (e != cudaSuccess) return nfail(QL_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+        std::string terr;
+        if (!ensure_device_tables(device, terr)) return nfail(QL_ECUDA, terr);
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return nfail(QL_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
         d.scratch = static_cast<unsigned char *>(p);
@@ -87,10 +84,16 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     if (opts->pr_mode == QL_PR_CONST && !(opts->pr_const > 0)) return nfail(QL_EINVAL, "bad pr_const");
     if (opts->chi_mode != QL_CHI_SET)
         return nfail(QL_EUNSUPPORTED, "ql_step_noalloc supports chi_SET only (chi_RET-FM needs density buffers)");
+    if (opts->sums != QL_SUMS_DFP32 && opts->sums != QL_SUMS_FP64) return nfail(QL_EINVAL, "bad sums");
     if (row_stride < qlbm::row_stride(grid->nx))
         return nfail(QL_EINVAL, "row_stride " + std::to_string(row_stride) + " is below the " +
                                     std::to_string(qlbm::row_stride(grid->nx)) + " pairs this nx needs");
     const size_t elem = opts->precision == QL_FP32 ? 8 : 16;
+    // the largest row_stride whose two stage buffers fit, checked before any
+    // product that could overflow
+    if (uint64_t(row_stride) > (kScratchBytes - kHeaderBytes) / (2 * size_t(vs->Q) * elem))
+        return nfail(QL_EINVAL, "state of row_stride " + std::to_string(row_stride) + " exceeds the " +
+                                    std::to_string(kScratchBytes) + "-byte scratch (two stage buffers)");
     // psi points at cell 0 of row 0; the buffer starts at the first ghost column
     void *rows = static_cast<unsigned char *>(psi) - kHalo * elem;
     if (reinterpret_cast<uintptr_t>(rows) % 16 != 0 || (size_t(row_stride) * elem) % 16 != 0)
@@ -135,12 +138,14 @@ ql_status ql_step_noalloc(const ql_velset *vs, const ql_grid *grid, double dense
     a.dt = grid->dt;
     a.eta0 = eta0;
     a.inv_rho_ref = 1.0 / opts->rho_ref;
-    a.tau_pref = 5.0 * sqrt(2.0 * 3.14159265358979323846) / 16.0 * kn * grid->length * chi_set(eta0);
+    a.tau_pref = tau_prefactor(kn, grid->length, eta0);
     a.pr_const = opts->pr_const;
     a.pr_mode = opts->pr_mode;
     a.enskog = opts->enskog ? 1 : 0;
     a.periodic = bc->kind == QL_BC_PERIODIC;
     a.fault = 0;
+    a.sums64 = opts->precision == QL_FP32 && opts->sums == QL_SUMS_FP64;
+    a.vsplit = 1;  // the launcher picks the FP64 split
     a.err = err;
     a.nbar = nullptr;
     a.nout = nullptr;

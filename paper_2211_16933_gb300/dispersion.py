@@ -1,4 +1,4 @@
-"""Sound-wave dispersion study (Sec. III.A): a sweep of the reduced density,
+"""Sound-wave dispersion study (Sec. IV.A): a sweep of the reduced density,
 the amplitude of the density mode followed in time, and a Levenberg-Marquardt
 fit of the sound speed and the two damping rates, against the linear-theory
 values of ql_sound_modes.

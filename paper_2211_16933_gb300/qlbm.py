@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libqlbm.so")
 
 QL_OK, QL_EINVAL, QL_ENOMEM, QL_ECUDA, QL_ENONPHYSICAL, QL_ETIMEOUT, QL_EUNSUPPORTED = range(7)
 QL_FP64, QL_FP32 = 0, 1
+QL_SUMS_DFP32, QL_SUMS_FP64 = 0, 1
 QL_BC_PERIODIC, QL_BC_FIXED = 0, 1
 QL_INIT_SOUND, QL_INIT_RIEMANN, QL_INIT_SHOCK, QL_INIT_FIELDS = 0, 1, 2, 3
 QL_PR_CONST, QL_PR_DENSE = 0, 1
@@ -30,6 +31,7 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error",
             "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
             "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc",
+            "ql_batch_set_shape",
             "ql_batch_fields", "ql_batch_project", "ql_sound_modes", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
             "ql_closure_train_step", "ql_closure_train_steps", "ql_closure_params", "ql_closure_destroy",
             "ql_closure_last_error", "ql_step_count", "ql_save", "ql_checkpoint_read_info", "ql_load")
@@ -67,7 +69,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class ql_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("pr_mode", C.c_int32), ("enskog", C.c_int32), ("device", C.c_int32),
-                ("chi_mode", C.c_int32), ("fault", C.c_int32), ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
+                ("chi_mode", C.c_int32), ("fault", C.c_int32), ("sums", C.c_int32), ("pad_", C.c_int32),
+                ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -124,6 +127,7 @@ def lib():
         L.ql_rankine_hugoniot.argtypes = [C.c_double] * 5 + [_DP]
         L.ql_batch_create.argtypes = [C.POINTER(ql_instance), C.c_int64, C.POINTER(ql_opts), C.POINTER(V)]
         L.ql_batch_tune.argtypes = [V, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.ql_batch_set_shape.argtypes = [V, C.c_int32, C.c_int32]
         L.ql_batch_run.argtypes = [V, C.c_int64]
         L.ql_batch_sync.argtypes = [V, C.POINTER(C.c_uint32)]
         L.ql_batch_moments.argtypes = [V, C.c_int64] + [_DP] * 7
@@ -304,6 +308,10 @@ def ql_batch_tune(b, trial_launches=3):
     return w.value, c.value
 
 
+def ql_batch_set_shape(b, warps, ctas_per_sm):
+    _bcheck(lib().ql_batch_set_shape(b, warps, ctas_per_sm), b)
+
+
 def ql_batch_run(b, nsteps):
     _bcheck(lib().ql_batch_run(b, nsteps), b)
 
@@ -372,9 +380,9 @@ def make_instance(Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_k
 class Batch:
     """A batch of instances on one device; stream from PyTorch when available."""
 
-    def __init__(self, instances, precision=QL_FP32, device=0, use_torch=True):
+    def __init__(self, instances, precision=QL_FP32, device=0, use_torch=True, sums=QL_SUMS_DFP32):
         o = ql_opts()
-        o.precision, o.device = precision, device
+        o.precision, o.device, o.sums = precision, device, sums
         self.n = len(instances)
         self.Qs = [I.vs.Q for I in instances]
         self.nxs = [I.grid.nx for I in instances]
@@ -388,6 +396,10 @@ class Batch:
 
     def tune(self, trial_launches=3):
         return ql_batch_tune(self.b, trial_launches)
+
+    def set_shape(self, warps, ctas_per_sm):
+        """warps per CTA (8 or 4); ctas_per_sm 0: one CTA per work item, else a persistent grid."""
+        ql_batch_set_shape(self.b, warps, ctas_per_sm)
 
     def run(self, nsteps):
         ql_batch_run(self.b, nsteps)
@@ -535,9 +547,10 @@ class Solver:
     def __init__(self, Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND,
                  prm=(1.0, 1.0, 1e-3), rho=None, u=None, T=None, ghost=None, precision=QL_FP64,
                  pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, device=0, use_torch=True,
-                 chi_mode=None, fault=0):
+                 chi_mode=None, fault=0, sums=QL_SUMS_DFP32):
         """fault = 1 is for failure-detection tests (ql_opts.fault): the stage kernels give up waiting for
-        copies that are never issued and the next synchronising call raises QLError(QL_ECUDA)."""
+        copies that are never issued and the next synchronising call raises QLError(QL_ECUDA).  sums
+        (FP32 only): QL_SUMS_DFP32 or QL_SUMS_FP64, the arithmetic of the per-cell conserved sums."""
         self.Q, self.nx, self.precision = Q, nx, precision
         vs = ql_velset(Q, 0)
         grid = ql_grid(nx, length, dt)
@@ -557,6 +570,7 @@ class Solver:
         o.pr_const, o.rho_ref = pr_const, rho_ref
         o.chi_mode = QL_CHI_SET if chi_mode is None else chi_mode
         o.fault = fault
+        o.sums = sums
         self._attach_torch(o, device, use_torch)
         self.ctx = ql_create(vs, grid, denseness, kn, b, ini, o)
         self._read_info()

@@ -63,26 +63,38 @@ def test_batch_matches_single_instance_runs_bitwise(gpu, precision):
 
 
 def test_batch_tuning_keeps_results(gpu):
+    """The tuned shape, one CTA per work item (the default) and persistent grids of 4- and 8-warp CTAs all give
+    the same state bit for bit."""
     q = gpu
     keep = []
     items = _instances(q, 10, 3, keep)
     b1 = q.Batch([I for _, _, I in items], precision=1)
     w, c = b1.tune(2)
-    assert w in (8, 4) and c >= 1
+    assert w in (8, 4) and c >= 0
     b1.run(4)
     b1.sync()
-    b2 = q.Batch([I for _, _, I in items], precision=1)
-    b2.run(2)
-    b2.run(2)  # a second graph launch continues the run
-    b2.sync()
-    for i in range(len(items)):
-        x, y = b1.state(i), b2.state(i)
-        np.testing.assert_array_equal(x[0], y[0])
-        np.testing.assert_array_equal(x[1], y[1])
     info = b1.info()
     assert info[0] == len(items) and info[2] == w
+    others = []
+    for shape in (None, (8, 1), (4, 2), (8, 0)):
+        b2 = q.Batch([I for _, _, I in items], precision=1)
+        if shape:
+            b2.set_shape(*shape)
+        b2.run(2)
+        b2.run(2)  # a second graph launch continues the run
+        b2.sync()
+        others.append(b2)
+    for b2 in others:
+        for i in range(len(items)):
+            x, y = b1.state(i), b2.state(i)
+            np.testing.assert_array_equal(x[0], y[0])
+            np.testing.assert_array_equal(x[1], y[1])
+    for bad in ((6, 1), (8, -1), (8, 99)):
+        with pytest.raises(q.QLError):
+            others[0].set_shape(*bad)
+    for b2 in others:
+        b2.close()
     b1.close()
-    b2.close()
 
 
 def test_batch_sample_matches_oracle(gpu):

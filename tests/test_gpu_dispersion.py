@@ -1,4 +1,4 @@
-"""Sound-wave dispersion study (Sec. III.A) on the GPU: the density-mode amplitude of a batch of sound
+"""Sound-wave dispersion study (Sec. IV.A) on the GPU: the density-mode amplitude of a batch of sound
 waves across reduced densities, fitted with Eq. (sw_solution), against the linear-theory c_s, alpha_a
 and alpha_t of the model's own transport coefficients (Eqs. sw_cs, sw_coeff).  The kinetic model has
 no bulk viscosity, so alpha_a is compared with its value for mu_v = 0; at k l ~ 0.03 the Burnett
@@ -29,7 +29,7 @@ def test_eta_sweep_matches_linear_theory(gpu):
         if r["denseness"] in tol:
             assert abs(r["fit_alpha_a"] / r["alpha_a_no_bulk"] - 1) < tol[r["denseness"]], r
             assert abs(r["fit_alpha_t"] / r["alpha_t"] - 1) < tol[r["denseness"]], r
-    # denser gases depart from it (Sec. III.A reports the same for the simplified collision operator)
+    # denser gases depart from it (Sec. IV.A reports the same for the simplified collision operator)
     dev = [abs(r["fit_alpha_t"] / r["alpha_t"] - 1) for r in rows]
     assert dev[-1] > dev[0]
     # the dense-gas sound speed differs from the ideal-gas one, and the fit follows it

@@ -1,4 +1,4 @@
-"""The shock tube at small Knudsen number against the exact inviscid solution of the dense gas (Sec. III.B,
+"""The shock tube at small Knudsen number against the exact inviscid solution of the dense gas (Sec. IV.B,
 "Inviscid limit"): left state eta = 0.05 (E_l = 0.4825), right state eta / 8, T = 1, u = 0, chi_SET.  At
 Kn = 2e-5 the viscous and heat-conduction layers are a few 1e-3 wide at t = 0.15, so the plateau values
 and the fan match the Euler solution to a fraction of a percent, and the shock sits within a few cells of

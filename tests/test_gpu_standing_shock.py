@@ -47,3 +47,55 @@ def test_mach14_shock_long_run_fp32_against_fp64(gpu):
     for f, tol in (("rho", 2e-4), ("u", 2e-4), ("T", 2e-4), ("P", 2e-4), ("q", 1e-3)):
         err = float(np.abs(ma[f] - mb[f]).max() / np.abs(ma[f]).max())
         assert err <= tol, (f, err)
+
+
+def _run_to_steady(q, El, precision, steps, chunk=4096):
+    """Steps the Mach 1.4 standing shock (128 l0, N_x = 4096, Q = 32) in chunks; returns the last chunk's residual
+    max |d rho| / (dt rho), the mid-density shock position after each chunk, the far-field means of the first and
+    last 8 cells against the Rankine-Hugoniot states, and the spread of the mass flux rho u against rho1 u1."""
+    s = _solver(q, 1.4, El, precision)
+    u1, r2, u2, T2 = q.ql_rankine_hugoniot(s.eta0, 1.0, 1.0, 1.0, 1.4)
+    nx, L = 4096, 128.0
+    x = (np.arange(nx) + 0.5) * L / nx
+    rho_old, xs, res = s.moments()["rho"], [], None
+    for _ in range(steps // chunk):
+        s.step(chunk)
+        m = s.moments()
+        rho = m["rho"]
+        res = float(np.max(np.abs(rho - rho_old) / rho) / (chunk * s.dt))
+        rho_old = rho
+        mid = 0.5 * (1.0 + r2)
+        j = int(np.argmax(rho > mid))
+        xs.append(x[j - 1] + (mid - rho[j - 1]) / (rho[j] - rho[j - 1]) * (x[j] - x[j - 1]))
+    far = {"rho1": abs(rho[:8].mean() - 1.0), "u1": abs(m["u"][:8].mean() / u1 - 1.0),
+           "T1": abs(m["T"][:8].mean() - 1.0), "rho2": abs(rho[-8:].mean() / r2 - 1.0),
+           "u2": abs(m["u"][-8:].mean() / u2 - 1.0), "T2": abs(m["T"][-8:].mean() / T2 - 1.0)}
+    spread = float(np.max(np.abs(rho * m["u"] / u1 - 1.0)))
+    s.close()
+    return res, xs, far, spread
+
+
+def test_mach14_fp64_shock_reaches_the_rankine_hugoniot_states(gpu):
+    """C2 run to a steady profile in FP64 (E_l = 0.1; 327,680 steps, about 400 upstream mean free times): the
+    residual falls below 1e-6, the far fields equal the Rankine-Hugoniot states of Eq. (rankine_hugoniot) to
+    5e-6, the mass flux rho u is uniform to 5e-6 of rho1 u1, and the shock has stopped (it moves less than
+    0.01 l0 over the last 32,768 steps) within 1 l0 of where the initial profile put it (measured: residual
+    2.3e-7, far fields 5e-7, spread 1e-6, position 64.70 l0 for a start at 64)."""
+    res, xs, far, spread = _run_to_steady(gpu, 0.1, gpu.QL_FP64, 327680)
+    assert res < 1e-6, res
+    assert max(far.values()) < 5e-6, far
+    assert spread < 5e-6, spread
+    assert abs(xs[-1] - xs[-9]) < 0.01, xs[-9:]
+    assert abs(xs[-1] - 64.0) < 1.0, xs[-1]
+
+
+def test_mach14_fp32_shock_stalls_at_its_rounding_floor(gpu):
+    """The same shock in FP32 stops changing (residual below 1e-8) once the update dt L of the stored state falls
+    below half a unit of FP32 rounding; the state it freezes in keeps the far fields and the mass flux within
+    2e-3 of the Rankine-Hugoniot values (measured 1e-3 and 8e-4).  FP64 is the form that reaches the steady
+    profile itself."""
+    res, xs, far, spread = _run_to_steady(gpu, 0.1, gpu.QL_FP32, 131072)
+    assert res < 1e-8, res
+    assert max(far.values()) < 2e-3, far
+    assert spread < 2e-3, spread
+    assert abs(xs[-1] - xs[-9]) < 1e-3, xs[-9:]

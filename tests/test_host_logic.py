@@ -84,6 +84,9 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
         with pytest.raises(q.QLError) as e:
             q.Solver(**args, **kw)
         assert e.value.status == q.QL_EINVAL
+    with pytest.raises(q.QLError) as e:
+        q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, precision=q.QL_FP32, sums=2, **kw)
+    assert e.value.status == q.QL_EINVAL and "sums" in str(e.value)
     # a sound wave needs a periodic domain
     with pytest.raises(q.QLError) as e:
         q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_SOUND,
@@ -174,6 +177,23 @@ def test_noalloc_rejects_bad_layouts_before_touching_the_gpu(qlbm_lib):
         with pytest.raises(q.QLError) as e:
             q.ql_step_noalloc(vs, grid, 0.1, 0.1, b, o, psi, stride, 1)
         assert e.value.status == q.QL_EINVAL and words in str(e.value), str(e.value)
+
+
+def test_noalloc_rejects_a_huge_stride_without_overflow(qlbm_lib):
+    """A row stride whose stage buffers would wrap the size product (2^59 pairs at Q = 32 in FP64) is
+    refused as too large for the scratch, before any device call, and so is an unknown sums mode."""
+    q = qlbm_lib
+    vs, grid, b = q.ql_velset(32, 0), q.ql_grid(1024, 1.0, 1e-4), q.ql_bc(q.QL_BC_FIXED, 0)
+    o = q.ql_opts()
+    o.precision, o.pr_mode, o.enskog, o.rho_ref = q.QL_FP64, q.QL_PR_DENSE, 1, 1.0
+    for stride in (1 << 59, (1 << 62) + 2, 1 << 40):
+        with pytest.raises(q.QLError) as e:
+            q.ql_step_noalloc(vs, grid, 0.1, 0.1, b, o, 1 << 12, stride, 1)
+        assert e.value.status == q.QL_EINVAL and "scratch" in str(e.value), str(e.value)
+    o.sums = 7
+    with pytest.raises(q.QLError) as e:
+        q.ql_step_noalloc(vs, grid, 0.1, 0.1, b, o, 1 << 12, 1344, 1)
+    assert e.value.status == q.QL_EINVAL and "sums" in str(e.value)
 
 
 def test_python_binding_has_no_cpu_path():

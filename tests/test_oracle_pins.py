@@ -422,7 +422,7 @@ def test_sound_wave_initial_pressure_is_uniform_and_eos():
 
 
 def test_sound_speed_formulas_agree():
-    """P:647-form c_s^2 (oracle) equals Eq. (sw_cs), d_rho P + P/(rho^2 c_V) d_T P with c_V = 3/2,
+    """The c_s^2 of Sec. IV.B (oracle) equals Eq. (sw_cs), d_rho P + P/(rho^2 c_V) d_T P with c_V = 3/2,
     the derivatives of P = rho T Z_CS(eta0 rho) taken by central differences."""
     for El in (1e-8, 0.48, 1.1, 4.4):
         eta0 = O.eta_from_denseness(El)

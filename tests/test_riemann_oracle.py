@@ -31,7 +31,7 @@ def test_dense_shock_satisfies_rankine_hugoniot(El):
 
 @pytest.mark.parametrize("El", [0.4825, 1.917])
 def test_rarefaction_is_isentropic_for_the_carnahan_starling_gas(El):
-    """Along dP = c_s^2 d rho with the sound speed of Sec. III.B, the hard-sphere entropy
+    """Along dP = c_s^2 d rho with the sound speed of Sec. IV.B, the hard-sphere entropy
     (3/2) ln T - ln rho - eta (4 - 3 eta) / (1 - eta)^2 stays constant; the ideal-gas entropy does not."""
     g = R.DenseGas(O.eta_from_denseness(El))
     st = R.ShockTube(g, 1.0, 1.0, 0.125, 1.0)

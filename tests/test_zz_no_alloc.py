@@ -3,8 +3,10 @@
 Some callers cannot call cudaMalloc (a memory budget reserved by another
 framework, or a latency-critical loop where an allocation could synchronise the
 device).  This entry point keeps its two stage buffers in a fixed scratch array
-of the library.  Its results must equal those of ql_step on the same state, on
-two calls in a row (the scratch keeps the previous call's contents).
+of the library.  It launches the same stage kernels as ql_step on the same state
+layout with the same launch shape, so its results must equal those of ql_step
+bit for bit, on two calls in a row (the scratch keeps the previous call's
+contents), and a call must leave the device's free memory unchanged.
 """
 import numpy as np
 import pytest
@@ -29,6 +31,15 @@ def _case(q, precision, kind):
     return w, dt, bc, pr, mk
 
 
+def _opts(q, w, precision, pr):
+    import torch
+    o = q.ql_opts()
+    o.precision, o.pr_mode, o.enskog, o.device = precision, pr, 1, 0
+    o.pr_const, o.rho_ref = w["pr_const"], 1.0
+    o.stream = torch.cuda.current_stream().cuda_stream
+    return o
+
+
 @pytest.mark.parametrize("precision,kind", [(0, "sound"), (1, "sound"), (0, "shock"), (1, "shock")])
 def test_noalloc_matches_ql_step_on_two_calls(gpu, precision, kind):
     q = gpu
@@ -36,19 +47,34 @@ def test_noalloc_matches_ql_step_on_two_calls(gpu, precision, kind):
     ref, own = mk(), mk()
     psi, stride = q.ql_state_device(own.ctx)
     vs, grid, b = q.ql_velset(w["Q"], 0), q.ql_grid(w["nx"], w["length"], dt), q.ql_bc(bc, 0)
-    o = q.ql_opts()
-    o.precision, o.pr_mode, o.enskog, o.device = precision, pr, 1, 0
-    o.pr_const, o.rho_ref = w["pr_const"], 1.0
-    import torch
-    o.stream = torch.cuda.current_stream().cuda_stream
+    o = _opts(q, w, precision, pr)
     for _ in range(2):
         q.ql_step_noalloc(vs, grid, w["denseness"], w["kn"], b, o, psi, stride, 3)
         ref.step(3)
-    a, c = own.state(), ref.state()
-    tol = 1e-12 if precision == 0 else 1e-6
-    for x, y in zip(a, c):
-        assert float(np.abs(x - y).max()) <= tol * float(np.abs(y).max())
+        a, c = own.state(), ref.state()
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y)
     ref.close()
+    own.close()
+
+
+def test_noalloc_call_leaves_device_memory_unchanged(gpu):
+    """After a first call (which may load kernels and looks up the scratch address), a further call takes no
+    device memory: the free memory the driver reports is the same before and after it."""
+    import torch
+    q = gpu
+    w, dt, bc, pr, mk = _case(q, 1, "shock")
+    own = mk()
+    psi, stride = q.ql_state_device(own.ctx)
+    vs, grid, b = q.ql_velset(w["Q"], 0), q.ql_grid(w["nx"], w["length"], dt), q.ql_bc(bc, 0)
+    o = _opts(q, w, 1, pr)
+    q.ql_step_noalloc(vs, grid, w["denseness"], w["kn"], b, o, psi, stride, 2)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    q.ql_step_noalloc(vs, grid, w["denseness"], w["kn"], b, o, psi, stride, 2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
     own.close()
 
 
