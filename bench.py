@@ -691,6 +691,71 @@ def run_dispersion(args):
     print(json.dumps(line), flush=True)
 
 
+def _shock_to_steady(q, inputs, mach, El, precision, max_steps, tol, chunk=8192):
+    """Runs the standing shock (128 upstream mean free paths, N_x = 4096, Q = 32) in chunks until the residual
+    max |d rho| / (dt rho) over a chunk falls below tol, or max_steps; returns the record of the run."""
+    import torch
+    w = inputs.normal_shock(mach, El)
+    p, _ = q.ql_velocity_set(w["Q"])
+    dt = inputs.cfl_dt(w["length"] / w["nx"], float(np.abs(p).max()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = q.Solver(w["Q"], w["nx"], w["length"], dt, El, w["kn"], bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_SHOCK,
+                 prm=w["prm"], precision=precision, pr_mode=q.QL_PR_DENSE)
+    u1, r2, u2, T2 = q.ql_rankine_hugoniot(s.eta0, 1.0, 1.0, 1.0, mach)
+    x = (np.arange(w["nx"]) + 0.5) * w["length"] / w["nx"]
+    rho_old, n, hist = s.moments()["rho"], 0, []
+    while n < max_steps:
+        s.step(chunk)
+        n += chunk
+        m = s.moments()
+        rho = m["rho"]
+        res = float(np.max(np.abs(rho - rho_old) / rho) / (chunk * dt))
+        rho_old = rho
+        mid = 0.5 * (1.0 + r2)
+        j = int(np.argmax(rho > mid))
+        hist.append((n, res, float(x[j - 1] + (mid - rho[j - 1]) / (rho[j] - rho[j - 1]) * (x[j] - x[j - 1]))))
+        if res < tol:
+            break
+    wall = time.perf_counter() - t0
+    far = {"rho1": abs(rho[:8].mean() - 1.0), "u1": abs(m["u"][:8].mean() / u1 - 1.0), "T1": abs(m["T"][:8].mean() - 1.0),
+           "rho2": abs(rho[-8:].mean() / r2 - 1.0), "u2": abs(m["u"][-8:].mean() / u2 - 1.0),
+           "T2": abs(m["T"][-8:].mean() / T2 - 1.0)}
+    s.close()
+    last = hist[-1]
+    back = hist[max(0, len(hist) - 5)]
+    return {"denseness": El, "mach": mach, "precision": "fp64" if precision == q.QL_FP64 else "fp32", "steps": n,
+            "t": n * dt, "wall_s": wall, "residual": last[1], "converged": last[1] < tol, "tol": tol,
+            "far_field_rel_err": far, "mass_flux_spread": float(np.max(np.abs(rho * m["u"] / u1 - 1.0))),
+            "shock_position_l0": last[2], "start_position_l0": 0.5 * w["length"],
+            "drift_last_chunks_l0": last[2] - back[2], "drift_steps": last[0] - back[0]}
+
+
+def run_standing_shock(args):
+    """C2: the Mach 1.4 standing shock at E_l = 0.05, 0.1, 0.2 (N_x = 4096, Q = 32, 128 upstream mean free
+    paths, Rankine-Hugoniot ghosts) run to a steady profile: FP64 to a residual below 1e-9 (or --shock-steps),
+    FP32 to the floor where its update falls below the rounding of the stored state."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import inputs
+    from paper_2211_16933_gb300 import qlbm as q
+    torch.cuda.set_device(0)
+    B.build()
+    rows = []
+    for El in (0.05, 0.1, 0.2):
+        rows.append(_shock_to_steady(q, inputs, 1.4, El, q.QL_FP64, args.shock_steps, 1e-9))
+        rows.append(_shock_to_steady(q, inputs, 1.4, El, q.QL_FP32, args.shock_steps, 1e-8))
+    steps = sum(r["steps"] for r in rows)
+    line = {"metric": "time to steady profile", "value": sum(r["wall_s"] for r in rows if r["precision"] == "fp64"),
+            "unit": "s", "n_gpus": 1, "steps": steps, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "gpu_launches": 3 * steps,
+            "config": {"workload": "standing_shock_M1.4_nx4096_Q32", "length_l0": 128, "tol_fp64": 1e-9,
+                       "tol_fp32": 1e-8, "max_steps": args.shock_steps,
+                       "value": "sum of the FP64 runs' times, solver creation to the last residual check"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 # The paper's timed shock-tube runs (Table comp_time): sigma, Q, N_x, and the LB wall time on one core of an
 # Intel Xeon Gold 6330.
 PAPER_SHOCK_TABLE = [(0.001, 8, 1600, 62.0), (0.01, 8, 800, 32.0), (0.1, 20, 640, 71.0), (1.0, 200, 160, 176.0)]
@@ -782,7 +847,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-with-FP64-sums, FP64 and batch sub-records")
     ap.add_argument("--fp64-steps", type=int, default=20)
-    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table"], default="sod")
+    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table", "standing_shock"],
+                    default="sod")
+    ap.add_argument("--shock-steps", type=int, default=1_200_000)
     ap.add_argument("--table-steps", type=int, default=9000)
     ap.add_argument("--sweep", type=int, default=16)
     ap.add_argument("--pairs", type=int, default=20000)
@@ -809,6 +876,9 @@ def main():
         return
     if args.workload == "paper_table" and args.impl == "ours":
         run_paper_table(args)
+        return
+    if args.workload == "standing_shock" and args.impl == "ours":
+        run_standing_shock(args)
         return
     if args.impl == "reference":
         run_reference(args, w)
