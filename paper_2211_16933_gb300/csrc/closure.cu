@@ -2,7 +2,9 @@
 // 64 hidden channels, ReLU) that maps coarse-grid moment fields to a
 // correction of those fields.  Training and inference run in this file's
 // kernels: BF16 weights and activations, FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), FP32 master weights updated by Adam.
+// (tcgen05.mma with TMEM accumulators for the forward and backward-data
+// convolutions, mma.sync m16n8k16 for the weight gradients), FP32 master
+// weights updated by Adam.
 //
 // Layout: activations are channels-last, act[b][x][c] (bf16), with channel
 // counts padded to multiples of 16; padded channels
@@ -94,8 +96,71 @@ __device__ __forceinline__ int wrap_pos(int p, int X, int mode, bool *inside)
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Blackwell tensor cores (tcgen05): the A and B operands are read from shared
+// memory through 64-bit matrix descriptors, the FP32 accumulator lives in
+// tensor memory (TMEM) and is read back by tcgen05.ld.
+//
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout: core
+// matrices of 8 rows x 16 bytes stored as 128 contiguous bytes; lbo is the byte
+// distance between core matrices adjacent along K, sbo along M (or N).  Fields:
+// address >> 4 in bits 0-13, lbo >> 4 in 16-29, sbo >> 4 in 32-45, descriptor
+// version 1 in bits 46-47, base offset 0, layout type 0 (no swizzle) in 61-63.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 =
+// 1), BF16 A and B (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, int accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init1(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane (lane = 32 (warp % 4) + lane id).
+__device__ __forceinline__ void tmem_ld16(float (&v)[16], uint32_t taddr)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+// Polls of the tensor cores' completion barrier before a CTA gives up (bit 1 of
+// the closure's error word; each try_wait may suspend the thread for a while).
+constexpr uint32_t kMmaPolls = 1u << 20;
+
 // Epilogues of the convolution kernel.
 enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
+
+// Positions per tile of the convolution (the M of one tensor-core instruction).
+constexpr int kConvM = 128;
 
 // y[b][x][co] = sum_{j, ci} w[co][j][ci] in[b][x + j - 2][ci] (+ bias), then
 //   EPI_RELU_BF16: relu, stored bf16;  EPI_F32: stored f32;
@@ -103,128 +168,180 @@ enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
 //     positions outside the sample are zero; at the two end positions of a
 //     replicate-padded sample edge[b][side][co] is added (edge_grad_kernel);
 //     then times (mask[b][x][co] > 0), stored bf16 (ReLU backward).
-// Persistent CTAs: the layer's weights are loaded into shared memory once, then
-// each CTA walks (sample, 64-position tile) items with a grid stride, the next
-// item's input window copied in by cp.async while the current one is used; per item
-// 4 warps x 16 positions, all COUT channels, as an implicit GEMM (M = positions,
-// N = COUT, K = 5 CIN) on mma.sync m16n8k16 with ldmatrix fragments.
+// An implicit GEMM per (sample, 128-position tile): M = positions, N = COUT,
+// K = 5 CIN, on tcgen05.mma (M 128, N COUT, K 16 per instruction, issued by one
+// thread) with the FP32 accumulator in TMEM.  Both operands are K-major in the
+// no-swizzle canonical layout.  The input window of 132 positions is stored as
+// [chunk of 8 channels][position][8], so every 8 consecutive positions of a
+// chunk are one core matrix and tap j is the same descriptor moved by j rows
+// (16 bytes): A(j) = window rows j .. j + 127.  The weights are stored as
+// [K chunk = (j, 8 channels)][co][8].  Persistent CTAs load the layer's
+// weights once, then walk the items with a grid stride, the next item's window
+// copied in by cp.async while the tensor cores work on the current one; after
+// each item's products complete (tcgen05.commit on an mbarrier), thread
+// 32 w + l reads position 32 w + l of the tile (TMEM lane) and applies the
+// epilogue.  A wait on the products that gives up sets bit 1 of *err.
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w,
                                                    const float *__restrict__ bias, const int *__restrict__ periodic,
                                                    int X, int B, void *__restrict__ out, const bf16 *__restrict__ mask,
-                                                   const float *__restrict__ edge)
+                                                   const float *__restrict__ edge, unsigned *__restrict__ err)
 {
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0, "padded channels");
-    constexpr int WS = CIN + 8;  // smem row stride (bf16): 16-byte rows, no ldmatrix bank conflicts
-    extern __shared__ __align__(16) unsigned char smem[];
-    bf16 *ws = reinterpret_cast<bf16 *>(smem);  // [COUT * 5][WS]
-    bf16 *const win_base = ws + COUT * kTaps * WS;  // two stages of [kTM + 4][WS]
-    constexpr int kWin = (kTM + 4) * WS;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
-    constexpr int VPR = CIN / 8;  // 16-byte vectors per row
-    for (int e = t; e < COUT * kTaps * VPR; e += blockDim.x) {
-        const int r = e / VPR, v = e % VPR;
-        *reinterpret_cast<uint4 *>(ws + r * WS + v * 8) = *reinterpret_cast<const uint4 *>(w + r * CIN + v * 8);
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "padded channels, one tcgen05 N");
+    constexpr int KC = CIN / 8;                       // 8-channel chunks of a position
+    constexpr int ROWS = kConvM + kTaps - 1;          // window positions
+    constexpr int WCH = kTaps * KC;                   // weight chunks along K
+    constexpr uint32_t ALBO = ROWS * 16, BLBO = COUT * 16;
+    constexpr uint32_t NCOL = COUT < 32 ? 32 : COUT;  // TMEM columns (a power of 2, at least 32)
+    constexpr int kWin = KC * ROWS * 8;               // bf16 per window stage
+    extern __shared__ __align__(128) unsigned char smem[];
+    bf16 *const ws = reinterpret_cast<bf16 *>(smem);  // [WCH][COUT][8]
+    bf16 *const win_base = ws + WCH * COUT * 8;       // two stages of [KC][ROWS][8]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_taddr;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // W[co][j][ci] -> chunk r = j KC + ci / 8, row co
+    for (int e = t; e < COUT * WCH; e += blockDim.x) {
+        const int co = e / WCH, r = e % WCH;
+        *reinterpret_cast<uint4 *>(ws + (r * COUT + co) * 8) =
+            *reinterpret_cast<const uint4 *>(w + (size_t(co) * WCH + r) * 8);
     }
-    const int tiles = (X + kTM - 1) / kTM;
-    const int m0 = warp * 16;
-    // ldmatrix row of this lane: matrix mat = lane / 8, row t8 = lane % 8
-    const int t8 = lane & 7, mat = lane >> 3;
+    if (t == 0) mbar_init1(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const int tiles = (X + kConvM - 1) / kConvM;
     // cp.async of the input window of `item` into stage `st` (positions beyond the
-    // padding are zero-filled: source size 0, nothing is read); the next item's
-    // window is copied in while the current one is multiplied
+    // padding are zero-filled: source size 0, nothing is read)
     auto stage_win = [&](int item, int st) {
         bf16 *win = win_base + st * kWin;
-        const int b = item / tiles, x0 = (item % tiles) * kTM;
+        const int b = item / tiles, x0 = (item % tiles) * kConvM;
         const int mode = periodic[b] != 0 ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
-        for (int e = t; e < (kTM + 4) * VPR; e += blockDim.x) {
-            const int r = e / VPR, v = e % VPR;
+        for (int e = t; e < ROWS * KC; e += blockDim.x) {
+            const int p = e / KC, c = e % KC;
             bool inside;
-            const int p = wrap_pos(x0 - 2 + r, X, mode, &inside);
-            const bf16 *src = inside ? in + (size_t(b) * X + p) * CIN + v * 8 : in;
-            cp_async16_zfill(win + r * WS + v * 8, src, inside ? 16u : 0u);
+            const int x = wrap_pos(x0 - 2 + p, X, mode, &inside);
+            const bf16 *src = inside ? in + (size_t(b) * X + x) * CIN + c * 8 : in;
+            cp_async16_zfill(win + (c * ROWS + p) * 8, src, inside ? 16u : 0u);
         }
         cp_async_commit();
     };
     int st = 0;
+    uint32_t phase = 0;
+    bool failed = false;
     if (blockIdx.x < B * tiles) stage_win(blockIdx.x, 0);
     for (int item = blockIdx.x; item < B * tiles; item += gridDim.x, st ^= 1) {
-        const int b = item / tiles, x0 = (item % tiles) * kTM;
-        const bool per = periodic[b] != 0;
+        const int b = item / tiles, x0 = (item % tiles) * kConvM;
         const bool more = item + int(gridDim.x) < B * tiles;
         if (more) stage_win(item + gridDim.x, st ^ 1);
         if (more) cp_async_wait<1>();
         else cp_async_wait<0>();
-        __syncthreads();  // this item's window (and, first time, the weights) visible
-        const bf16 *win = win_base + st * kWin;
-        // ReLU-backward mask of this thread's outputs, loaded before the products so
-        // that its latency is hidden behind them
-        __nv_bfloat162 mk[EPI == EPI_MASK_BF16 ? COUT / 8 : 1][2];
+        // this thread's copies (and, the first time, its weight stores) before the
+        // tensor cores read them through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t wa = smem_u32(win_base + st * kWin), wb = smem_u32(ws);
+            int step = 0;
+#pragma unroll
+            for (int j = 0; j < kTaps; ++j)
+#pragma unroll
+                for (int kc = 0; kc < KC; kc += 2, ++step)
+                    umma_bf16(taddr, umma_desc(wa + kc * ALBO + j * 16, ALBO, 128),
+                              umma_desc(wb + (j * KC + kc) * BLBO, BLBO, 128), umma_idesc_bf16(kConvM, COUT), step);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        // the thread's position and, for the backward pass, its ReLU mask (loaded
+        // while the tensor cores work)
+        const int m = warp * 32 + lane, x = x0 + m;
+        const bool valid = x < X;
+        uint4 mk[EPI == EPI_MASK_BF16 ? COUT / 8 : 1];
         if constexpr (EPI == EPI_MASK_BF16) {
 #pragma unroll
-            for (int n = 0; n < COUT / 8; ++n)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int x = x0 + m0 + g + 8 * h;
-                    mk[n][h] = x < X ? *reinterpret_cast<const __nv_bfloat162 *>(
-                                           mask + (size_t(b) * X + x) * COUT + n * 8 + 2 * tg)
-                                     : __floats2bfloat162_rn(0.f, 0.f);
-                }
+            for (int v = 0; v < COUT / 8; ++v)
+                mk[v] = valid ? *reinterpret_cast<const uint4 *>(mask + (size_t(b) * X + x) * COUT + v * 8)
+                              : make_uint4(0u, 0u, 0u, 0u);
         }
-
-        float acc[COUT / 8][4];
+        uint32_t polls = 0;
+        while (!mbar_test(&mbar, phase) && ++polls < kMmaPolls) {
+        }
+        if (__syncthreads_or(polls >= kMmaPolls)) {
+            if (t == 0) atomicOr(err, 2u);
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool per = periodic[b] != 0;
+        const size_t o = (size_t(b) * X + (valid ? x : 0)) * COUT;
 #pragma unroll
-        for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tmem_ld16(v, taddr + (uint32_t(warp * 32) << 16) + c0);
+            if (!valid) continue;
+            if (EPI != EPI_MASK_BF16) {
 #pragma unroll
-        for (int j = 0; j < kTaps; ++j) {
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                // A[m][k] = win[m0 + m + j][16 kc + k]: matrices (m 0-7 | 8-15) x (k 0-7 | 8-15)
-                uint32_t a[4];
-                ldsm_x4(a, win + (m0 + j + (mat & 1) * 8 + t8) * WS + kc * 16 + (mat >> 1) * 8);
-#pragma unroll
-                for (int n = 0; n < COUT / 8; n += 2) {
-                    // B[k][co] = ws[co * 5 + j][16 kc + k]: matrices (co 0-7: k 0-7, 8-15), (co 8-15: ...)
-                    uint32_t bb[4];
-                    ldsm_x4(bb, ws + ((n * 8 + (mat >> 1) * 8 + t8) * kTaps + j) * WS + kc * 16 + (mat & 1) * 8);
-                    mma16816(acc[n], a, bb);
-                    mma16816(acc[n + 1], a, bb + 2);
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 bb = *reinterpret_cast<const float4 *>(bias + c0 + q);
+                    v[q] += bb.x;
+                    v[q + 1] += bb.y;
+                    v[q + 2] += bb.z;
+                    v[q + 3] += bb.w;
                 }
             }
-        }
-        __syncthreads();  // every warp is done with this window: it is refilled two items later
+            if (EPI == EPI_F32) {
+                float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(out) + o + c0);
 #pragma unroll
-        for (int n = 0; n < COUT / 8; ++n) {
-            const int co = n * 8 + 2 * tg;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = x0 + m0 + g + 8 * h;
-                if (x >= X) continue;
-                float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
-                const size_t o = (size_t(b) * X + x) * COUT + co;
-                if (EPI != EPI_MASK_BF16) {
-                    v0 += bias[co];
-                    v1 += bias[co + 1];
-                }
-                if (EPI == EPI_RELU_BF16) {
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) =
-                        __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
-                } else if (EPI == EPI_F32) {
-                    *reinterpret_cast<float2 *>(static_cast<float *>(out) + o) = make_float2(v0, v1);
-                } else {
-                    if (!per && (x == 0 || x == X - 1)) {
-                        const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + co;
-                        v0 += eg[0];
-                        v1 += eg[1];
-                    }
-                    const __nv_bfloat162 mv = mk[n][h];
-                    v0 = __bfloat162float(mv.x) > 0.f ? v0 : 0.f;
-                    v1 = __bfloat162float(mv.y) > 0.f ? v1 : 0.f;
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(out) + o) = __floats2bfloat162_rn(v0, v1);
-                }
+                for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                continue;
             }
+            if (EPI == EPI_MASK_BF16) {
+                if (!per && (x == 0 || x == X - 1)) {
+                    const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + c0;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] += eg[q];
+                }
+                const __nv_bfloat162 *mp = reinterpret_cast<const __nv_bfloat162 *>(&mk[c0 / 8]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __nv_bfloat162 mv = mp[q];
+                    v[2 * q] = __bfloat162float(mv.x) > 0.f ? v[2 * q] : 0.f;
+                    v[2 * q + 1] = __bfloat162float(mv.y) > 0.f ? v[2 * q + 1] : 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
+            }
+            uint4 pk[2];
+            __nv_bfloat162 *pp = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) pp[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            uint4 *dst = reinterpret_cast<uint4 *>(static_cast<bf16 *>(out) + o + c0);
+            dst[0] = pk[0];
+            dst[1] = pk[1];
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // TMEM and this window stage are reused by later items
+    }
+    cp_async_wait<0>();
+    if (failed) {  // let products still in flight land before their TMEM is freed
+        uint32_t polls = 0;
+        while (!mbar_test(&mbar, phase) && ++polls < kMmaPolls) {
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(NCOL) : "memory");
 }
 
 // Weight and bias gradients of one layer:
@@ -611,11 +728,15 @@ struct Layer {
     int64_t woff, boff;  // offsets of W [cout][5][cin] and bias [cout] in the f32 parameter vector
 };
 
+// Persistent grid of the convolution: the CTAs an SM holds by shared memory,
+// at most as many as its 512 TMEM columns give accumulators (each CTA allocates
+// its columns for the whole launch).
 template <int CIN, int COUT, int EPI>
 cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const int *per, int B, int X, void *out,
-                        const bf16 *mask, const float *edge, cudaStream_t s)
+                        const bf16 *mask, const float *edge, unsigned *err, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(bf16) * (2 * (kTM + 4) * (CIN + 8) + COUT * kTaps * (CIN + 8));
+    constexpr size_t smem = 16 * (size_t(kTaps) * (CIN / 8) * COUT + 2 * size_t(CIN / 8) * (kConvM + kTaps - 1));
+    constexpr int ncol = COUT < 32 ? 32 : COUT;
     auto k = conv_kernel<CIN, COUT, EPI>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -624,18 +745,19 @@ cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
     if (e != cudaSuccess) return e;
-    const int items = B * ((X + kTM - 1) / kTM);
-    const int grid = std::max(1, std::min(items, std::max(1, sms) * std::max(1, per_sm)));
-    k<<<grid, 128, smem, s>>>(in, w, bias, per, X, B, out, mask, edge);
+    per_sm = std::max(1, std::min(per_sm, 512 / ncol));
+    const int items = B * ((X + kConvM - 1) / kConvM);
+    const int grid = std::max(1, std::min(items, std::max(1, sms) * per_sm));
+    k<<<grid, 128, smem, s>>>(in, w, bias, per, X, B, out, mask, edge, err);
     return cudaGetLastError();
 }
 
 cudaError_t conv_any(int cin, int cout, int epi, const bf16 *in, const bf16 *w, const float *bias, const int *per,
-                     int B, int X, void *out, const bf16 *mask, const float *edge, cudaStream_t s)
+                     int B, int X, void *out, const bf16 *mask, const float *edge, unsigned *err, cudaStream_t s)
 {
 #define QC(CI, CO, EP)                                                                 \
     if (cin == CI && cout == CO && epi == EP)                                          \
-        return conv_launch<CI, CO, EP>(in, w, bias, per, B, X, out, mask, edge, s);
+        return conv_launch<CI, CO, EP>(in, w, bias, per, B, X, out, mask, edge, err, s);
     QC(16, 64, EPI_RELU_BF16)
     QC(64, 64, EPI_RELU_BF16)
     QC(64, 16, EPI_F32)
@@ -774,7 +896,7 @@ static ql_status forward(ql_closure *c, const int *per, int B)
         const bool last = l == nl - 1;
         void *out = last ? static_cast<void *>(c->pred) : static_cast<void *>(c->act[l + 1]);
         QC_CUDA(c, conv_any(L.cin, L.cout, last ? EPI_F32 : EPI_RELU_BF16, c->act[l], c->w16 + L.woff,
-                            c->param + L.boff, per, B, X, out, nullptr, nullptr, c->stream));
+                            c->param + L.boff, per, B, X, out, nullptr, nullptr, c->bad, c->stream));
     }
     return QL_OK;
 }
@@ -790,6 +912,19 @@ static ql_status pack(ql_closure *c, const float *x, int B)
 }
 
 static ql_status adam_step(ql_closure *c, float lr);
+
+// The device flags (synchronises): bit 0, a mini-batch index outside the data
+// set; bit 1, a convolution that gave up waiting for its tensor-core products.
+static ql_status check_flags(ql_closure *c)
+{
+    unsigned bad = 0;
+    QC_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    QC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad & 2u) return cfail(c, QL_ECUDA, "a convolution gave up waiting for its tensor-core products");
+    if (bad & 1u) return cfail(c, QL_EINVAL, "perm holds a sample index outside [0, n); sample 0 was used in its place");
+    return QL_OK;
+}
+
 static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic,
                                     int64_t n, const int32_t *perm, int64_t B, float *losses);
 
@@ -826,7 +961,7 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
                                                                  c->edge);
             QC_CUDA(c, cudaGetLastError());
             QC_CUDA(c, conv_any(L.cout, L.cin, EPI_MASK_BF16, c->dz[l], c->wt16 + L.woff, nullptr, per, B, X,
-                                c->dz[l - 1], c->act[l], c->edge, c->stream));
+                                c->dz[l - 1], c->act[l], c->edge, c->bad, c->stream));
         }
     }
     if (loss) {
@@ -964,7 +1099,7 @@ ql_status ql_closure_gradients(ql_closure *c, const float *x, const float *y, co
         QC_CUDA(c, cudaMemcpyAsync(grad_host, c->grad, sizeof(float) * c->nparam, cudaMemcpyDeviceToHost, c->stream));
         QC_CUDA(c, cudaStreamSynchronize(c->stream));
     }
-    return QL_OK;
+    return grad_host || loss ? check_flags(c) : QL_OK;
 }
 
 ql_status ql_closure_train_step(ql_closure *c, const float *x, const float *y, const int32_t *periodic, int64_t B,
@@ -1042,11 +1177,7 @@ ql_status ql_closure_train_steps(ql_closure *c, const float *x, const float *y, 
         }
         c->step += nsteps;
     }
-    unsigned bad = 0;
-    QC_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    QC_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (bad) return cfail(c, QL_EINVAL, "perm holds a sample index outside [0, n); sample 0 was used in its place");
-    return QL_OK;
+    return check_flags(c);
 }
 
 }  // extern "C"

@@ -198,9 +198,12 @@ def test_device_training_loop_across_calls(gpu):
 
 
 def test_trained_closure_improves_held_out_coarse_fields(gpu):
+    """256 training pairs (2048 samples), 40 epochs; on 64 held-out pairs the corrected coarse fields are at
+    least 2.5 times closer to the fine solve than the coarse fields alone, summed over rho, u, T, q, Pxx, and at
+    least 1.8 times closer in every field (measured: 4.6 and 2.3 for q, the field the net helps least)."""
     from paper_2211_16933_gb300 import learned as L
-    train_specs = L.pair_specs(48, 0)
-    test_specs = L.pair_specs(16, 10 ** 6)
+    train_specs = L.pair_specs(256, 0)
+    test_specs = L.pair_specs(64, 10 ** 6)
     x, y, per, _ = L.generate(train_specs, fine_steps=512)
     xt, yt, pt, ct = L.generate(test_specs, fine_steps=512)
     net, losses = L.train(x, y, per, epochs=40, batch=64, lr=2e-3, seed=0)
@@ -211,4 +214,6 @@ def test_trained_closure_improves_held_out_coarse_fields(gpu):
     rms_base = sum(v["l2"] for v in base.values())
     rms_corr = sum(v["l2"] for v in corr.values())
     assert losses[-1] < losses[0]
-    assert rms_corr < 0.8 * rms_base, (base, corr)
+    assert rms_corr < rms_base / 2.5, (base, corr)
+    for k in base:
+        assert corr[k]["l2"] < base[k]["l2"] / 1.8, (k, base[k], corr[k])
