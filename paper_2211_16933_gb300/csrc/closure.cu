@@ -2,13 +2,13 @@
 // 64 hidden channels, ReLU) that maps coarse-grid moment fields to a
 // correction of those fields.  Training and inference run in this file's
 // kernels: BF16 weights and activations, FP32 accumulation on the tensor cores
-// (tcgen05.mma with TMEM accumulators for the forward and backward-data
-// convolutions, mma.sync m16n8k16 for the weight gradients), FP32 master
-// weights updated by Adam.
+// (tcgen05.mma with TMEM accumulators: the forward and backward-data
+// convolutions and the weight gradients), FP32 master weights updated by Adam.
 //
-// Layout: activations are channels-last, act[b][x][c] (bf16), with channel
-// counts padded to multiples of 16; padded channels
-// hold zeros and their weights stay zero.  Weights of layer l are
+// Layout: activations and their gradients are bf16 [B][X][C] tensors stored
+// chunk-major (16-byte rows of 8 channels, see cm_index), with channel counts
+// padded to multiples of 16; padded channels hold zeros and their weights
+// stay zero.  Weights of layer l are
 // W[co][j][ci] (tap j = 0..4 reads position x + j - 2).  Sample b is padded
 // periodically (periodic[b] != 0) or by replicating its end values.
 #include <cuda_bf16.h>
@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -26,66 +27,16 @@
 namespace {
 
 constexpr int kTaps = 5;
-constexpr int kTM = 64;  // positions per CTA tile
-// Resident weight-gradient CTAs per SM the kernel is compiled for.
-#ifndef QL_WGRAD_MINBLOCKS
-#define QL_WGRAD_MINBLOCKS 2
-#endif
+constexpr int kMaxDevices = 64;  // devices whose launch shapes are remembered
 typedef __nv_bfloat16 bf16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-// ldmatrix: lanes 8i..8i+7 give the 16-byte row addresses of 8x8 matrix i; each
-// lane receives, per matrix, the element pair (row lane/4, columns 2 (lane%4),
-// +1) of the matrix, or of its transpose with .trans (the mma.sync fragment
-// layouts).
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const bf16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x2_trans(uint32_t (&r)[2], const bf16 *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
-                 : "=r"(r[0]), "=r"(r[1])
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma16816(float *d, const uint32_t *a, const uint32_t *b)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // Padding of a position outside [0, X): periodic image, copy of the nearest end
 // value, or zero (the transposed convolution of the backward pass).
 enum { PAD_ZERO = 0, PAD_PERIODIC = 1, PAD_REPLICATE = 2 };
-// 16-byte asynchronous copy global -> shared; src_bytes 0 writes zeros and
-// reads nothing.  Completion per thread by commit / wait groups.
-__device__ __forceinline__ void cp_async16_zfill(void *smem_dst, const void *src, unsigned src_bytes)
-{
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 __device__ __forceinline__ int wrap_pos(int p, int X, int mode, bool *inside)
 {
     *inside = true;
@@ -125,11 +76,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t
                  "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
                  : "memory");
 }
-__device__ __forceinline__ void mbar_init1(uint64_t *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -140,21 +86,103 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// 16 consecutive FP32 columns of this thread's TMEM lane (lane = 32 (warp % 4) + lane id).
-__device__ __forceinline__ void tmem_ld16(float (&v)[16], uint32_t taddr)
+// 16 consecutive FP32 columns of this thread's TMEM lane (lane = 32 (warp % 4) +
+// lane id), without waiting for them: tmem_wait() makes them usable.
+__device__ __forceinline__ void tmem_ld16(uint32_t *r, uint32_t taddr)
 {
-    uint32_t r[16];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
+}
+// Waits for this thread's tcgen05.ld; the registers pass through an empty asm
+// after the wait, so no use of them is scheduled before it.
+template <int N>
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[N])
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+    for (int q = 0; q < N; ++q) asm volatile("" : "+r"(r[q])::"memory");
 }
-// Polls of the tensor cores' completion barrier before a CTA gives up (bit 1 of
-// the closure's error word; each try_wait may suspend the thread for a while).
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// Polls of an mbarrier before a thread gives up (bit 1 of the closure's error
+// word; each try_wait may suspend the thread for a while).
 constexpr uint32_t kMmaPolls = 1u << 20;
+// Waits until the phase of parity `parity` of *bar has completed.  Gives up
+// (false) after kMmaPolls polls, or early once another role of the CTA has
+// given up (*abort != 0; null: never early).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const volatile int *abort)
+{
+    for (uint32_t polls = 0; !mbar_test(bar, parity);) {
+        if (++polls >= kMmaPolls) return false;
+        if (abort && (polls & 63u) == 0 && *abort) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void give_up(volatile int *abort, unsigned *err)
+{
+    *abort = 1;
+    atomicOr(err, 2u);
+}
+
+// Chunk-major layout of the network's [B][X][C] tensors: the channels of a
+// position are split into 16-byte rows of V elements (8 bf16 or 4 f32), and
+// row q of sample b holds those V channels for every position in turn.
+// Element (b, x, c) sits at ((b (C / V) + c / V) X + x) V + c % V.  A window
+// of consecutive positions of one row is contiguous (one bulk copy), and a
+// warp whose lanes take consecutive positions reads or writes 512 contiguous
+// bytes per row.
+__host__ __device__ __forceinline__ int64_t cm_index(int64_t b, int64_t x, int c, int C, int X, int V)
+{
+    return ((b * (C / V) + c / V) * X + x) * V + c % V;
+}
+
+// The bf16 weight copies of a layer (cout x 5 x cin) are stored in the order
+// a convolution CTA stages them, so that one bulk copy brings them in: W[co][j][ci]
+// at [K chunk r = j (cin / 8) + ci / 8][co][8].
+__host__ __device__ __forceinline__ int64_t wstage_index(int co, int j, int ci, int cout, int cin)
+{
+    return (int64_t(j * (cin / 8) + ci / 8) * cout + co) * 8 + ci % 8;
+}
+
+// Bulk copy (TMA engine, no tensor map) of `bytes` global -> shared, counted
+// against the transaction bytes of *bar; 16-byte aligned addresses, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Warp roles of the two tensor-core kernels: epilogue warps 0 .. E - 1 (warp w
+// may access TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31), warp E copies the
+// operands into shared memory, one thread of warp E + 1 issues the tensor-core
+// instructions.
+__host__ __device__ constexpr int role_threads(int epi_warps) { return 32 * (epi_warps + 2); }
+// Epilogue warps of the convolution: two per TMEM lane quarter (each takes half
+// the output channels) for 64 channels, one for fewer.
+__host__ __device__ constexpr int conv_epi_warps(int cout) { return cout >= 64 ? 8 : 4; }
+constexpr int kWgradEpiWarps = 4;
+// Operand stages in shared memory.
+constexpr int kConvStages = 4, kWgradStages = 4;
 
 // Epilogues of the convolution kernel.
 enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
@@ -162,52 +190,314 @@ enum { EPI_RELU_BF16 = 0, EPI_F32 = 1, EPI_MASK_BF16 = 2 };
 // Positions per tile of the convolution (the M of one tensor-core instruction).
 constexpr int kConvM = 128;
 
+// Fills stage rows 0 .. rows - 1 = positions x0 - halo .. of sample b of a
+// chunk-major operand (C channels, [chunk][row][8] in shared memory) with the
+// copy warp: lane 0 has the TMA engine copy the positions inside [0, X) of
+// each chunk (one bulk copy per chunk), the lanes write the others (`mode`:
+// zero, periodic image or nearest end value) with plain stores before it.
+// Every lane then arrives on *full (32 arrivals; lane 0 also adds the bulk
+// bytes to the phase's transaction count).
+template <int C>
+__device__ __forceinline__ void fill_rows(bf16 *dst, const bf16 *src, int b, int x0, int halo, int rows, int X,
+                                          int mode, int lane, uint64_t *full)
+{
+    constexpr int KC = C / 8;
+    const int first = x0 - halo;                                   // position of stage row 0
+    const int lo = first < 0 ? 0 : first, hi = first + rows > X ? X : first + rows;  // inside [lo, hi)
+    const int nl = lo - first, nr = first + rows - hi;            // rows before and after
+    for (int e = lane; e < (nl + nr) * KC; e += 32) {
+        const int r = e / KC, c = e % KC, p = r < nl ? r : (hi - first) + (r - nl);
+        bool inside;
+        const int x = wrap_pos(first + p, X, mode, &inside);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (inside) v = *reinterpret_cast<const uint4 *>(src + cm_index(b, x, c * 8, C, X, 8));
+        *reinterpret_cast<uint4 *>(dst + (c * rows + p) * 8) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // plain stores before the tensor cores' reads
+    __syncwarp();
+    if (lane == 0) {
+        const uint32_t bytes = uint32_t(hi - lo) * 16u;
+        mbar_arrive_tx(full, KC * bytes);
+        for (int c = 0; c < KC; ++c)
+            bulk_g2s(dst + (c * rows + nl) * 8, src + cm_index(b, lo, c * 8, C, X, 8), bytes, full);
+    } else {
+        mbar_arrive(full);
+    }
+}
+
+// The copy warp before it leaves: the bulk copies of its last fills (items
+// max(0, n - ns) .. n - 1 of stages full[item % ns]) have landed, so that none
+// writes to shared memory after the CTA has ended, whatever the other roles did.
+__device__ __forceinline__ void drain_fills(uint64_t *full, int ns, int n)
+{
+    for (int r = n - ns < 0 ? 0 : n - ns; r < n; ++r) mbar_wait(&full[r % ns], (r / ns) & 1, nullptr);
+}
+
 // y[b][x][co] = sum_{j, ci} w[co][j][ci] in[b][x + j - 2][ci] (+ bias), then
 //   EPI_RELU_BF16: relu, stored bf16;  EPI_F32: stored f32;
 //   EPI_MASK_BF16: the transposed convolution of the backward pass: input
 //     positions outside the sample are zero; at the two end positions of a
 //     replicate-padded sample edge[b][side][co] is added (edge_grad_kernel);
 //     then times (mask[b][x][co] > 0), stored bf16 (ReLU backward).
-// An implicit GEMM per (sample, 128-position tile): M = positions, N = COUT,
-// K = 5 CIN, on tcgen05.mma (M 128, N COUT, K 16 per instruction, issued by one
-// thread) with the FP32 accumulator in TMEM.  Both operands are K-major in the
-// no-swizzle canonical layout.  The input window of 132 positions is stored as
-// [chunk of 8 channels][position][8], so every 8 consecutive positions of a
-// chunk are one core matrix and tap j is the same descriptor moved by j rows
-// (16 bytes): A(j) = window rows j .. j + 127.  The weights are stored as
-// [K chunk = (j, 8 channels)][co][8].  Persistent CTAs load the layer's
-// weights once, then walk the items with a grid stride, the next item's window
-// copied in by cp.async while the tensor cores work on the current one; after
-// each item's products complete (tcgen05.commit on an mbarrier), thread
-// 32 w + l reads position 32 w + l of the tile (TMEM lane) and applies the
-// epilogue.  A wait on the products that gives up sets bit 1 of *err.
+// Tensors are chunk-major (cm_index; f32 output in rows of 4).
+// An implicit GEMM per (sample, 128-position tile) item: M = positions, N =
+// COUT, K = 5 CIN, on tcgen05.mma (M 128, N COUT, K 16 per instruction) with
+// the FP32 accumulator in TMEM.  Both operands are K-major in the no-swizzle
+// canonical layout.  The input window of 132 positions is stored as [chunk of
+// 8 channels][position][8] (a bulk copy per chunk), so every 8 consecutive
+// positions of a chunk are one core matrix and tap j is the same descriptor
+// moved by j rows (16 bytes): A(j) = window rows j .. j + 127.  The weights w
+// come in staging order (wstage_index: [K chunk = (j, 8 channels)][co][8]),
+// one bulk copy per persistent CTA, which then walks the items with a grid
+// stride as a pipeline: the copy warp
+// fills kConvStages window stages ahead of the tensor cores, the tensor cores
+// write two accumulators in turn, and the epilogue warps read one (position
+// 32 (w % 4) + lane of the tile, channel group w / 4) while the next item's
+// products go to the other.  The stages and accumulators hand over by
+// mbarriers (copies -> full, products -> empty and tfull, accumulator read ->
+// tempty).  A wait that gives up sets bit 1 of *err and ends the CTA's work.
 template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w,
-                                                   const float *__restrict__ bias, const int *__restrict__ periodic,
-                                                   int X, int B, void *__restrict__ out, const bf16 *__restrict__ mask,
-                                                   const float *__restrict__ edge, unsigned *__restrict__ err)
+__global__ void __launch_bounds__(role_threads(conv_epi_warps(COUT)), 2)
+    conv_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const float *__restrict__ bias,
+                const int *__restrict__ periodic, int X, int B, void *__restrict__ out, const bf16 *__restrict__ mask,
+                const float *__restrict__ edge, unsigned *__restrict__ err)
 {
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "padded channels, one tcgen05 N");
-    constexpr int KC = CIN / 8;                       // 8-channel chunks of a position
-    constexpr int ROWS = kConvM + kTaps - 1;          // window positions
-    constexpr int WCH = kTaps * KC;                   // weight chunks along K
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 64, "padded channels");
+    constexpr int EW = conv_epi_warps(COUT), CG = EW / 4;  // epilogue warps, channel groups
+    constexpr int NCG = COUT / CG;                        // channels of a group
+    constexpr int kCopy = EW, kMma = EW + 1;
+    constexpr int KC = CIN / 8;                           // 8-channel chunks of a position
+    constexpr int ROWS = kConvM + kTaps - 1;              // window positions
+    constexpr int WCH = kTaps * KC;                       // weight chunks along K
+    constexpr int NS = kConvStages;
     constexpr uint32_t ALBO = ROWS * 16, BLBO = COUT * 16;
-    constexpr uint32_t NCOL = COUT < 32 ? 32 : COUT;  // TMEM columns (a power of 2, at least 32)
-    constexpr int kWin = KC * ROWS * 8;               // bf16 per window stage
+    constexpr uint32_t ACOL = COUT < 32 ? 32 : COUT;      // TMEM columns of one accumulator (a power of 2)
+    constexpr int kWin = KC * ROWS * 8;                   // bf16 per window stage
     extern __shared__ __align__(128) unsigned char smem[];
-    bf16 *const ws = reinterpret_cast<bf16 *>(smem);  // [WCH][COUT][8]
-    bf16 *const win_base = ws + WCH * COUT * 8;       // two stages of [KC][ROWS][8]
-    __shared__ __align__(8) uint64_t mbar;
+    bf16 *const ws = reinterpret_cast<bf16 *>(smem);      // [WCH][COUT][8]
+    bf16 *const win_base = ws + WCH * COUT * 8;           // NS stages of [KC][ROWS][8]
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2], done, wbar;
+    __shared__ __align__(16) float s_bias[COUT];
     __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // W[co][j][ci] -> chunk r = j KC + ci / 8, row co
-    for (int e = t; e < COUT * WCH; e += blockDim.x) {
-        const int co = e / WCH, r = e % WCH;
-        *reinterpret_cast<uint4 *>(ws + (r * COUT + co) * 8) =
-            *reinterpret_cast<const uint4 *>(w + (size_t(co) * WCH + r) * 8);
+    if (t == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 32);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 32 * EW);
+        }
+        mbar_init(&done, 1);
+        mbar_init(&wbar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (t == 0) mbar_init1(&mbar);
-    if (warp == 0) {
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(2 * ACOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const int tiles = (X + kConvM - 1) / kConvM, nitems = B * tiles;
+    volatile int *const abort = &s_abort;
+    if (warp == kCopy) {
+        // the layer's weights (already in staging order, see wstage_index), then the
+        // window of item `it` into stage it % NS once the products of item it - NS have read it
+        if (lane == 0) {
+            constexpr uint32_t wbytes = uint32_t(WCH) * COUT * 16;
+            mbar_arrive_tx(&wbar, wbytes);
+            bulk_g2s(ws, w, wbytes, &wbar);
+        }
+        int it = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+            const int s = it % NS;
+            if (it >= NS && !mbar_wait(&empty[s], (it / NS - 1) & 1, abort)) {
+                give_up(abort, err);
+                break;
+            }
+            const int b = item / tiles;
+            const int mode = periodic[b] != 0 ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
+            fill_rows<CIN>(win_base + s * kWin, in, b, (item % tiles) * kConvM, 2, ROWS, X, mode, lane, &full[s]);
+        }
+        drain_fills(full, NS, it);
+        mbar_wait(&wbar, 0, nullptr);
+    } else if (warp == kMma) {
+        if (lane == 0) {
+            int it = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+                const int s = it % NS, a = it & 1;
+                if ((it == 0 && !mbar_wait(&wbar, 0, abort)) || !mbar_wait(&full[s], (it / NS) & 1, abort) ||
+                    (it >= 2 && !mbar_wait(&tempty[a], ((it >> 1) - 1) & 1, abort))) {
+                    give_up(abort, err);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t wa = smem_u32(win_base + s * kWin), wb = smem_u32(ws);
+                int step = 0;
+#pragma unroll
+                for (int j = 0; j < kTaps; ++j)
+#pragma unroll
+                    for (int kc = 0; kc < KC; kc += 2, ++step)
+                        umma_bf16(taddr + a * ACOL, umma_desc(wa + kc * ALBO + j * 16, ALBO, 128),
+                                  umma_desc(wb + (j * KC + kc) * BLBO, BLBO, 128), umma_idesc_bf16(kConvM, COUT),
+                                  step);
+                umma_commit(&empty[s]);
+                umma_commit(&tfull[a]);
+            }
+            // every product has landed before the accumulators are freed
+            umma_commit(&done);
+            if (!mbar_wait(&done, 0, nullptr)) give_up(abort, err);
+        }
+        __syncwarp();
+    } else {
+        const int m = 32 * (warp & 3) + lane;  // position of the tile = TMEM lane
+        const int c0 = (warp >> 2) * NCG;      // first channel of this thread's group
+        if (EPI != EPI_MASK_BF16) {
+            for (int e = t; e < COUT; e += 32 * EW) s_bias[e] = bias[e];
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");  // the epilogue warps only
+        }
+        int it = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+            const int a = it & 1, b = item / tiles, x = (item % tiles) * kConvM + m;
+            const bool valid = x < X;
+            // the ReLU mask of the backward pass, loaded while the tensor cores work
+            uint4 mk[EPI == EPI_MASK_BF16 ? NCG / 8 : 1];
+            if constexpr (EPI == EPI_MASK_BF16) {
+#pragma unroll
+                for (int v = 0; v < NCG / 8; ++v)
+                    mk[v] = valid ? *reinterpret_cast<const uint4 *>(mask + cm_index(b, x, c0 + 8 * v, COUT, X, 8))
+                                  : make_uint4(0u, 0u, 0u, 0u);
+            }
+            // warp-uniform: tcgen05.ld below is issued by whole warps
+            if (!__all_sync(0xffffffffu, mbar_wait(&tfull[a], (it >> 1) & 1, abort))) {
+                give_up(abort, err);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t r[NCG];
+#pragma unroll
+            for (int q = 0; q < NCG; q += 16)
+                tmem_ld16(r + q, taddr + (uint32_t(32 * (warp & 3)) << 16) + a * ACOL + c0 + q);
+            tmem_wait(r);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[a]);  // the tensor cores may now overwrite this accumulator
+            if (!valid) continue;
+            float v[NCG];
+#pragma unroll
+            for (int q = 0; q < NCG; ++q) v[q] = __uint_as_float(r[q]);
+            if constexpr (EPI != EPI_MASK_BF16) {
+#pragma unroll
+                for (int q = 0; q < NCG; q += 4) {
+                    const float4 bb = *reinterpret_cast<const float4 *>(s_bias + c0 + q);
+                    v[q] += bb.x;
+                    v[q + 1] += bb.y;
+                    v[q + 2] += bb.z;
+                    v[q + 3] += bb.w;
+                }
+            }
+            if constexpr (EPI == EPI_F32) {
+                float *o = static_cast<float *>(out);
+#pragma unroll
+                for (int q = 0; q < NCG; q += 4)
+                    *reinterpret_cast<float4 *>(o + cm_index(b, x, c0 + q, COUT, X, 4)) =
+                        make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                continue;
+            }
+            if constexpr (EPI == EPI_MASK_BF16) {
+                if (periodic[b] == 0 && (x == 0 || x == X - 1)) {
+                    const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + c0;
+#pragma unroll
+                    for (int q = 0; q < NCG; ++q) v[q] += eg[q];
+                }
+                const __nv_bfloat162 *mp = reinterpret_cast<const __nv_bfloat162 *>(mk);
+#pragma unroll
+                for (int q = 0; q < NCG / 2; ++q) {
+                    const __nv_bfloat162 mv = mp[q];
+                    v[2 * q] = __bfloat162float(mv.x) > 0.f ? v[2 * q] : 0.f;
+                    v[2 * q + 1] = __bfloat162float(mv.y) > 0.f ? v[2 * q + 1] : 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NCG; ++q) v[q] = fmaxf(v[q], 0.f);
+            }
+            bf16 *o = static_cast<bf16 *>(out);
+#pragma unroll
+            for (int q = 0; q < NCG; q += 8) {
+                uint4 pk;
+                __nv_bfloat162 *pp = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) pp[h] = __floats2bfloat162_rn(v[q + 2 * h], v[q + 2 * h + 1]);
+                *reinterpret_cast<uint4 *>(o + cm_index(b, x, c0 + q, COUT, X, 8)) = pk;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == kMma) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * ACOL) : "memory");
+    }
+}
+
+// Weight and bias gradients of one layer on the tensor cores:
+//   dW[co][j][ci] = sum_{b,x} dz[b][x][co] in[b][x + j - 2][ci],  db[co] = sum dz[b][x][co].
+// Per tap j a GEMM over K = positions, accumulated in TMEM over every (sample,
+// 128-position tile) item of the CTA: the operand with 64 channels is A (M =
+// 64), the other B (N = its channel count), D_j in TMEM columns [j N, (j + 1) N).
+// Both operands are MN-major in the no-swizzle canonical layout, staged as
+// [chunk of 8 channels][position][8] (a bulk copy per chunk of the
+// chunk-major tensors): 8 consecutive positions of a chunk are one core
+// matrix, the next 8 positions follow at 128 bytes (LBO) and the next chunk at
+// a whole chunk's rows (SBO); tap j of the input window is the same descriptor
+// moved by j rows.  An M = 64 accumulator keeps row m in TMEM lane
+// 32 (m / 16) + m % 16.  The copy warp fills kWgradStages stages ahead of the
+// tensor cores; a stage is free again once its products have completed and
+// the epilogue warps have added its dz tile into their bias-gradient partial
+// sums (empty: one commit + 128 arrivals).  Each CTA writes one partial
+// [co][5 cin] + [co]; reduce_partials_kernel sums the partials in a fixed
+// order.  A wait that gives up sets bit 1 of *err and ends the CTA's work.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(role_threads(kWgradEpiWarps), 1)
+    wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ in, const int *__restrict__ periodic, int X,
+                 int ntiles, float *__restrict__ partial, unsigned *__restrict__ err)
+{
+    static_assert((COUT == 64 && (CIN == 16 || CIN == 64)) || (COUT == 16 && CIN == 64), "layer shapes");
+    constexpr bool DZ_A = COUT == 64;           // A = dz (M = cout); else A = input window (M = cin)
+    constexpr int NB = DZ_A ? CIN : COUT;       // N of one tap
+    constexpr int KCD = COUT / 8, KCI = CIN / 8;
+    constexpr int RD = kConvM, RI = kConvM + kTaps - 1;  // staged positions of dz and of the input window
+    constexpr uint32_t SD = RD * 16, SI = RI * 16;       // chunk strides (bytes)
+    constexpr int NTOT = kTaps * NB, NS = kWgradStages;
+    constexpr int kCopy = kWgradEpiWarps, kMma = kWgradEpiWarps + 1;
+    constexpr uint32_t NCOL = NTOT <= 32 ? 32 : (NTOT <= 64 ? 64 : (NTOT <= 128 ? 128 : (NTOT <= 256 ? 256 : 512)));
+    constexpr int kStage = KCD * RD * 8 + KCI * RI * 8;  // bf16 per stage
+    // bias gradient: epilogue warp w sums dz chunks w and w + 4 (those below KCD),
+    // lane l the rows l, l + 32, l + 64, l + 96 of each tile
+    constexpr int DBC = KCD > 4 ? 2 : 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    bf16 *const stage_base = reinterpret_cast<bf16 *>(smem);
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], done;
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int tiles = (X + kConvM - 1) / kConvM;
+    if (t == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 64);
+            mbar_init(&empty[s], 1 + 32 * kWgradEpiWarps);
+        }
+        mbar_init(&done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
                      "r"(NCOL)
                      : "memory");
@@ -217,240 +507,148 @@ __global__ void __launch_bounds__(128) conv_kernel(const bf16 *__restrict__ in, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = s_taddr;
-    const int tiles = (X + kConvM - 1) / kConvM;
-    // cp.async of the input window of `item` into stage `st` (positions beyond the
-    // padding are zero-filled: source size 0, nothing is read)
-    auto stage_win = [&](int item, int st) {
-        bf16 *win = win_base + st * kWin;
-        const int b = item / tiles, x0 = (item % tiles) * kConvM;
-        const int mode = periodic[b] != 0 ? PAD_PERIODIC : (EPI == EPI_MASK_BF16 ? PAD_ZERO : PAD_REPLICATE);
-        for (int e = t; e < ROWS * KC; e += blockDim.x) {
-            const int p = e / KC, c = e % KC;
-            bool inside;
-            const int x = wrap_pos(x0 - 2 + p, X, mode, &inside);
-            const bf16 *src = inside ? in + (size_t(b) * X + x) * CIN + c * 8 : in;
-            cp_async16_zfill(win + (c * ROWS + p) * 8, src, inside ? 16u : 0u);
+    volatile int *const abort = &s_abort;
+    int nit = 0;  // items of this CTA
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x) ++nit;
+    if (warp == kCopy) {
+        // dz rows x0 .. x0 + 127 (zero beyond the sample), input window rows x0 - 2 ..
+        // x0 + 129 (periodic or replicated ends): two fills, 64 arrivals on full
+        int it = 0;
+        for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
+            const int s = it % NS;
+            if (it >= NS && !mbar_wait(&empty[s], (it / NS - 1) & 1, abort)) {
+                give_up(abort, err);
+                break;
+            }
+            const int b = item / tiles, x0 = (item % tiles) * kConvM;
+            bf16 *sdz = stage_base + s * kStage;
+            fill_rows<COUT>(sdz, dz, b, x0, 0, RD, X, PAD_ZERO, lane, &full[s]);
+            fill_rows<CIN>(sdz + KCD * RD * 8, in, b, x0, 2, RI, X, periodic[b] != 0 ? PAD_PERIODIC : PAD_REPLICATE,
+                           lane, &full[s]);
         }
-        cp_async_commit();
-    };
-    int st = 0;
-    uint32_t phase = 0;
-    bool failed = false;
-    if (blockIdx.x < B * tiles) stage_win(blockIdx.x, 0);
-    for (int item = blockIdx.x; item < B * tiles; item += gridDim.x, st ^= 1) {
-        const int b = item / tiles, x0 = (item % tiles) * kConvM;
-        const bool more = item + int(gridDim.x) < B * tiles;
-        if (more) stage_win(item + gridDim.x, st ^ 1);
-        if (more) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        // this thread's copies (and, the first time, its weight stores) before the
-        // tensor cores read them through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (t == 0) {
+        drain_fills(full, NS, it);
+    } else if (warp == kMma) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                       (uint32_t(NB >> 3) << 17) | (uint32_t(64 >> 4) << 24);  // MN-major A and B, M = 64
+            for (int it = 0; it < nit; ++it) {
+                const int s = it % NS;
+                if (!mbar_wait(&full[s], (it / NS) & 1, abort)) {
+                    give_up(abort, err);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ad = smem_u32(stage_base + s * kStage), ai = ad + KCD * RD * 16;
+#pragma unroll
+                for (int j = 0; j < kTaps; ++j)
+#pragma unroll
+                    for (int k0 = 0; k0 < kConvM; k0 += 16) {
+                        const uint64_t dd = umma_desc(ad + k0 * 16, 128, SD);
+                        const uint64_t di = umma_desc(ai + (k0 + j) * 16, 128, SI);
+                        umma_bf16(taddr + j * NB, DZ_A ? dd : di, DZ_A ? di : dd, idesc, it > 0 || k0 > 0);
+                    }
+                umma_commit(&empty[s]);
+            }
+            umma_commit(&done);
+            if (!mbar_wait(&done, 0, nullptr)) give_up(abort, err);
+        }
+        __syncwarp();
+    } else {
+        float db[DBC][8];
+#pragma unroll
+        for (int d = 0; d < DBC; ++d)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) db[d][k] = 0.f;
+        bool ok = true;
+        for (int it = 0; it < nit; ++it) {
+            const int s = it % NS;
+            if (!mbar_wait(&full[s], (it / NS) & 1, abort)) {
+                give_up(abort, err);
+                ok = false;
+                break;
+            }
+            const bf16 *sdz = stage_base + s * kStage;
+#pragma unroll
+            for (int d = 0; d < DBC; ++d) {
+                const int c = warp + 4 * d;
+                if (c < KCD)
+#pragma unroll
+                    for (int r = 0; r < RD; r += 32) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(sdz + (c * RD + r + lane) * 8);
+                        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            db[d][2 * k] += __bfloat162float(h[k].x);
+                            db[d][2 * k + 1] += __bfloat162float(h[k].y);
+                        }
+                    }
+            }
+            mbar_arrive(&empty[s]);
+        }
+        // every epilogue warp has read its last dz tile before the stage buffers
+        // are reused below (also one that gave up)
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kWgradEpiWarps) : "memory");
+        // the lane sums of each column, in a fixed order
+#pragma unroll
+        for (int d = 0; d < DBC; ++d)
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) db[d][k] += __shfl_xor_sync(0xffffffffu, db[d][k], o);
+        // the accumulators once every product of the CTA has landed
+        if (!__all_sync(0xffffffffu, ok && mbar_wait(&done, 0, abort))) {  // warp-uniform, as tcgen05.ld
+            if (ok) give_up(abort, err);
+            ok = false;
+        }
+        if (ok) {
+            // the accumulators go through shared memory (the idle stage buffers) as
+            // [co][5 cin] rows padded by one word, then out in coalesced rows
+            constexpr int RW = kTaps * CIN, RP = RW + 1;
+            static_assert(COUT * RP * 4 <= NS * kStage * 2, "transpose buffer");
+            float *T = reinterpret_cast<float *>(smem);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the tensor cores' reads
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t wa = smem_u32(win_base + st * kWin), wb = smem_u32(ws);
-            int step = 0;
+            // lane l < 16 of warp w holds row m = 16 w + l of every D_j
+            const int m = 16 * warp + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < NTOT; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(r, taddr + (uint32_t(warp * 32) << 16) + c0);
+                tmem_wait(r);
+                if (lane < 16) {
 #pragma unroll
-            for (int j = 0; j < kTaps; ++j)
-#pragma unroll
-                for (int kc = 0; kc < KC; kc += 2, ++step)
-                    umma_bf16(taddr, umma_desc(wa + kc * ALBO + j * 16, ALBO, 128),
-                              umma_desc(wb + (j * KC + kc) * BLBO, BLBO, 128), umma_idesc_bf16(kConvM, COUT), step);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar))
-                         : "memory");
-        }
-        // the thread's position and, for the backward pass, its ReLU mask (loaded
-        // while the tensor cores work)
-        const int m = warp * 32 + lane, x = x0 + m;
-        const bool valid = x < X;
-        uint4 mk[EPI == EPI_MASK_BF16 ? COUT / 8 : 1];
-        if constexpr (EPI == EPI_MASK_BF16) {
-#pragma unroll
-            for (int v = 0; v < COUT / 8; ++v)
-                mk[v] = valid ? *reinterpret_cast<const uint4 *>(mask + (size_t(b) * X + x) * COUT + v * 8)
-                              : make_uint4(0u, 0u, 0u, 0u);
-        }
-        uint32_t polls = 0;
-        while (!mbar_test(&mbar, phase) && ++polls < kMmaPolls) {
-        }
-        if (__syncthreads_or(polls >= kMmaPolls)) {
-            if (t == 0) atomicOr(err, 2u);
-            failed = true;
-            break;
-        }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool per = periodic[b] != 0;
-        const size_t o = (size_t(b) * X + (valid ? x : 0)) * COUT;
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-            float v[16];
-            tmem_ld16(v, taddr + (uint32_t(warp * 32) << 16) + c0);
-            if (!valid) continue;
-            if (EPI != EPI_MASK_BF16) {
-#pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    const float4 bb = *reinterpret_cast<const float4 *>(bias + c0 + q);
-                    v[q] += bb.x;
-                    v[q + 1] += bb.y;
-                    v[q + 2] += bb.z;
-                    v[q + 3] += bb.w;
+                    for (int q = 0; q < 16; ++q) {
+                        const int col = c0 + q, j = col / NB, n = col % NB;  // tap j, channel n of B
+                        // DZ_A: m = co, n = ci; else m = ci, n = co
+                        const int co = DZ_A ? m : n, ci = DZ_A ? n : m;
+                        T[co * RP + j * CIN + ci] = nit > 0 ? __uint_as_float(r[q]) : 0.f;
+                    }
                 }
             }
-            if (EPI == EPI_F32) {
-                float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(out) + o + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                continue;
-            }
-            if (EPI == EPI_MASK_BF16) {
-                if (!per && (x == 0 || x == X - 1)) {
-                    const float *eg = edge + (size_t(b) * 2 + (x != 0)) * COUT + c0;
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] += eg[q];
-                }
-                const __nv_bfloat162 *mp = reinterpret_cast<const __nv_bfloat162 *>(&mk[c0 / 8]);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const __nv_bfloat162 mv = mp[q];
-                    v[2 * q] = __bfloat162float(mv.x) > 0.f ? v[2 * q] : 0.f;
-                    v[2 * q + 1] = __bfloat162float(mv.y) > 0.f ? v[2 * q + 1] : 0.f;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
-            }
-            uint4 pk[2];
-            __nv_bfloat162 *pp = reinterpret_cast<__nv_bfloat162 *>(pk);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) pp[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            uint4 *dst = reinterpret_cast<uint4 *>(static_cast<bf16 *>(out) + o + c0);
-            dst[0] = pk[0];
-            dst[1] = pk[1];
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // TMEM and this window stage are reused by later items
-    }
-    cp_async_wait<0>();
-    if (failed) {  // let products still in flight land before their TMEM is freed
-        uint32_t polls = 0;
-        while (!mbar_test(&mbar, phase) && ++polls < kMmaPolls) {
+        // every epilogue warp, also one that gave up (the transpose buffer is shared)
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kWgradEpiWarps) : "memory");
+        if (ok) {
+            constexpr int RW = kTaps * CIN, RP = RW + 1;
+            const float *T = reinterpret_cast<const float *>(smem);
+            float *P = partial + size_t(blockIdx.x) * (COUT * RW + COUT);
+            for (int e = t; e < COUT * RW; e += 32 * kWgradEpiWarps) P[e] = T[(e / RW) * RP + e % RW];
+            if (lane == 0)
+#pragma unroll
+                for (int d = 0; d < DBC; ++d) {
+                    const int c = warp + 4 * d;
+                    if (c < KCD)
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) P[size_t(COUT) * RW + 8 * c + k] = db[d][k];
+                }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(NCOL) : "memory");
-}
-
-// Weight and bias gradients of one layer:
-//   dW[co][j][ci] = sum_{b,x} dz[b][x][co] in[b][x + j - 2][ci],  db[co] = sum dz[b][x][co],
-// a GEMM with M = COUT, N = 5 CIN, K = positions.  Each CTA accumulates over
-// its share of the (sample, tile) items and writes a partial;
-// reduce_partials_kernel sums the partials in a fixed order.  The dz tile and
-// the input window are staged channels-last by 16-byte cp.async copies, two
-// items deep; the transposed operands (K = positions contiguous) come from
-// ldmatrix .trans.
-// 8 warps: warp (mw, nw) holds couts [16 mw, 16 mw + 16) and NTW of the N/8
-// column tiles.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256, QL_WGRAD_MINBLOCKS) wgrad_kernel(const bf16 *__restrict__ dz, const bf16 *__restrict__ in,
-                                                    const int *__restrict__ periodic, int X, int ntiles,
-                                                    float *__restrict__ partial)
-{
-    static_assert(CIN % 8 == 0 && COUT % 16 == 0, "padded channels");
-    constexpr int N = kTaps * CIN;
-    constexpr int MT = COUT / 16;            // m tiles
-    constexpr int NT = N / 8;                // n tiles
-    constexpr int NW = 8 / MT;               // warps along N
-    constexpr int NTW = (NT + NW - 1) / NW;  // n tiles per warp
-    constexpr int DS = COUT + 8, IS = CIN + 8;  // smem row strides (bf16)
-    extern __shared__ __align__(16) unsigned char smem[];
-    // two stages of [kTM][DS] dz tile (positions x couts) and [kTM + 4][IS]
-    // input window (positions x cins): the next item is copied in while the
-    // current one is multiplied
-    constexpr int kStage = kTM * DS + (kTM + 4) * IS;
-    bf16 *const stage_base = reinterpret_cast<bf16 *>(smem);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, tg = lane & 3;
-    const int t8 = lane & 7, mat = lane >> 3;
-    const int mw = warp % MT, nw = warp / MT;
-    float acc[NTW][4];
-#pragma unroll
-    for (int n = 0; n < NTW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    float db = 0.f;
-    const int tiles = (X + kTM - 1) / kTM;
-    // cp.async of item `item` into stage `st`: positions outside the sample (and
-    // outside the padding) are zero-filled (source size 0, nothing is read)
-    auto stage_item = [&](int item, int st) {
-        bf16 *sdz = stage_base + st * kStage, *sin = sdz + kTM * DS;
-        const int b = item / tiles, x0 = (item % tiles) * kTM;
-        const int mode = periodic[b] != 0 ? PAD_PERIODIC : PAD_REPLICATE;
-        for (int e = t; e < kTM * (COUT / 8); e += blockDim.x) {
-            const int p = e / (COUT / 8), v = e % (COUT / 8);
-            const int x = x0 + p;
-            const bf16 *src = x < X ? dz + (size_t(b) * X + x) * COUT + v * 8 : dz;
-            cp_async16_zfill(sdz + p * DS + v * 8, src, x < X ? 16u : 0u);
-        }
-        for (int e = t; e < (kTM + 4) * (CIN / 8); e += blockDim.x) {
-            const int p = e / (CIN / 8), v = e % (CIN / 8);
-            bool inside;
-            const int x = wrap_pos(x0 - 2 + p, X, mode, &inside);
-            const bf16 *src = inside ? in + (size_t(b) * X + x) * CIN + v * 8 : in;
-            cp_async16_zfill(sin + p * IS + v * 8, src, inside ? 16u : 0u);
-        }
-        cp_async_commit();
-    };
-    int st = 0;
-    if (blockIdx.x < ntiles) stage_item(blockIdx.x, 0);
-    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, st ^= 1) {
-        const bool more = item + int(gridDim.x) < ntiles;
-        if (more) stage_item(item + gridDim.x, st ^ 1);
-        if (more) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        __syncthreads();
-        const bf16 *sdz = stage_base + st * kStage, *sin = sdz + kTM * DS;
-        // bias gradient: thread t < COUT sums column t of the dz tile
-        if (t < COUT) {
-            float s = 0.f;
-            for (int p = 0; p < kTM; ++p) s += __bfloat162float(sdz[p * DS + t]);
-            db += s;
-        }
-#pragma unroll
-        for (int k0 = 0; k0 < kTM; k0 += 16) {
-            // A[m = co][k = position] = sdz[k0 + k][16 mw + m]: transposed 8x8 blocks
-            // (co 0-7 | 8-15) x (positions 0-7 | 8-15)
-            uint32_t a[4];
-            ldsm_x4_trans(a, sdz + (k0 + (mat >> 1) * 8 + t8) * DS + 16 * mw + (mat & 1) * 8);
-#pragma unroll
-            for (int n = 0; n < NTW; ++n) {
-                const int nt = nw * NTW + n;
-                if (nt >= NT) break;
-                // column tile nt: tap j, cins [ci0, ci0 + 8); B[k][c] = in[x0 + k0 + k + j - 2][ci0 + c]
-                // = sin[k0 + k + j][ci0 + c]: transposed blocks for k 0-7 and 8-15 (lanes 0-15)
-                const int j = (nt * 8) / CIN, ci0 = (nt * 8) % CIN;
-                uint32_t bb[2];
-                ldsm_x2_trans(bb, sin + (k0 + (mat & 1) * 8 + t8 + j) * IS + ci0);
-                mma16816(acc[n], a, bb);
-            }
-        }
-        __syncthreads();  // this stage is refilled two items later
+    if (warp == kMma) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(NCOL) : "memory");
     }
-    // partial[cta][co][col] with col = j CIN + ci, then the bias partials
-    float *P = partial + size_t(blockIdx.x) * (COUT * N + COUT);
-#pragma unroll
-    for (int n = 0; n < NTW; ++n) {
-        const int nt = nw * NTW + n;
-        if (nt >= NT) break;
-        const int col = nt * 8 + 2 * tg;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int co = 16 * mw + g + 8 * h;
-            P[co * N + col] = acc[n][2 * h];
-            P[co * N + col + 1] = acc[n][2 * h + 1];
-        }
-    }
-    if (t < COUT) P[COUT * N + t] = db;
 }
 
 // Replicate padding feeds the end values a[0] and a[X-1] of a sample into the
@@ -458,7 +656,7 @@ __global__ void __launch_bounds__(256, QL_WGRAD_MINBLOCKS) wgrad_kernel(const bf
 // transposed convolution lacks:
 //   left  (x = 0):     sum_co (W0 + W1)[co][ci] dz[0][co] + W0[co][ci] dz[1][co]
 //   right (x = X - 1): sum_co (W3 + W4)[co][ci] dz[X-1][co] + W4[co][ci] dz[X-2][co]
-// w is the forward layer's W[co][j][ci].  One block per side, kEdgeSamples
+// w is the forward layer's W[co][j][ci] (staging order); dz is chunk-major.  One block per side, kEdgeSamples
 // samples and kEdgeChannels input channels: the two weight combinations of
 // that side and channel range (the same for every sample) and the samples' end
 // gradients are staged in shared memory once.
@@ -475,8 +673,9 @@ __global__ void __launch_bounds__(256) edge_grad_kernel(const bf16 *__restrict__
         const int co = e / kEdgeChannels, cc = e - co * kEdgeChannels, ci = c0 + cc;
         float a = 0.f, n = 0.f;
         if (ci < cin) {
-            a = __bfloat162float(w[(co * kTaps + ja) * cin + ci]) + __bfloat162float(w[(co * kTaps + jb) * cin + ci]);
-            n = __bfloat162float(w[(co * kTaps + jn) * cin + ci]);
+            a = __bfloat162float(w[wstage_index(co, ja, ci, cout, cin)]) +
+                __bfloat162float(w[wstage_index(co, jb, ci, cout, cin)]);
+            n = __bfloat162float(w[wstage_index(co, jn, ci, cout, cin)]);
         }
         s_a[co][cc] = a;
         s_n[co][cc] = n;
@@ -485,8 +684,8 @@ __global__ void __launch_bounds__(256) edge_grad_kernel(const bf16 *__restrict__
         const int sm = e / cout, co = e - sm * cout, b = b0 + sm;
         float d0 = 0.f, d1 = 0.f;
         if (b < B) {
-            d0 = __bfloat162float(dz[(size_t(b) * X + (side ? X - 1 : 0)) * cout + co]);
-            d1 = __bfloat162float(dz[(size_t(b) * X + (side ? X - 2 : 1)) * cout + co]);
+            d0 = __bfloat162float(dz[cm_index(b, side ? X - 1 : 0, co, cout, X, 8)]);
+            d1 = __bfloat162float(dz[cm_index(b, side ? X - 2 : 1, co, cout, X, 8)]);
         }
         s_d0[sm][co] = d0;
         s_d1[sm][co] = d1;
@@ -539,18 +738,36 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
     }
 }
 
-// Input features (f32 [B][X][cin_real]) -> normalised bf16 [B][X][CINP].
-__global__ void pack_input_kernel(const float *__restrict__ x, int64_t n, int cin, int cinp,
+// Network inputs are padded to this many channels (two 16-byte rows).
+constexpr int kInPad = 16;
+
+// Position pos = b X + p of the input: sample k's features (f32 [n][X][cin],
+// cin <= kInPad) normalised, stored bf16 chunk-major with kInPad channels.
+__device__ __forceinline__ void pack_position(const float *__restrict__ x, int64_t k, int64_t b, int p, int X,
+                                              int cin, const float *__restrict__ shift,
+                                              const float *__restrict__ inv_scale, bf16 *__restrict__ out)
+{
+    float v[kInPad];
+#pragma unroll
+    for (int c = 0; c < kInPad; ++c) v[c] = c < cin ? (x[(k * X + p) * cin + c] - shift[c]) * inv_scale[c] : 0.f;
+#pragma unroll
+    for (int q = 0; q < kInPad / 8; ++q) {
+        uint4 pk;
+        __nv_bfloat162 *pp = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) pp[h] = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+        *reinterpret_cast<uint4 *>(out + cm_index(b, p, 8 * q, kInPad, X, 8)) = pk;
+    }
+}
+
+// Input features (f32 [B][X][cin]) -> the network's input; one thread per position.
+__global__ void pack_input_kernel(const float *__restrict__ x, int64_t npos, int X, int cin,
                                   const float *__restrict__ shift, const float *__restrict__ inv_scale,
                                   bf16 *__restrict__ out)
 {
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= n * cinp) return;
-    const int64_t pos = e / cinp;
-    const int c = int(e % cinp);
-    float v = 0.f;
-    if (c < cin) v = (x[pos * cin + c] - shift[c]) * inv_scale[c];
-    out[e] = __float2bfloat16(v);
+    const int64_t pos = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    pack_position(x, pos / X, pos / X, int(pos % X), X, cin, shift, inv_scale, out);
 }
 
 // The same for the mini-batch idx[0..B) = perm[step B ..] (step read from the
@@ -559,7 +776,7 @@ __global__ void pack_input_kernel(const float *__restrict__ x, int64_t n, int ci
 // [0, n) sets *bad and reads sample 0 instead, so nothing is read out of bounds.
 __global__ void pack_gather_kernel(const float *__restrict__ x, const int32_t *__restrict__ per,
                                    const int32_t *__restrict__ perm, const int *__restrict__ step, int64_t n, int B,
-                                   int X, int cin, int cinp, const float *__restrict__ shift,
+                                   int X, int cin, const float *__restrict__ shift,
                                    const float *__restrict__ inv_scale, bf16 *__restrict__ out,
                                    int32_t *__restrict__ perb, unsigned *__restrict__ bad)
 {
@@ -571,65 +788,87 @@ __global__ void pack_gather_kernel(const float *__restrict__ x, const int32_t *_
         if (!ok) atomicOr(bad, 1u);
         perb[e] = per[ok ? k : 0];
     }
-    if (e >= int64_t(B) * X * cinp) return;
-    const int64_t pos = e / cinp;
-    const int c = int(e % cinp);
-    const int64_t b = pos / X;
+    if (e >= int64_t(B) * X) return;
+    const int64_t b = e / X;
     int64_t k = idx[b];
     if (k < 0 || k >= n) k = 0;
-    float v = 0.f;
-    if (c < cin) v = (x[(k * X + (pos - b * X)) * cin + c] - shift[c]) * inv_scale[c];
-    out[e] = __float2bfloat16(v);
+    pack_position(x, k, b, int(e % X), X, cin, shift, inv_scale, out);
 }
 
-// Mean squared error between prediction (f32 [B][X][COUTP], first cout used) and
-// target / out_scale; writes dL/dpred (bf16, padded channels zero) and
-// per-block partial sums of the squared error.
+// Output channels of the last layer as computed: four 16-byte rows of 4 f32 in
+// the prediction, two rows of 8 bf16 in its gradient.
+constexpr int kOutPad = 16;
+// Blocks (and loss partials) of mse_kernel for npos positions.
+inline unsigned mse_blocks(int64_t npos) { return unsigned((npos + 255) / 256); }
+
+// Mean squared error between prediction (f32 chunk-major in rows of 4, kOutPad
+// channels, first cout used) and target / out_scale; writes dL/dpred (bf16
+// chunk-major, padded channels zero) and per-block partial sums of the squared
+// error (256 threads, one per position).
 // y rows of the batch: y[b] directly, or y[idx[b]] of the whole data set
 // (idx already checked by pack_gather_kernel; X positions per sample).
-__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ y, const int32_t *__restrict__ idx,
-                           const int *__restrict__ step, int X, int64_t npos, int cout, int coutp,
-                           const float *__restrict__ inv_out_scale, float grad_scale, bf16 *__restrict__ dpred,
-                           float *__restrict__ partial)
+__global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ pred, const float *__restrict__ y,
+                                                  const int32_t *__restrict__ idx, const int *__restrict__ step, int X,
+                                                  int64_t npos, int cout, const float *__restrict__ inv_out_scale,
+                                                  float grad_scale, bf16 *__restrict__ dpred,
+                                                  float *__restrict__ partial)
 {
     // step (device, may be null): the batch is idx[step * B ..] of a training run's permutation
     if (idx && step) idx += int64_t(*step) * (npos / X);
-    __shared__ float red[256];
-    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    __shared__ float red[8];
+    const int64_t pos = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     float se = 0.f;
-    if (e < npos * coutp) {
-        const int64_t pos = e / coutp;
-        const int c = int(e % coutp);
-        float d = 0.f;
-        if (c < cout) {
-            int64_t row = pos;
-            if (idx) {
-                const int64_t b = pos / X;
-                row = int64_t(idx[b]) * X + (pos - b * X);
+    if (pos < npos) {
+        const int64_t b = pos / X;
+        const int p = int(pos % X);
+        const int64_t row = (idx ? int64_t(idx[b]) : b) * X + p;
+        float g[kOutPad];
+#pragma unroll
+        for (int q = 0; q < kOutPad / 4; ++q) {
+            const float4 pr = *reinterpret_cast<const float4 *>(pred + cm_index(b, p, 4 * q, kOutPad, X, 4));
+            const float pv[4] = {pr.x, pr.y, pr.z, pr.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = 4 * q + k;
+                float d = 0.f;
+                if (c < cout) {
+                    d = pv[k] - y[row * cout + c] * inv_out_scale[c];
+                    se += d * d;
+                }
+                g[c] = grad_scale * d;
             }
-            d = pred[e] - y[row * cout + c] * inv_out_scale[c];
-            se = d * d;
         }
-        dpred[e] = __float2bfloat16(grad_scale * d);
+#pragma unroll
+        for (int q = 0; q < kOutPad / 8; ++q) {
+            uint4 pk;
+            __nv_bfloat162 *pp = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) pp[h] = __floats2bfloat162_rn(g[8 * q + 2 * h], g[8 * q + 2 * h + 1]);
+            *reinterpret_cast<uint4 *>(dpred + cm_index(b, p, 8 * q, kOutPad, X, 8)) = pk;
+        }
     }
-    red[threadIdx.x] = se;
+    // block sum in a fixed order: lanes by shuffles, then the 8 warps in turn
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = se;
     __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        partial[blockIdx.x] = t;
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// Prediction in physical units: y[pos][c] = pred[pos][c] * out_scale[c], c < cout.
-__global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npos, int cout, int coutp,
+// Prediction in physical units: y[b][x][c] = pred(b, x, c) * out_scale[c], c < cout
+// (pred chunk-major f32 in rows of 4, coutp channels).
+__global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npos, int X, int cout, int coutp,
                                      const float *__restrict__ out_scale, float *__restrict__ y)
 {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= npos * cout) return;
     const int64_t pos = e / cout;
     const int c = int(e % cout);
-    y[e] = pred[pos * coutp + c] * out_scale[c];
+    y[e] = pred[cm_index(pos / X, pos % X, c, coutp, X, 4)] * out_scale[c];
 }
 
 // Mean loss of one batch from the per-block partial sums of mse_kernel, summed
@@ -672,7 +911,7 @@ struct AdamArgs {
     const float *lr_arr, *c1_arr, *c2_arr;
     // bf16 copies written in the same pass (nl = 0: none): layer l's W[co][j][ci]
     // at woff[l] (cout[l] x 5 x cin[l]) into w16 and, tap-flipped and
-    // transposed, into wt16 at the same offset
+    // transposed, into wt16 at the same offset (both in staging order)
     bf16 *w16, *wt16;
     int nl;
     int64_t woff[kAdamLayers];
@@ -702,14 +941,15 @@ __global__ void adam_kernel(AdamArgs a)
         if (e >= 0 && e < int64_t(cout_) * kTaps * ci_) {
             const int co = int(e / (kTaps * ci_)), j = int((e / ci_) % kTaps), ci = int(e % ci_);
             const bf16 b = __float2bfloat16(p);
-            a.w16[i] = b;
-            a.wt16[a.woff[l] + (int64_t(ci) * kTaps + (kTaps - 1 - j)) * cout_ + co] = b;
+            a.w16[a.woff[l] + wstage_index(co, j, ci, cout_, ci_)] = b;
+            a.wt16[a.woff[l] + wstage_index(ci, kTaps - 1 - j, co, ci_, cout_)] = b;
             break;
         }
     }
 }
 
-// bf16 copies of one layer's weights: w[co][j][ci] and wt[ci][4 - j][co].
+// bf16 copies of one layer's weights, in staging order (wstage_index): w =
+// W[co][j][ci] and wt = the transposed convolution's W[ci][4 - j][co].
 __global__ void cast_weights_kernel(const float *__restrict__ wf, int cout, int cin, bf16 *__restrict__ w,
                                     bf16 *__restrict__ wt)
 {
@@ -717,8 +957,8 @@ __global__ void cast_weights_kernel(const float *__restrict__ wf, int cout, int 
     if (e >= cout * kTaps * cin) return;
     const int co = e / (kTaps * cin), j = (e / cin) % kTaps, ci = e % cin;
     const bf16 v = __float2bfloat16(wf[e]);
-    w[e] = v;
-    wt[(ci * kTaps + (kTaps - 1 - j)) * cout + co] = v;
+    w[wstage_index(co, j, ci, cout, cin)] = v;
+    wt[wstage_index(ci, kTaps - 1 - j, co, cin, cout)] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -728,27 +968,61 @@ struct Layer {
     int64_t woff, boff;  // offsets of W [cout][5][cin] and bias [cout] in the f32 parameter vector
 };
 
-// Persistent grid of the convolution: the CTAs an SM holds by shared memory,
-// at most as many as its 512 TMEM columns give accumulators (each CTA allocates
-// its columns for the whole launch).
+// CTAs per SM of a tensor-core kernel: as many as shared memory and the 512
+// TMEM columns of an SM hold (each CTA allocates tmem_cols for the whole
+// launch), at most cap.  Sets the kernel's shared-memory limit on the current
+// device the first time, and remembers the result per device in the kernel's
+// own cache ({CTAs per SM, SMs} + 1; 0: not known yet).
+typedef std::atomic<int> ShapeCache[kMaxDevices][2];
+template <typename K>
+cudaError_t ctas_per_sm(K k, int threads, size_t smem, int tmem_cols, int cap, ShapeCache &cache, int *per_sm,
+                        int *sms)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices && cache[dev][0].load() > 0) {
+        *per_sm = cache[dev][0].load() - 1;
+        *sms = cache[dev][1].load() - 1;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    // all of the SM's unified L1 / shared memory as shared memory, so that the
+    // occupancy below counts every CTA the SM's shared memory can hold
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    int occ = 0, n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *per_sm = std::max(1, std::min(std::min(occ, 512 / tmem_cols), cap));
+    *sms = std::max(1, n);
+    if (dev >= 0 && dev < kMaxDevices) {
+        cache[dev][1].store(*sms + 1);
+        cache[dev][0].store(*per_sm + 1);
+    }
+    return cudaSuccess;
+}
+
+// Persistent grid of the convolution: every CTA an SM holds, at most one per item.
 template <int CIN, int COUT, int EPI>
 cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const int *per, int B, int X, void *out,
                         const bf16 *mask, const float *edge, unsigned *err, cudaStream_t s)
 {
-    constexpr size_t smem = 16 * (size_t(kTaps) * (CIN / 8) * COUT + 2 * size_t(CIN / 8) * (kConvM + kTaps - 1));
-    constexpr int ncol = COUT < 32 ? 32 : COUT;
+    constexpr size_t smem =
+        16 * (size_t(kTaps) * (CIN / 8) * COUT + size_t(kConvStages) * (CIN / 8) * (kConvM + kTaps - 1));
+    constexpr int ncol = 2 * (COUT < 32 ? 32 : COUT);
     auto k = conv_kernel<CIN, COUT, EPI>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    constexpr int threads = role_threads(conv_epi_warps(COUT));
+    static ShapeCache cache;
+    int per_sm = 0, sms = 0;
+    cudaError_t e = ctas_per_sm(k, threads, smem, ncol, 8, cache, &per_sm, &sms);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
-    if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, 512 / ncol));
     const int items = B * ((X + kConvM - 1) / kConvM);
-    const int grid = std::max(1, std::min(items, std::max(1, sms) * per_sm));
-    k<<<grid, 128, smem, s>>>(in, w, bias, per, X, B, out, mask, edge, err);
+    const int grid = std::max(1, std::min(items, sms * per_sm));
+    k<<<grid, threads, smem, s>>>(in, w, bias, per, X, B, out, mask, edge, err);
     return cudaGetLastError();
 }
 
@@ -767,25 +1041,36 @@ cudaError_t conv_any(int cin, int cout, int epi, const bf16 *in, const bf16 *w, 
     return cudaErrorInvalidValue;
 }
 
+// The weight-gradient grid: CTAs per SM by shared memory and by the TMEM
+// columns of their five accumulators, at most 2 (the partial buffer holds
+// 2 x SMs parts); *parts receives the grid, the number of partials to sum.
 template <int CIN, int COUT>
-cudaError_t wgrad_launch(const bf16 *dz, const bf16 *in, const int *per, int B, int X, int grid, float *partial,
-                         cudaStream_t s)
+cudaError_t wgrad_launch(const bf16 *dz, const bf16 *in, const int *per, int B, int X, int sms, float *partial,
+                         unsigned *err, int *parts, cudaStream_t s)
 {
-    constexpr size_t smem = 2 * sizeof(bf16) * (kTM * (COUT + 8) + (kTM + 4) * (CIN + 8));
+    constexpr int RD = kConvM, RI = kConvM + kTaps - 1;
+    constexpr size_t smem = size_t(kWgradStages) * 16 * (size_t(COUT / 8) * RD + size_t(CIN / 8) * RI);
+    constexpr int ntot = kTaps * (COUT == 64 ? CIN : COUT);
+    constexpr int ncol = ntot <= 32 ? 32 : (ntot <= 64 ? 64 : (ntot <= 128 ? 128 : (ntot <= 256 ? 256 : 512)));
     auto k = wgrad_kernel<CIN, COUT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    constexpr int threads = role_threads(kWgradEpiWarps);
+    static ShapeCache cache;
+    int per_sm = 0, dev_sms = 0;
+    cudaError_t e = ctas_per_sm(k, threads, smem, ncol, 2, cache, &per_sm, &dev_sms);
     if (e != cudaSuccess) return e;
-    const int ntiles = B * ((X + kTM - 1) / kTM);
-    k<<<grid, 256, smem, s>>>(dz, in, per, X, ntiles, partial);
+    const int ntiles = B * ((X + kConvM - 1) / kConvM);
+    const int grid = std::max(1, std::min(ntiles, std::max(1, sms) * per_sm));
+    *parts = grid;
+    k<<<grid, threads, smem, s>>>(dz, in, per, X, ntiles, partial, err);
     return cudaGetLastError();
 }
 
-cudaError_t wgrad_any(int cin, int cout, const bf16 *dz, const bf16 *in, const int *per, int B, int X, int grid,
-                      float *partial, cudaStream_t s)
+cudaError_t wgrad_any(int cin, int cout, const bf16 *dz, const bf16 *in, const int *per, int B, int X, int sms,
+                      float *partial, unsigned *err, int *parts, cudaStream_t s)
 {
-    if (cin == 16 && cout == 64) return wgrad_launch<16, 64>(dz, in, per, B, X, grid, partial, s);
-    if (cin == 64 && cout == 64) return wgrad_launch<64, 64>(dz, in, per, B, X, grid, partial, s);
-    if (cin == 64 && cout == 16) return wgrad_launch<64, 16>(dz, in, per, B, X, grid, partial, s);
+    if (cin == 16 && cout == 64) return wgrad_launch<16, 64>(dz, in, per, B, X, sms, partial, err, parts, s);
+    if (cin == 64 && cout == 64) return wgrad_launch<64, 64>(dz, in, per, B, X, sms, partial, err, parts, s);
+    if (cin == 64 && cout == 16) return wgrad_launch<64, 16>(dz, in, per, B, X, sms, partial, err, parts, s);
     return cudaErrorInvalidValue;
 }
 
@@ -822,7 +1107,7 @@ struct ql_closure {
     int *d_step = nullptr;
     float *d_sched = nullptr;
     int64_t sched_cap = 0;
-    int wgrid = 0;
+    int sms = 0;  // SMs of the device; the weight-gradient partial buffer holds 2 x sms parts
     int64_t step = 0;
     std::string err;
 };
@@ -904,9 +1189,8 @@ static ql_status forward(ql_closure *c, const int *per, int B)
 static ql_status pack(ql_closure *c, const float *x, int B)
 {
     const int64_t npos = int64_t(B) * c->d.positions;
-    const int cinp = c->layers[0].cin;
-    pack_input_kernel<<<unsigned((npos * cinp + 255) / 256), 256, 0, c->stream>>>(
-        x, npos, c->d.in_channels, cinp, c->norm, c->norm + 8, c->act[0]);
+    pack_input_kernel<<<unsigned((npos + 255) / 256), 256, 0, c->stream>>>(x, npos, c->d.positions, c->d.in_channels,
+                                                                          c->norm, c->norm + 8, c->act[0]);
     QC_CUDA(c, cudaGetLastError());
     return QL_OK;
 }
@@ -934,21 +1218,20 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
 {
     const int X = c->d.positions, nl = int(c->layers.size());
     const int64_t npos = int64_t(B) * X;
-    const int coutp = c->layers[nl - 1].cout;
-    const int64_t nel = npos * coutp;
-    const unsigned nb = unsigned((nel + 255) / 256);
+    const unsigned nb = mse_blocks(npos);
     const float gscale = 2.f / float(npos * c->d.out_channels);
-    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, yidx, ystep, X, npos, c->d.out_channels, coutp, c->norm + 24,
-                                          gscale,
+    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, yidx, ystep, X, npos, c->d.out_channels, c->norm + 24, gscale,
                                           c->dz[nl - 1], c->loss_partial);
     QC_CUDA(c, cudaGetLastError());
     for (int l = nl - 1; l >= 0; --l) {
         const Layer &L = c->layers[l];
         const int len = L.cout * kTaps * L.cin + L.cout;  // a multiple of 4 (channels are padded to 16)
         if (len % 4 != 0) return cfail(c, QL_EUNSUPPORTED, "channel padding");
-        QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->wgrid, c->partial, c->stream));
+        int parts = 0;
+        QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->sms, c->partial, c->bad, &parts,
+                             c->stream));
         // partial layout per CTA: [cout][5 cin] then [cout]; W and b are contiguous in the parameter vector
-        reduce_partials_kernel<<<(len + 127) / 128, 32 * kReduceWarps, 0, c->stream>>>(c->partial, c->wgrid, len,
+        reduce_partials_kernel<<<(len + 127) / 128, 32 * kReduceWarps, 0, c->stream>>>(c->partial, parts, len,
                                                                                      c->grad + L.woff);
         QC_CUDA(c, cudaGetLastError());
         if (l > 0) {
@@ -1003,8 +1286,8 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
         Layer L;
         L.cin_real = l == 0 ? d->in_channels : 64;
         L.cout_real = l == d->layers - 1 ? d->out_channels : 64;
-        L.cin = l == 0 ? 16 : 64;
-        L.cout = l == d->layers - 1 ? 16 : 64;
+        L.cin = l == 0 ? kInPad : 64;
+        L.cout = l == d->layers - 1 ? kOutPad : 64;
         L.woff = off;
         off += int64_t(L.cout) * kTaps * L.cin;
         L.boff = off;
@@ -1020,7 +1303,7 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
     c->v = static_cast<float *>(calloc_dev(c, sizeof(float) * off));
     c->w16 = static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * off));
     c->wt16 = static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * off));
-    c->pred = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * 16));
+    c->pred = static_cast<float *>(calloc_dev(c, sizeof(float) * npos * kOutPad));
     c->norm = static_cast<float *>(calloc_dev(c, sizeof(float) * 32));
     for (int l = 0; l < d->layers; ++l) {
         c->act.push_back(static_cast<bf16 *>(calloc_dev(c, sizeof(bf16) * npos * c->layers[l].cin)));
@@ -1028,9 +1311,9 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    c->wgrid = sms > 0 ? 2 * sms : 256;
-    c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(c->wgrid) * (64 * kTaps * 64 + 64)));
-    c->loss_partial = static_cast<float *>(calloc_dev(c, sizeof(float) * ((npos * 16 + 255) / 256)));
+    c->sms = sms > 0 ? sms : 128;
+    c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(2 * c->sms) * (64 * kTaps * 64 + 64)));
+    c->loss_partial = static_cast<float *>(calloc_dev(c, sizeof(float) * mse_blocks(npos)));
     c->edge = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(B) * 2 * 64));
     c->perb = static_cast<int32_t *>(calloc_dev(c, sizeof(int32_t) * size_t(B)));
     c->bad = static_cast<unsigned *>(calloc_dev(c, sizeof(unsigned)));
@@ -1082,7 +1365,7 @@ ql_status ql_closure_forward(ql_closure *c, const float *x, const int32_t *perio
     if (st != QL_OK) return st;
     const int64_t npos = B * c->d.positions;
     unpack_output_kernel<<<unsigned((npos * c->d.out_channels + 255) / 256), 256, 0, c->stream>>>(
-        c->pred, npos, c->d.out_channels, c->layers.back().cout, c->norm + 16, y);
+        c->pred, npos, c->d.positions, c->d.out_channels, c->layers.back().cout, c->norm + 16, y);
     QC_CUDA(c, cudaGetLastError());
     return QL_OK;
 }
@@ -1230,11 +1513,10 @@ static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *
 {
     const int X = c->d.positions;
     const int64_t npos = B * X;
-    const unsigned nb = unsigned((npos * c->layers.back().cout + 255) / 256);
+    const unsigned nb = mse_blocks(npos);
     const float lscale = float(1.0 / double(npos * c->d.out_channels));
-    const int cinp = c->layers[0].cin;
-    pack_gather_kernel<<<unsigned((B * X * cinp + 255) / 256), 256, 0, c->stream>>>(
-        x, periodic, perm, c->d_step, n, int(B), X, c->d.in_channels, cinp, c->norm, c->norm + 8, c->act[0], c->perb,
+    pack_gather_kernel<<<unsigned((B * X + 255) / 256), 256, 0, c->stream>>>(
+        x, periodic, perm, c->d_step, n, int(B), X, c->d.in_channels, c->norm, c->norm + 8, c->act[0], c->perb,
         c->bad);
     QC_CUDA(c, cudaGetLastError());
     ql_status st = forward(c, c->perb, int(B));
