@@ -47,6 +47,18 @@ __device__ __forceinline__ int wrap_pos(int p, int X, int mode, bool *inside)
     return 0;
 }
 
+// Programmatic dependent launch: every kernel of the network is launched so that
+// it may start while the kernel before it in the stream is finishing.  Each
+// one calls pdl_wait() before it touches memory that kernel writes or reads
+// (the wait returns once that kernel has completed and its writes are
+// visible), and pdl_trigger() only after that, so that when a kernel starts,
+// every kernel two or more places before it has completed.  Work that reads
+// nothing a recent kernel writes (barrier set-up, tensor-memory allocation,
+// the weight copy of a convolution, which only Adam writes, at the end of a
+// step) goes before the wait and overlaps the previous kernel's tail.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Blackwell tensor cores (tcgen05): the A and B operands are read from shared
 // memory through 64-bit matrix descriptors, the FP32 accumulator lives in
@@ -294,6 +306,10 @@ __global__ void __launch_bounds__(role_threads(conv_epi_warps(COUT)), 2)
         mbar_init(&wbar, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // the layer's weights, already in staging order (see wstage_index)
+        constexpr uint32_t wbytes = uint32_t(WCH) * COUT * 16;
+        mbar_arrive_tx(&wbar, wbytes);
+        bulk_g2s(ws, w, wbytes, &wbar);
     }
     if (warp == kMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
@@ -304,17 +320,13 @@ __global__ void __launch_bounds__(role_threads(conv_epi_warps(COUT)), 2)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    pdl_wait();
+    if (t == 0) pdl_trigger();
     const uint32_t taddr = s_taddr;
     const int tiles = (X + kConvM - 1) / kConvM, nitems = B * tiles;
     volatile int *const abort = &s_abort;
     if (warp == kCopy) {
-        // the layer's weights (already in staging order, see wstage_index), then the
-        // window of item `it` into stage it % NS once the products of item it - NS have read it
-        if (lane == 0) {
-            constexpr uint32_t wbytes = uint32_t(WCH) * COUT * 16;
-            mbar_arrive_tx(&wbar, wbytes);
-            bulk_g2s(ws, w, wbytes, &wbar);
-        }
+        // the window of item `it` into stage it % NS once the products of item it - NS have read it
         int it = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
             const int s = it % NS;
@@ -506,6 +518,8 @@ __global__ void __launch_bounds__(role_threads(kWgradEpiWarps), 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    pdl_wait();
+    if (t == 0) pdl_trigger();
     const uint32_t taddr = s_taddr;
     volatile int *const abort = &s_abort;
     int nit = 0;  // items of this CTA
@@ -608,20 +622,23 @@ __global__ void __launch_bounds__(role_threads(kWgradEpiWarps), 1)
             float *T = reinterpret_cast<float *>(smem);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the tensor cores' reads
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // lane l < 16 of warp w holds row m = 16 w + l of every D_j
+            // lane l < 16 of warp w holds row m = 16 w + l of every D_j; 64 columns per wait
             const int m = 16 * warp + lane;
+            static_assert(NTOT % 16 == 0, "whole 16-column loads");
 #pragma unroll 1
-            for (int c0 = 0; c0 < NTOT; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(r, taddr + (uint32_t(warp * 32) << 16) + c0);
+            for (int c0 = 0; c0 < NTOT; c0 += 64) {
+                uint32_t r[64];
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                    if (c0 + 16 * h < NTOT) tmem_ld16(r + 16 * h, taddr + (uint32_t(warp * 32) << 16) + c0 + 16 * h);
                 tmem_wait(r);
                 if (lane < 16) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
+                    for (int q = 0; q < 64; ++q) {
                         const int col = c0 + q, j = col / NB, n = col % NB;  // tap j, channel n of B
                         // DZ_A: m = co, n = ci; else m = ci, n = co
                         const int co = DZ_A ? m : n, ci = DZ_A ? n : m;
-                        T[co * RP + j * CIN + ci] = nit > 0 ? __uint_as_float(r[q]) : 0.f;
+                        if (col < NTOT) T[co * RP + j * CIN + ci] = nit > 0 ? __uint_as_float(r[q]) : 0.f;
                     }
                 }
             }
@@ -632,7 +649,11 @@ __global__ void __launch_bounds__(role_threads(kWgradEpiWarps), 1)
             constexpr int RW = kTaps * CIN, RP = RW + 1;
             const float *T = reinterpret_cast<const float *>(smem);
             float *P = partial + size_t(blockIdx.x) * (COUT * RW + COUT);
-            for (int e = t; e < COUT * RW; e += 32 * kWgradEpiWarps) P[e] = T[(e / RW) * RP + e % RW];
+            static_assert(RW % 4 == 0, "rows of whole float4");
+            for (int e = 4 * t; e < COUT * RW; e += 4 * 32 * kWgradEpiWarps) {
+                const float *src = T + (e / RW) * RP + e % RW;  // four values of one row
+                *reinterpret_cast<float4 *>(P + e) = make_float4(src[0], src[1], src[2], src[3]);
+            }
             if (lane == 0)
 #pragma unroll
                 for (int d = 0; d < DBC; ++d) {
@@ -665,6 +686,8 @@ __global__ void __launch_bounds__(256) edge_grad_kernel(const bf16 *__restrict__
                                                         const int *__restrict__ periodic, int B, int X, int cout,
                                                         int cin, float *__restrict__ edge)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float s_a[64][kEdgeChannels], s_n[64][kEdgeChannels];  // [co][ci - c0], cout <= 64
     __shared__ float s_d0[kEdgeSamples][64], s_d1[kEdgeSamples][64];
     const int side = blockIdx.y, b0 = blockIdx.x * kEdgeSamples, c0 = blockIdx.z * kEdgeChannels, t = threadIdx.x;
@@ -714,6 +737,8 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
                                                                            int nparts, int len,
                                                                            float *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float4 s_w[kReduceWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i4 = blockIdx.x * 32 + lane;  // float4 index
@@ -765,6 +790,8 @@ __global__ void pack_input_kernel(const float *__restrict__ x, int64_t npos, int
                                   const float *__restrict__ shift, const float *__restrict__ inv_scale,
                                   bf16 *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t pos = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (pos >= npos) return;
     pack_position(x, pos / X, pos / X, int(pos % X), X, cin, shift, inv_scale, out);
@@ -780,6 +807,8 @@ __global__ void pack_gather_kernel(const float *__restrict__ x, const int32_t *_
                                    const float *__restrict__ inv_scale, bf16 *__restrict__ out,
                                    int32_t *__restrict__ perb, unsigned *__restrict__ bad)
 {
+    pdl_wait();
+    pdl_trigger();
     const int32_t *__restrict__ idx = perm + int64_t(*step) * B;  // this step's samples
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < B) {
@@ -813,6 +842,8 @@ __global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ pred
                                                   float grad_scale, bf16 *__restrict__ dpred,
                                                   float *__restrict__ partial)
 {
+    pdl_wait();
+    pdl_trigger();
     // step (device, may be null): the batch is idx[step * B ..] of a training run's permutation
     if (idx && step) idx += int64_t(*step) * (npos / X);
     __shared__ float red[8];
@@ -864,6 +895,8 @@ __global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ pred
 __global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npos, int X, int cout, int coutp,
                                      const float *__restrict__ out_scale, float *__restrict__ y)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= npos * cout) return;
     const int64_t pos = e / cout;
@@ -877,6 +910,8 @@ __global__ void unpack_output_kernel(const float *__restrict__ pred, int64_t npo
 __global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, float scale, float *__restrict__ out,
                                 const int *__restrict__ step)
 {
+    pdl_wait();
+    pdl_trigger();
     if (step) out += *step;
     __shared__ double red[256];
     // four independent running sums per thread (loads in flight), combined in order
@@ -896,7 +931,12 @@ __global__ void loss_sum_kernel(const float *__restrict__ partial, int nparts, f
 }
 
 // Advances the device step counter of a training run (last node of a step).
-__global__ void step_inc_kernel(int *step) { *step += 1; }
+__global__ void step_inc_kernel(int *step)
+{
+    pdl_wait();
+    pdl_trigger();
+    *step += 1;
+}
 
 // Adam on FP32 master parameters; refreshes the bf16 weight copies, the
 // tap-flipped transposed copies used by the backward pass, and the f32 biases.
@@ -919,6 +959,8 @@ struct AdamArgs {
 };
 __global__ void adam_kernel(AdamArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const float g = a.grad[i];
@@ -953,6 +995,8 @@ __global__ void adam_kernel(AdamArgs a)
 __global__ void cast_weights_kernel(const float *__restrict__ wf, int cout, int cin, bf16 *__restrict__ w,
                                     bf16 *__restrict__ wt)
 {
+    pdl_wait();
+    pdl_trigger();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= cout * kTaps * cin) return;
     const int co = e / (kTaps * cin), j = (e / cin) % kTaps, ci = e % cin;
@@ -967,6 +1011,24 @@ struct Layer {
     int cin_real, cout_real;
     int64_t woff, boff;  // offsets of W [cout][5][cin] and bias [cout] in the f32 parameter vector
 };
+
+// Launches kernel k on stream s with programmatic stream serialisation (see
+// pdl_wait): it may start before the previous kernel in the stream ends.
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 // CTAs per SM of a tensor-core kernel: as many as shared memory and the 512
 // TMEM columns of an SM hold (each CTA allocates tmem_cols for the whole
@@ -997,6 +1059,21 @@ cudaError_t ctas_per_sm(K k, int threads, size_t smem, int tmem_cols, int cap, S
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    // the same bound from the SM's shared memory, registers (allocated per warp
+    // in units of 256) and threads; the larger of the two counts is used (a grid
+    // above what fits only queues CTAs, it stays correct)
+    cudaFuncAttributes fa;
+    int smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess) {
+        const int by_smem = smem_sm / int(smem + fa.sharedSizeBytes + size_t(resv));
+        const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = regs_sm / std::max(1, warp_regs * (threads / 32));
+        occ = std::max(occ, std::min(std::min(by_smem, by_regs), thr_sm / threads));
+    }
     *per_sm = std::max(1, std::min(std::min(occ, 512 / tmem_cols), cap));
     *sms = std::max(1, n);
     if (dev >= 0 && dev < kMaxDevices) {
@@ -1022,8 +1099,7 @@ cudaError_t conv_launch(const bf16 *in, const bf16 *w, const float *bias, const 
     if (e != cudaSuccess) return e;
     const int items = B * ((X + kConvM - 1) / kConvM);
     const int grid = std::max(1, std::min(items, sms * per_sm));
-    k<<<grid, threads, smem, s>>>(in, w, bias, per, X, B, out, mask, edge, err);
-    return cudaGetLastError();
+    return launch(k, dim3(grid), dim3(threads), smem, s, in, w, bias, per, X, B, out, mask, edge, err);
 }
 
 cudaError_t conv_any(int cin, int cout, int epi, const bf16 *in, const bf16 *w, const float *bias, const int *per,
@@ -1061,8 +1137,7 @@ cudaError_t wgrad_launch(const bf16 *dz, const bf16 *in, const int *per, int B, 
     const int ntiles = B * ((X + kConvM - 1) / kConvM);
     const int grid = std::max(1, std::min(ntiles, std::max(1, sms) * per_sm));
     *parts = grid;
-    k<<<grid, threads, smem, s>>>(dz, in, per, X, ntiles, partial, err);
-    return cudaGetLastError();
+    return launch(k, dim3(grid), dim3(threads), smem, s, dz, in, per, X, ntiles, partial, err);
 }
 
 cudaError_t wgrad_any(int cin, int cout, const bf16 *dz, const bf16 *in, const int *per, int B, int X, int sms,
@@ -1156,10 +1231,9 @@ static ql_status refresh_weights(ql_closure *c)
 {
     for (const Layer &L : c->layers) {
         const int n = L.cout * kTaps * L.cin;
-        cast_weights_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->param + L.woff, L.cout, L.cin, c->w16 + L.woff,
-                                                                    c->wt16 + L.woff);
+        QC_CUDA(c, launch(cast_weights_kernel, dim3((n + 255) / 256), dim3(256), 0, c->stream, c->param + L.woff,
+                          L.cout, L.cin, c->w16 + L.woff, c->wt16 + L.woff));
     }
-    QC_CUDA(c, cudaGetLastError());
     return QL_OK;
 }
 
@@ -1189,9 +1263,8 @@ static ql_status forward(ql_closure *c, const int *per, int B)
 static ql_status pack(ql_closure *c, const float *x, int B)
 {
     const int64_t npos = int64_t(B) * c->d.positions;
-    pack_input_kernel<<<unsigned((npos + 255) / 256), 256, 0, c->stream>>>(x, npos, c->d.positions, c->d.in_channels,
-                                                                          c->norm, c->norm + 8, c->act[0]);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(pack_input_kernel, dim3(unsigned((npos + 255) / 256)), dim3(256), 0, c->stream, x, npos,
+                      c->d.positions, c->d.in_channels, c->norm, c->norm + 8, c->act[0]));
     return QL_OK;
 }
 
@@ -1220,9 +1293,8 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
     const int64_t npos = int64_t(B) * X;
     const unsigned nb = mse_blocks(npos);
     const float gscale = 2.f / float(npos * c->d.out_channels);
-    mse_kernel<<<nb, 256, 0, c->stream>>>(c->pred, y, yidx, ystep, X, npos, c->d.out_channels, c->norm + 24, gscale,
-                                          c->dz[nl - 1], c->loss_partial);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(mse_kernel, dim3(nb), dim3(256), 0, c->stream, c->pred, y, yidx, ystep, X, npos,
+                      c->d.out_channels, c->norm + 24, gscale, c->dz[nl - 1], c->loss_partial));
     for (int l = nl - 1; l >= 0; --l) {
         const Layer &L = c->layers[l];
         const int len = L.cout * kTaps * L.cin + L.cout;  // a multiple of 4 (channels are padded to 16)
@@ -1231,18 +1303,15 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
         QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->sms, c->partial, c->bad, &parts,
                              c->stream));
         // partial layout per CTA: [cout][5 cin] then [cout]; W and b are contiguous in the parameter vector
-        reduce_partials_kernel<<<(len + 127) / 128, 32 * kReduceWarps, 0, c->stream>>>(c->partial, parts, len,
-                                                                                     c->grad + L.woff);
-        QC_CUDA(c, cudaGetLastError());
+        QC_CUDA(c, launch(reduce_partials_kernel, dim3((len + 127) / 128), dim3(32 * kReduceWarps), 0, c->stream,
+                          c->partial, parts, len, c->grad + L.woff));
         if (l > 0) {
             // dz[l-1] = (W^T * dz[l] + end terms of replicate padding) masked by act[l] > 0
             // (act[l] is the output of layer l-1)
             static_assert(kEdgeSamples * kEdgeChannels == 256, "one output per thread");
-            edge_grad_kernel<<<dim3((B + kEdgeSamples - 1) / kEdgeSamples, 2, (L.cin + kEdgeChannels - 1) / kEdgeChannels),
-                               256, 0, c->stream>>>(
-                c->dz[l], c->w16 + L.woff, per, B, X, L.cout, L.cin,
-                                                                 c->edge);
-            QC_CUDA(c, cudaGetLastError());
+            QC_CUDA(c, launch(edge_grad_kernel,
+                              dim3((B + kEdgeSamples - 1) / kEdgeSamples, 2, (L.cin + kEdgeChannels - 1) / kEdgeChannels),
+                              dim3(256), 0, c->stream, c->dz[l], c->w16 + L.woff, per, B, X, L.cout, L.cin, c->edge));
             QC_CUDA(c, conv_any(L.cout, L.cin, EPI_MASK_BF16, c->dz[l], c->wt16 + L.woff, nullptr, per, B, X,
                                 c->dz[l - 1], c->act[l], c->edge, c->bad, c->stream));
         }
@@ -1364,9 +1433,9 @@ ql_status ql_closure_forward(ql_closure *c, const float *x, const int32_t *perio
     if (st == QL_OK) st = forward(c, periodic, int(B));
     if (st != QL_OK) return st;
     const int64_t npos = B * c->d.positions;
-    unpack_output_kernel<<<unsigned((npos * c->d.out_channels + 255) / 256), 256, 0, c->stream>>>(
-        c->pred, npos, c->d.positions, c->d.out_channels, c->layers.back().cout, c->norm + 16, y);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(unpack_output_kernel, dim3(unsigned((npos * c->d.out_channels + 255) / 256)), dim3(256), 0,
+                      c->stream, c->pred, npos, c->d.positions, c->d.out_channels, c->layers.back().cout, c->norm + 16,
+                      y));
     return QL_OK;
 }
 
@@ -1474,8 +1543,7 @@ static ql_status adam_step(ql_closure *c, float lr)
     a.lr = lr;
     a.c1 = float(1.0 / (1.0 - pow(0.9, double(c->step))));
     a.c2 = float(1.0 / (1.0 - pow(0.999, double(c->step))));
-    adam_kernel<<<unsigned((c->nparam + 255) / 256), 256, 0, c->stream>>>(a);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(adam_kernel, dim3(unsigned((c->nparam + 255) / 256)), dim3(256), 0, c->stream, a));
     return a.nl ? QL_OK : refresh_weights(c);
 }
 
@@ -1515,30 +1583,27 @@ static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *
     const int64_t npos = B * X;
     const unsigned nb = mse_blocks(npos);
     const float lscale = float(1.0 / double(npos * c->d.out_channels));
-    pack_gather_kernel<<<unsigned((B * X + 255) / 256), 256, 0, c->stream>>>(
-        x, periodic, perm, c->d_step, n, int(B), X, c->d.in_channels, c->norm, c->norm + 8, c->act[0], c->perb,
-        c->bad);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(pack_gather_kernel, dim3(unsigned((B * X + 255) / 256)), dim3(256), 0, c->stream, x, periodic,
+                      perm, c->d_step, n, int(B), X, c->d.in_channels, c->norm, c->norm + 8, c->act[0], c->perb,
+                      c->bad));
     ql_status st = forward(c, c->perb, int(B));
     if (st == QL_OK) st = backward(c, y, perm, c->d_step, c->perb, int(B), nullptr);
     if (st != QL_OK) return st;
     if (losses) {
-        loss_sum_kernel<<<1, 256, 0, c->stream>>>(c->loss_partial, int(nb), lscale, losses, c->d_step);
-        QC_CUDA(c, cudaGetLastError());
+        QC_CUDA(c, launch(loss_sum_kernel, dim3(1), dim3(256), 0, c->stream, c->loss_partial, int(nb), lscale, losses,
+                          c->d_step));
     }
     AdamArgs a = adam_args(c);
     a.step = c->d_step;
     a.lr_arr = c->d_sched;
     a.c1_arr = c->d_sched + c->sched_cap;
     a.c2_arr = c->d_sched + 2 * c->sched_cap;
-    adam_kernel<<<unsigned((c->nparam + 255) / 256), 256, 0, c->stream>>>(a);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(adam_kernel, dim3(unsigned((c->nparam + 255) / 256)), dim3(256), 0, c->stream, a));
     if (!a.nl) {
         st = refresh_weights(c);
         if (st != QL_OK) return st;
     }
-    step_inc_kernel<<<1, 1, 0, c->stream>>>(c->d_step);
-    QC_CUDA(c, cudaGetLastError());
+    QC_CUDA(c, launch(step_inc_kernel, dim3(1), dim3(1), 0, c->stream, c->d_step));
     return QL_OK;
 }
 
