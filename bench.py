@@ -761,6 +761,70 @@ def run_standing_shock(args):
     print(json.dumps(line), flush=True)
 
 
+def run_inviscid(args):
+    """The paper's near-inviscid shock tube (Sec. IV.B, "Inviscid regime"): L = 80, sigma = 1e-6 (tau~ = 1e-6) with
+    eta_i = 0.05 (E_l = 0.4825), chi_SET, N_x = 8e4 (dx = 1e-3), dt = 1e-6, Q = 8, Sod state with the membrane at
+    L / 2, fixed ends, dense Pr; FP64 and FP32 to t = --inviscid-t.  Per precision: wall time of the step loop
+    (CUDA events), updates/s, and the profile errors against the exact inviscid solution (ql_riemann_exact)
+    inside the fan and the two plateaus, eight cells away from their edges, plus the shock position."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import qlbm as q
+    torch.cuda.set_device(0)
+    B.build()
+    L, nx, El, sigma, dt, Q = 80.0, 80000, 0.4825, 1e-6, 1e-6, 8
+    steps = int(round(args.inviscid_t / dt))
+    t = steps * dt
+    eta0 = q.ql_eta_of_denseness(El)
+    x = (np.arange(nx) + 0.5) * L / nx
+    xi = (x - 0.5 * L) / t
+    waves, r_ex, u_ex, T_ex = q.ql_riemann_exact(eta0, 1.0, (1.0, 1.0), (0.125, 1.0), xi)
+    pad = 8 * L / nx / t
+    regions = {"fan": (waves["xi_head"] + pad, waves["xi_tail"] - pad),
+               "plateau_left": (waves["xi_tail"] + pad, waves["u_c"] - pad),
+               "plateau_right": (waves["u_c"] + pad, waves["xi_shock"] - pad)}
+    stream = torch.cuda.current_stream()
+    rows, fields = [], {}
+    for prec, name in ((q.QL_FP64, "fp64"), (q.QL_FP32, "fp32")):
+        s = q.Solver(Q, nx, L, dt, El, sigma / (El * L), bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN,
+                     prm=(1.0, 0.0, 1.0, 0.125, 0.0, 1.0), precision=prec, pr_mode=q.QL_PR_DENSE)
+        s.step(3)  # warm-up: loads the kernels and records the step graph
+        s.sync()
+        s.close()
+        s = q.Solver(Q, nx, L, dt, El, sigma / (El * L), bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN,
+                     prm=(1.0, 0.0, 1.0, 0.125, 0.0, 1.0), precision=prec, pr_mode=q.QL_PR_DENSE)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        f = s.moments()
+        s.close()
+        sec = e0.elapsed_time(e1) * 1e-3
+        err = {}
+        for reg, (a, b) in regions.items():
+            sel = (xi > a) & (xi < b)
+            err[reg] = {k: float(np.abs(f[k][sel] - ref[sel]).max() / max(1.0, np.abs(ref[sel]).max()))
+                        for k, ref in (("rho", r_ex), ("u", u_ex), ("T", T_ex))}
+            err[reg]["cells"] = int(sel.sum())
+        mid = 0.5 * (waves["rho2"] + 0.125)
+        i = np.flatnonzero((f["rho"][:-1] >= mid) & (f["rho"][1:] < mid) & (x[:-1] > 0.5 * L + waves["u_c"] * t))[0]
+        x_s = x[i] + (f["rho"][i] - mid) / (f["rho"][i] - f["rho"][i + 1]) * (x[i + 1] - x[i])
+        fields[name] = f
+        rows.append({"precision": name, "steps": steps, "t": t, "step_loop_s": sec,
+                     "updates_per_s": nx * Q * steps / sec, "errors_vs_inviscid": err,
+                     "shock_offset_cells": float((x_s - (0.5 * L + waves["xi_shock"] * t)) / (L / nx))})
+    rows[1]["fp32_vs_fp64"] = {k: float(np.abs(fields["fp32"][k] - fields["fp64"][k]).max() /
+                                        np.abs(fields["fp64"][k]).max()) for k in ("rho", "u", "T", "P")}
+    line = {"metric": "time to solution", "value": rows[0]["step_loop_s"], "unit": "s", "n_gpus": 1, "steps": steps,
+            "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "gpu_launches": 3 * steps,
+            "config": {"workload": "near_inviscid_shock_tube", "length": L, "nx": nx, "Q": Q, "sigma": sigma, "dt": dt,
+                       "denseness": El, "chi": "SET", "t_end": t,
+                       "value": "FP64 step loop on CUDA events; FP32 in rows"},
+            "waves": waves, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 # The paper's timed shock-tube runs (Table comp_time): sigma, Q, N_x, and the LB wall time on one core of an
 # Intel Xeon Gold 6330.
 PAPER_SHOCK_TABLE = [(0.001, 8, 1600, 62.0), (0.01, 8, 800, 32.0), (0.1, 20, 640, 71.0), (1.0, 200, 160, 176.0)]
@@ -852,8 +916,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-with-FP64-sums, FP64 and batch sub-records")
     ap.add_argument("--fp64-steps", type=int, default=20)
-    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table", "standing_shock"],
-                    default="sod")
+    ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table", "standing_shock",
+                                           "inviscid"], default="sod")
+    ap.add_argument("--inviscid-t", type=float, default=0.05)
     ap.add_argument("--shock-steps", type=int, default=1_200_000)
     ap.add_argument("--table-steps", type=int, default=9000)
     ap.add_argument("--sweep", type=int, default=16)
@@ -884,6 +949,9 @@ def main():
         return
     if args.workload == "standing_shock" and args.impl == "ours":
         run_standing_shock(args)
+        return
+    if args.workload == "inviscid" and args.impl == "ours":
+        run_inviscid(args)
         return
     if args.impl == "reference":
         run_reference(args, w)

@@ -452,6 +452,25 @@ ql_status ql_sound_modes(double denseness, double kn, double length, double rho_
 ql_status ql_rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach,
                               double *out);
 
+/* Inviscid limit of the dense-gas shock tube, Sec. IV.B ("Inviscid limit"),
+ * Eqs. (euler), (euler_xi), (sod_sol), (rankine_hugoniot): the exact solution
+ * of the Euler equations with P = rho T (1 + 4 eta chi_SET(eta)), eta =
+ * eta0 rho / rho_ref and internal energy e = (3/2) rho T, for a left state
+ * (left[0] = rho, left[1] = T) and a right state (right[0], right[1]), both at
+ * rest, with the left pressure above the right: a left-facing rarefaction, a
+ * contact and a right-facing shock.  The energy relation across the shock is
+ * taken with -e_R xi_s on its right-hand side, as energy conservation across
+ * a shock moving into gas at rest requires (the printed relation has +e_R xi_s).
+ * waves (host, 9 doubles; may be NULL) = {P_c, u_c, rho1, T1, rho2, T2,
+ * xi_head, xi_tail, xi_shock}: star pressure and velocity, the states left (1)
+ * and right (2) of the contact, the speeds of the fan's head and tail and of
+ * the shock.  For i < n, rho[i], u[i], T[i] at the similarity variable xi[i] =
+ * (x - x0) / t (host arrays; may be NULL when n = 0).  Runs on the host; no
+ * device memory.  QL_EINVAL on invalid states or a left pressure not above the
+ * right. */
+ql_status ql_riemann_exact(double eta0, double rho_ref, const double *left, const double *right, double *waves,
+                           int64_t n, const double *xi, double *rho, double *u, double *T);
+
 /* Frees the context and its device buffers (waits for its stream). */
 ql_status ql_destroy(ql_ctx *ctx);
 

@@ -8,6 +8,7 @@
 #include <unistd.h>
 
 #include <mutex>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -748,6 +749,23 @@ ql_status ql_rankine_hugoniot(double eta0, double rho_ref, double rho1, double T
 {
     if (!out || !rankine_hugoniot(eta0, rho_ref, rho1, T1, mach, out))
         return fail(nullptr, QL_EINVAL, "no compressive Rankine-Hugoniot solution");
+    return QL_OK;
+}
+
+ql_status ql_riemann_exact(double eta0, double rho_ref, const double *left, const double *right, double *waves,
+                           int64_t n, const double *xi, double *rho, double *u, double *T)
+{
+    if (!left || !right || n < 0 || (n > 0 && (!xi || !rho || !u || !T)) || !(eta0 >= 0.0) || !(eta0 < 0.5) ||
+        !(rho_ref > 0.0))
+        return fail(nullptr, QL_EINVAL, "bad arguments to ql_riemann_exact");
+    std::unique_ptr<RiemannWaves> w(new RiemannWaves());
+    if (!riemann_solve(eta0, rho_ref, left[0], left[1], right[0], right[1], w.get()))
+        return fail(nullptr, QL_EINVAL, "no rarefaction-contact-shock solution for these states");
+    if (waves) {
+        const double v[9] = {w->P_c, w->u_c, w->rho1, w->T1, w->rho2, w->T2, w->xi_head, w->xi_tail, w->xi_shock};
+        for (int k = 0; k < 9; ++k) waves[k] = v[k];
+    }
+    for (int64_t i = 0; i < n; ++i) riemann_sample(*w, xi[i], &rho[i], &u[i], &T[i]);
     return QL_OK;
 }
 

@@ -237,6 +237,150 @@ bool rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, doubl
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Inviscid limit of the shock tube (Sec. IV.B, Eqs. euler - rankine_hugoniot).
+
+static double pressure_of(double eta0, double rho_ref, double rho, double T)
+{
+    return rho * T * cs_z(eta0 * rho / rho_ref);
+}
+static double temperature_of(double eta0, double rho_ref, double rho, double P)
+{
+    return P / (rho * cs_z(eta0 * rho / rho_ref));
+}
+
+// Along the left-facing rarefaction (u = xi + c_s, Eq. sod_sol) the similarity
+// form of Eq. (euler_xi) gives dP = c_s^2 drho and du = -c_s drho / rho; with
+// the pressure as the variable, drho/dP = 1 / c_s^2 and du/dP = -1 / (rho c_s).
+static void fan_rates(double eta0, double rho_ref, double rho, double P, double *drho, double *du)
+{
+    const double c2 = sound_speed2(eta0, rho_ref, rho, temperature_of(eta0, rho_ref, rho, P));
+    *drho = 1.0 / c2;
+    *du = -1.0 / (rho * sqrt(c2));
+}
+
+// Classical fourth-order Runge-Kutta in P from (P0, rho0, u0) to P1 in n steps;
+// rho and u at every node when the tables are given (n + 1 entries).
+static void fan_integrate(double eta0, double rho_ref, double P0, double rho0, double u0, double P1, int n,
+                          double *rho1, double *u1, double *tP, double *trho, double *tu)
+{
+    const double h = (P1 - P0) / n;
+    double P = P0, r = rho0, u = u0;
+    if (tP) { tP[0] = P; trho[0] = r; tu[0] = u; }
+    for (int k = 0; k < n; ++k) {
+        double k1r, k1u, k2r, k2u, k3r, k3u, k4r, k4u;
+        fan_rates(eta0, rho_ref, r, P, &k1r, &k1u);
+        fan_rates(eta0, rho_ref, r + 0.5 * h * k1r, P + 0.5 * h, &k2r, &k2u);
+        fan_rates(eta0, rho_ref, r + 0.5 * h * k2r, P + 0.5 * h, &k3r, &k3u);
+        fan_rates(eta0, rho_ref, r + h * k3r, P + h, &k4r, &k4u);
+        r += h / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+        u += h / 6.0 * (k1u + 2.0 * k2u + 2.0 * k3u + k4u);
+        P = P0 + (k + 1) * h;
+        if (tP) { tP[k + 1] = P; trho[k + 1] = r; tu[k + 1] = u; }
+    }
+    *rho1 = r;
+    *u1 = u;
+}
+
+// Eq. (rankine_hugoniot) for a shock moving at xi_s into the right state at rest
+// (the energy relation with -e_R xi_s on its right-hand side, as energy
+// conservation across it requires): mass and momentum give u_c^2 =
+// (P_c - P_R)(1 - rho_R / rho_2) / rho_R; the energy balance divided by xi_s is
+// the residual below in rho_2, with e = (3/2) rho T = (3/2) P / Z.
+static double shock_residual(double eta0, double rho_ref, double Pc, double rhoR, double PR, double rho2)
+{
+    const double r = rhoR / rho2;
+    const double uc2 = (Pc - PR) * (1.0 - r) / rhoR;
+    const double ec = 1.5 * Pc / cs_z(eta0 * rho2 / rho_ref), eR = 1.5 * PR / cs_z(eta0 * rhoR / rho_ref);
+    return -(ec + 0.5 * rho2 * uc2) * r + (1.0 - r) * Pc + eR;
+}
+
+// Post-shock density for the star pressure Pc (bisection on a bracket where
+// the residual changes sign); u_c and xi_s follow.
+static bool shock_state(double eta0, double rho_ref, double Pc, double rhoR, double PR, double *rho2, double *uc,
+                        double *xis)
+{
+    double lo = rhoR * (1.0 + 1e-12), hi = 4.0 * rhoR;
+    const double rmax = eta0 > 0.0 ? 0.999 * rho_ref / eta0 : 1e300;  // eta < 1
+    double flo = shock_residual(eta0, rho_ref, Pc, rhoR, PR, lo), fhi = shock_residual(eta0, rho_ref, Pc, rhoR, PR, hi);
+    while ((flo < 0.0) == (fhi < 0.0)) {
+        if (hi >= rmax) return false;
+        lo = hi;
+        flo = fhi;
+        hi = fmin(2.0 * hi, rmax);
+        fhi = shock_residual(eta0, rho_ref, Pc, rhoR, PR, hi);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi), fm = shock_residual(eta0, rho_ref, Pc, rhoR, PR, mid);
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+    }
+    *rho2 = 0.5 * (lo + hi);
+    const double r = rhoR / *rho2;
+    *uc = sqrt(fmax(0.0, (Pc - PR) * (1.0 - r) / rhoR));
+    *xis = *uc / (1.0 - r);
+    return true;
+}
+
+bool riemann_solve(double eta0, double rho_ref, double rhoL, double TL, double rhoR, double TR, RiemannWaves *w)
+{
+    if (!(rhoL > 0.0) || !(TL > 0.0) || !(rhoR > 0.0) || !(TR > 0.0) || !w) return false;
+    const double PL = pressure_of(eta0, rho_ref, rhoL, TL), PR = pressure_of(eta0, rho_ref, rhoR, TR);
+    if (!(PL > PR)) return false;
+    // star pressure: the rarefaction's u_c falls and the shock's rises with P_c
+    double lo = PR, hi = PL, rho1 = rhoL, uL = 0.0, rho2 = rhoR, us = 0.0, xis = 0.0;
+    for (int it = 0; it < 100 && hi - lo > 1e-15 * hi; ++it) {
+        const double Pc = 0.5 * (lo + hi);
+        fan_integrate(eta0, rho_ref, PL, rhoL, 0.0, Pc, RiemannWaves::kFan, &rho1, &uL, nullptr, nullptr, nullptr);
+        if (!shock_state(eta0, rho_ref, Pc, rhoR, PR, &rho2, &us, &xis)) return false;
+        if (uL > us) lo = Pc; else hi = Pc;
+    }
+    w->P_c = 0.5 * (lo + hi);
+    fan_integrate(eta0, rho_ref, PL, rhoL, 0.0, w->P_c, RiemannWaves::kFan, &w->rho1, &w->u_c, w->fan_P, w->fan_rho,
+                  w->fan_u);
+    if (!shock_state(eta0, rho_ref, w->P_c, rhoR, PR, &w->rho2, &us, &w->xi_shock)) return false;
+    w->T1 = temperature_of(eta0, rho_ref, w->rho1, w->P_c);
+    w->T2 = temperature_of(eta0, rho_ref, w->rho2, w->P_c);
+    w->xi_head = -sqrt(sound_speed2(eta0, rho_ref, rhoL, TL));
+    w->xi_tail = w->u_c - sqrt(sound_speed2(eta0, rho_ref, w->rho1, w->T1));
+    w->eta0 = eta0;
+    w->rho_ref = rho_ref;
+    w->rhoL = rhoL;
+    w->TL = TL;
+    w->rhoR = rhoR;
+    w->TR = TR;
+    return true;
+}
+
+void riemann_sample(const RiemannWaves &w, double xi, double *rho, double *u, double *T)
+{
+    if (xi < w.xi_head) {
+        *rho = w.rhoL; *u = 0.0; *T = w.TL;
+    } else if (xi < w.xi_tail) {
+        // inside the fan: xi = u - c_s rises monotonically along the table
+        auto xi_at = [&](int k) {
+            const double Tk = temperature_of(w.eta0, w.rho_ref, w.fan_rho[k], w.fan_P[k]);
+            return w.fan_u[k] - sqrt(sound_speed2(w.eta0, w.rho_ref, w.fan_rho[k], Tk));
+        };
+        int a = 0, b = RiemannWaves::kFan;
+        while (b - a > 1) {
+            const int m = (a + b) / 2;
+            if (xi_at(m) <= xi) a = m; else b = m;
+        }
+        const double xa = xi_at(a), xb = xi_at(b), f = xb > xa ? (xi - xa) / (xb - xa) : 0.0;
+        const double r = w.fan_rho[a] + f * (w.fan_rho[b] - w.fan_rho[a]);
+        const double P = w.fan_P[a] + f * (w.fan_P[b] - w.fan_P[a]);
+        *rho = r;
+        *u = w.fan_u[a] + f * (w.fan_u[b] - w.fan_u[a]);
+        *T = temperature_of(w.eta0, w.rho_ref, r, P);
+    } else if (xi < w.u_c) {
+        *rho = w.rho1; *u = w.u_c; *T = w.T1;
+    } else if (xi < w.xi_shock) {
+        *rho = w.rho2; *u = w.u_c; *T = w.T2;
+    } else {
+        *rho = w.rhoR; *u = 0.0; *T = w.TR;
+    }
+}
+
 bool initial_fields(int kind, const double *prm, int64_t nx, double length, int periodic, double eta0,
                     double rho_ref, const double *urho, const double *uu, const double *uT,
                     const double *ughost, int halo, double *rho, double *u, double *T)

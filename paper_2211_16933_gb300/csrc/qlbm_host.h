@@ -40,6 +40,24 @@ bool sound_modes(double denseness, double kn, double length, double rho_ref, int
 // Eq. (rankine_hugoniot) for a standing shock.  out = {u1, rho2, u2, T2}.
 bool rankine_hugoniot(double eta0, double rho_ref, double rho1, double T1, double mach, double *out);
 
+// Inviscid limit of the dense-gas shock tube (Sec. IV.B, Eqs. euler -
+// rankine_hugoniot): left state (rhoL, TL) and right state (rhoR, TR), both at
+// rest, left pressure above the right.  The wave pattern is a left-facing
+// rarefaction (integrated in the pressure by fourth-order Runge-Kutta, kFan
+// steps, and kept as a table for sampling), a contact at u_c and a
+// right-facing shock; the star pressure is found by bisection so that the
+// rarefaction and the shock give the same u_c.
+struct RiemannWaves {
+    static constexpr int kFan = 4000;
+    double P_c, u_c, rho1, T1, rho2, T2;   // star state: 1 left, 2 right of the contact
+    double xi_head, xi_tail, xi_shock;     // fan head and tail, shock
+    double eta0, rho_ref, rhoL, TL, rhoR, TR;
+    double fan_P[kFan + 1], fan_rho[kFan + 1], fan_u[kFan + 1];
+};
+bool riemann_solve(double eta0, double rho_ref, double rhoL, double TL, double rhoR, double TR, RiemannWaves *w);
+// The solution at xi = (x - x0) / t.
+void riemann_sample(const RiemannWaves &w, double xi, double *rho, double *u, double *T);
+
 // Initial fields at cells -halo .. nx+halo-1 (arrays of nx + 2 halo).
 // kind/prm as in ql_init; user fields/ghost for kind 3.  Returns false on
 // invalid parameters.

@@ -28,7 +28,7 @@ MAX_Q = 200
 SUPPORTED_BATCH_Q = (8, 16, 24, 32)
 EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_get_state", "ql_set_state",
             "ql_load_fields", "ql_rhs", "ql_state_device", "ql_info", "ql_velocity_set", "ql_eta_of_denseness",
-            "ql_sound_speed2", "ql_rankine_hugoniot", "ql_destroy", "ql_last_error",
+            "ql_sound_speed2", "ql_rankine_hugoniot", "ql_riemann_exact", "ql_destroy", "ql_last_error",
             "ql_batch_create", "ql_batch_tune", "ql_batch_run", "ql_batch_sync", "ql_batch_moments",
             "ql_batch_get_state", "ql_batch_info", "ql_batch_destroy", "ql_batch_last_error", "ql_step_noalloc",
             "ql_batch_set_shape",
@@ -125,6 +125,7 @@ def lib():
         L.ql_sound_speed2.argtypes = [C.c_double] * 4
         L.ql_sound_speed2.restype = C.c_double
         L.ql_rankine_hugoniot.argtypes = [C.c_double] * 5 + [_DP]
+        L.ql_riemann_exact.argtypes = [C.c_double, C.c_double, _DP, _DP, _DP, C.c_int64, _DP, _DP, _DP, _DP]
         L.ql_batch_create.argtypes = [C.POINTER(ql_instance), C.c_int64, C.POINTER(ql_opts), C.POINTER(V)]
         L.ql_batch_tune.argtypes = [V, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.ql_batch_set_shape.argtypes = [V, C.c_int32, C.c_int32]
@@ -202,6 +203,22 @@ def ql_rankine_hugoniot(eta0, rho_ref, rho1, T1, mach):
     out = np.zeros(4)
     _check(lib().ql_rankine_hugoniot(eta0, rho_ref, rho1, T1, mach, _ptr(out)))
     return tuple(out)
+
+
+def ql_riemann_exact(eta0, rho_ref, left, right, xi=()):
+    """Inviscid shock tube of the dense gas (host): left and right states (rho, T) at rest.  Returns the waves
+    {P_c, u_c, rho1, T1, rho2, T2, xi_head, xi_tail, xi_shock} as a dict and rho, u, T at the given xi."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64).ravel()
+    n = xi.size
+    waves, rho, u, T = np.zeros(9), np.zeros(max(n, 1)), np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    lv = np.ascontiguousarray(left, dtype=np.float64)
+    rv = np.ascontiguousarray(right, dtype=np.float64)
+    if lv.size != 2 or rv.size != 2:
+        raise ValueError("left and right are (rho, T) pairs")
+    _check(lib().ql_riemann_exact(eta0, rho_ref, _ptr(lv), _ptr(rv), _ptr(waves), n, _ptr(xi) if n else None,
+                                  _ptr(rho), _ptr(u), _ptr(T)))
+    keys = ("P_c", "u_c", "rho1", "T1", "rho2", "T2", "xi_head", "xi_tail", "xi_shock")
+    return dict(zip(keys, waves.tolist())), rho[:n], u[:n], T[:n]
 
 
 # ---------------------------------------------------------------- context entry points

@@ -72,6 +72,47 @@ def test_rankine_hugoniot_matches_oracle(qlbm_lib):
         qlbm_lib.ql_rankine_hugoniot(0.01, 1.0, 1.0, 1.0, 0.9)
 
 
+@pytest.mark.parametrize("El", [0.0, 0.4825, 1.917])
+def test_exact_riemann_solution_matches_oracle(qlbm_lib, El):
+    """ql_riemann_exact (host: RK4 in the pressure along the fan, bisection for P_c and for rho_2) against the
+    oracle's dense-gas shock tube (its own fan table and star-pressure search): Sod states at the paper's
+    E_l = 0 (dilute), 0.4825 and 1.917 (Sec. IV.B), waves and sampled profiles."""
+    from oracle import riemann as R
+    eta = O.eta_from_denseness(El) if El > 0 else 0.0
+    st = R.ShockTube(R.DenseGas(eta), 1.0, 1.0, 0.125, 1.0)
+    xi = np.linspace(-2.5, 2.5, 2001)
+    waves, rho, u, T = qlbm_lib.ql_riemann_exact(eta, 1.0, (1.0, 1.0), (0.125, 1.0), xi)
+    for k, ref in (("P_c", st.Pc), ("u_c", st.uc), ("rho1", st.rho1), ("rho2", st.rho2), ("xi_shock", st.xi_s),
+                   ("xi_head", st.xi_head), ("xi_tail", st.xi_tail)):
+        # 1e-7: the oracle interpolates its tabulated fan (measured differences up to 3e-8); the product's
+        # RK4 fan meets the ideal-gas closed forms to 1e-10 (next test)
+        assert abs(waves[k] - ref) <= 1e-7 * max(1.0, abs(ref)), (k, waves[k], ref)
+    r2, u2, T2 = st.sample(xi)
+    # away from the jumps (a grid point may fall on either side of one)
+    near = np.zeros_like(xi, dtype=bool)
+    for x0 in (waves["u_c"], waves["xi_shock"]):
+        near |= np.abs(xi - x0) < 5e-3
+    for got, ref in ((rho, r2), (u, u2), (T, T2)):
+        assert np.abs(got - ref)[~near].max() <= 1e-6, El
+
+
+def test_exact_riemann_solution_dilute_limit_is_the_ideal_gas_solution(qlbm_lib):
+    """eta0 = 0: the monatomic ideal gas (gamma = 5/3), whose star state solves the textbook relation
+    u_rarefaction(P) = (2 c_L / (gamma - 1)) (1 - (P / P_L)^((gamma - 1) / (2 gamma))) = u_shock(P) =
+    (P - P_R) sqrt(2 / (rho_R ((gamma + 1) P + (gamma - 1) P_R))), and the shock density ratio
+    ((gamma + 1) P + (gamma - 1) P_R) / ((gamma - 1) P + (gamma + 1) P_R)."""
+    g = 5.0 / 3.0
+    waves, *_ = qlbm_lib.ql_riemann_exact(0.0, 1.0, (1.0, 1.0), (0.125, 1.0))
+    P, PL, PR, cL = waves["P_c"], 1.0, 0.125, math.sqrt(g)
+    u_rar = 2 * cL / (g - 1) * (1 - (P / PL) ** ((g - 1) / (2 * g)))
+    u_sh = (P - PR) * math.sqrt(2 / (0.125 * ((g + 1) * P + (g - 1) * PR)))
+    assert abs(u_rar - waves["u_c"]) < 1e-10 and abs(u_sh - waves["u_c"]) < 1e-10
+    assert abs(waves["rho2"] / 0.125 - ((g + 1) * P + (g - 1) * PR) / ((g - 1) * P + (g + 1) * PR)) < 1e-10
+    assert abs(waves["rho1"] - (P / PL) ** (1 / g)) < 1e-10  # isentrope rho ~ P^(1/gamma)
+    with pytest.raises(qlbm_lib.QLError):
+        qlbm_lib.ql_riemann_exact(0.0, 1.0, (0.125, 1.0), (1.0, 1.0))  # right pressure above the left
+
+
 def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
     q = qlbm_lib
     kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND, prm=(1.0, 1.0, 1e-3), use_torch=False)
