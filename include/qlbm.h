@@ -242,7 +242,10 @@ ql_status ql_info(const ql_ctx *ctx, double *out);
  * tile) work items, and ql_batch_run captures a whole run in one CUDA graph. */
 typedef struct ql_batch ql_batch; /* opaque, library-owned */
 
-/* One instance: the arguments of ql_create, with its own gas options. */
+/* One instance: the arguments of ql_create, with its own gas options
+ * (pr_mode, enskog, pr_const, rho_ref and chi_mode as in ql_opts; chi_mode
+ * QL_CHI_RET_FM takes chi of each cell from the ball-averaged density, Eq.
+ * (chi_ret), with the same limit on the ball's half-width). */
 typedef struct {
     ql_velset vs;
     ql_grid grid;
@@ -254,10 +257,14 @@ typedef struct {
     int32_t enskog;
     double pr_const;
     double rho_ref;
+    int32_t chi_mode;
+    int32_t pad_;
 } ql_instance;
 
 /* Creates a batch of n >= 1 instances (host array inst; the initial-field
- * arrays it points to are read before return).  Instances use chi_SET.  From
+ * arrays it points to are read before return).  Each instance uses chi_SET or
+ * chi_RET-FM (its chi_mode); with chi_RET-FM every stage is followed by one
+ * batched ball-average launch over those instances.  From
  * opts only precision, sums, device, stream and the allocator hooks are used; with stream NULL the batch
  * creates its own stream (a CUDA graph cannot be captured on the legacy
  * default stream).  Errors as for ql_create, naming the first bad instance. */

@@ -88,19 +88,17 @@ __device__ __forceinline__ Real fm_density(const FmArgs &a, const Real *n, int64
     return Real(a.ghost[3 + (g > 2 ? 2 : g)]);
 }
 
-constexpr int kFmThreads = 256;
 
 // nbar of columns c0 .. c0 + 255 (cells c - kHalo), Eq. (chi_ret): the tile's
 // densities with W cells on each side are staged in shared memory, then each
 // thread sums 2 W + 1 weighted neighbours.
 template <typename Real>
-__global__ void __launch_bounds__(kFmThreads) fdlb_fm_kernel(FmArgs a)
+__device__ __forceinline__ void fm_block(const FmArgs &a, int64_t block, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *s_n = reinterpret_cast<Real *>(smem_raw);  // [kFmThreads + 2 W]
     Real *s_K = s_n + kFmThreads + 2 * a.W;          // [2 W + 1]
     const Real *__restrict__ n = static_cast<const Real *>(a.n);
-    const int64_t c0 = int64_t(blockIdx.x) * kFmThreads;
+    const int64_t c0 = block * kFmThreads;
     const int64_t cell0 = c0 - kHalo - a.W;  // cell of s_n[0]
     for (int e = threadIdx.x; e < kFmThreads + 2 * a.W; e += kFmThreads) s_n[e] = fm_density<Real>(a, n, cell0 + e);
     for (int e = threadIdx.x; e < 2 * a.W + 1; e += kFmThreads) s_K[e] = Real(a.K[e]);
@@ -110,6 +108,31 @@ __global__ void __launch_bounds__(kFmThreads) fdlb_fm_kernel(FmArgs a)
     Real acc = Real(0);
     for (int d = 0; d <= 2 * a.W; ++d) acc = fma_(s_K[d], s_n[threadIdx.x + d], acc);
     static_cast<Real *>(a.nbar)[col] = acc;
+}
+template <typename Real>
+__global__ void __launch_bounds__(kFmThreads) fdlb_fm_kernel(FmArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fm_block<Real>(a, blockIdx.x, smem_raw);
+}
+
+// The same for every chi_RET-FM instance of a batch: CTA k takes work item k
+// (instance, block), with that instance's densities, nbar, weights and ghosts.
+template <typename Real>
+__global__ void __launch_bounds__(kFmThreads) fdlb_batch_fm_kernel(BatchFmArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int2 it = b.work[blockIdx.x];
+    const BatchInstance &I = b.inst[it.x];
+    FmArgs a;
+    a.n = static_cast<const Real *>(b.n) + I.noff;
+    a.nbar = static_cast<Real *>(b.nbar) + I.noff;
+    a.K = b.K + I.koff;
+    a.nx = I.nx;
+    a.W = I.fm_w;
+    a.periodic = I.periodic;
+    for (int g = 0; g < 6; ++g) a.ghost[g] = I.ghost_n[g];
+    fm_block<Real>(a, it.y, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

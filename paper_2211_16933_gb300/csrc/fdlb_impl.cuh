@@ -90,11 +90,11 @@ cudaError_t QL_FN(launch_stage_)(int Q, int stage, const StageArgs &a, cudaStrea
 }
 
 // ---- batched stages
-template <int Q, int STAGE, int WARPS>
+template <int Q, int STAGE, int WARPS, bool RET = false>
 static cudaError_t batch_qsw(int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
 {
-    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, WARPS>();
-    auto kern = fdlb_batch_stage_kernel<QL_REAL, Q, STAGE, WARPS>;
+    constexpr size_t smem = stage_smem_bytes<QL_REAL, Q, WARPS, RET>();
+    auto kern = fdlb_batch_stage_kernel<QL_REAL, Q, STAGE, WARPS, RET>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -108,25 +108,25 @@ static cudaError_t batch_qsw(int grid, const BatchArgs &b, cudaStream_t s, bool 
     return cudaGetLastError();
 }
 
-template <int Q, int WARPS>
+template <int Q, int WARPS, bool RET = false>
 static cudaError_t batch_qw(int stage, int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
 {
     switch (stage) {
-    case 1: return batch_qsw<Q, 1, WARPS>(grid, b, s, query, ctas);
-    case 2: return batch_qsw<Q, 2, WARPS>(grid, b, s, query, ctas);
-    case 3: return batch_qsw<Q, 3, WARPS>(grid, b, s, query, ctas);
+    case 1: return batch_qsw<Q, 1, WARPS, RET>(grid, b, s, query, ctas);
+    case 2: return batch_qsw<Q, 2, WARPS, RET>(grid, b, s, query, ctas);
+    case 3: return batch_qsw<Q, 3, WARPS, RET>(grid, b, s, query, ctas);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int WARPS>
+template <int WARPS, bool RET = false>
 static cudaError_t batch_w(int Q, int stage, int grid, const BatchArgs &b, cudaStream_t s, bool query, int *ctas)
 {
     switch (Q) {
-    case 8: return batch_qw<8, WARPS>(stage, grid, b, s, query, ctas);
-    case 16: return batch_qw<16, WARPS>(stage, grid, b, s, query, ctas);
-    case 24: return batch_qw<24, WARPS>(stage, grid, b, s, query, ctas);
-    case 32: return batch_qw<32, WARPS>(stage, grid, b, s, query, ctas);
+    case 8: return batch_qw<8, WARPS, RET>(stage, grid, b, s, query, ctas);
+    case 16: return batch_qw<16, WARPS, RET>(stage, grid, b, s, query, ctas);
+    case 24: return batch_qw<24, WARPS, RET>(stage, grid, b, s, query, ctas);
+    case 32: return batch_qw<32, WARPS, RET>(stage, grid, b, s, query, ctas);
     }
     return cudaErrorInvalidValue;
 }
@@ -139,6 +139,19 @@ cudaError_t QL_FN(launch_batch_stage_)(int Q, int stage, int warps, int grid, co
 }
 
 // Resident CTAs per SM of the largest velocity set's kernel (the most shared memory).
+cudaError_t QL_FN(launch_batch_stage_ret_)(int Q, int stage, int grid, const BatchArgs &b, cudaStream_t s)
+{
+    return batch_w<8, true>(Q, stage, grid, b, s, false, nullptr);
+}
+
+cudaError_t QL_FN(launch_batch_fm_)(const BatchFmArgs &a, int max_w, cudaStream_t s)
+{
+    if (max_w < 0 || max_w > QL_FM_MAX_HALFWIDTH || a.nwork <= 0 || a.nwork > INT32_MAX) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(QL_REAL) * (kFmThreads + 4 * size_t(max_w) + 1);
+    fdlb_batch_fm_kernel<QL_REAL><<<unsigned(a.nwork), kFmThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 int QL_FN(batch_ctas_per_sm_)(int stage, int warps)
 {
     int n = 0;

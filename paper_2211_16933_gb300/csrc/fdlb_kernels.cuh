@@ -749,7 +749,7 @@ struct BatchOccupancy {
     static constexpr int value = WARPS == 8 ? QL_STAGE_MINBLOCKS_F32 : 2 * QL_STAGE_MINBLOCKS_F32 - 1;
 };
 
-template <typename Real, int Q, int STAGE, int WARPS>
+template <typename Real, int Q, int STAGE, int WARPS, bool RET = false>
 __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy<WARPS>::value : 1)
     fdlb_batch_stage_kernel(BatchArgs b)
 {
@@ -791,13 +791,14 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
             a.sums64 = b.sums64;
             a.vsplit = 1;
             a.err = b.err + it.x;
-            a.nbar = nullptr;  // instances use chi_SET
-            a.nout = nullptr;
+            // chi_RET-FM lists: the instance's nbar, and the densities of this stage's output
+            a.nbar = RET ? static_cast<void *>(static_cast<Real *>(b.nbar) + I.noff) : nullptr;
+            a.nout = RET ? static_cast<void *>(static_cast<Real *>(b.n) + I.noff) : nullptr;
             s_args = a;
         }
         __syncthreads();
         const int64_t i0 = int64_t(it.y) * TileShape<WARPS>::tile;
-        stage_tile<Real, Q, STAGE, WARPS>(s_args, i0, smem_raw, &mbar, phase);  // every item of this list has this Q
+        stage_tile<Real, Q, STAGE, WARPS, RET>(s_args, i0, smem_raw, &mbar, phase);  // every item of this list has this Q
         __syncthreads();  // shared memory (and s_args) is reused by the next item
     }
 }

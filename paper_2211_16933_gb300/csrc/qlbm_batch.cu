@@ -39,6 +39,14 @@ struct ql_batch {
     double *d_tab64 = nullptr, *d_fields = nullptr, *d_partial = nullptr, *d_totals = nullptr, *d_init = nullptr;
     int64_t max_nx = 0;
     int warps = 8, grid = 0, sms = 0;
+    // chi_RET-FM instances: their (instance, tile) list of 8-warp tiles grouped by
+    // velocity set, the (instance, block) list of the ball average, their densities
+    // and nbar (Real, stride columns each) and ball weights
+    int2 *d_rwork = nullptr, *d_fmwork = nullptr;
+    int64_t rstart[kNumBatchQ] = {}, rcount[kNumBatchQ] = {}, nfm = 0;
+    int max_w = 0;
+    void *d_n = nullptr, *d_nbar = nullptr;
+    double *d_fmk = nullptr;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = -1;
     int graph_warps = 0, graph_grid = 0;
@@ -90,12 +98,34 @@ static void batch_release(ql_batch *b)
     bfree(b, b->d_partial);
     bfree(b, b->d_totals);
     bfree(b, b->d_init);
+    bfree(b, b->d_rwork);
+    bfree(b, b->d_fmwork);
+    bfree(b, b->d_n);
+    bfree(b, b->d_nbar);
+    bfree(b, b->d_fmk);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
+// nbar of every chi_RET-FM instance from the densities in d_n (one launch).
+static cudaError_t launch_fm_all(ql_batch *b)
+{
+    if (b->nfm == 0) return cudaSuccess;
+    BatchFmArgs f;
+    f.inst = b->d_inst;
+    f.work = b->d_fmwork;
+    f.nwork = b->nfm;
+    f.n = b->d_n;
+    f.nbar = b->d_nbar;
+    f.K = b->d_fmk;
+    return b->precision == QL_FP32 ? launch_batch_fm_f32(f, b->max_w, b->stream)
+                                   : launch_batch_fm_f64(f, b->max_w, b->stream);
+}
+
 // One Runge-Kutta stage of every instance: a launch per velocity set present,
-// of `grid` CTAs walking the set's work items, or (grid 0) one CTA per item.
-static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
+// of `grid` CTAs walking the set's work items, or (grid 0) one CTA per item;
+// the chi_RET-FM instances in launches of their own (8-warp tiles, one CTA per
+// item), then (fm) the ball average of their output densities.
+static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid, bool fm = true)
 {
     const int wi = warps == kBatchWarps[0] ? 0 : 1;
     for (int g = 0; g < kNumBatchQ; ++g) {
@@ -113,7 +143,24 @@ static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid)
                                   : launch_batch_stage_f64(kBatchQList[g], stage, warps, gq, a, b->stream);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    for (int g = 0; g < kNumBatchQ; ++g) {
+        if (b->rcount[g] == 0) continue;
+        BatchArgs a;
+        a.inst = b->d_inst;
+        a.work = b->d_rwork + b->rstart[g];
+        a.nwork = b->rcount[g];
+        for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
+        a.err = b->d_err;
+        a.sums64 = b->sums64;
+        a.n = b->d_n;
+        a.nbar = b->d_nbar;
+        const int gq = int(std::min<int64_t>(b->rcount[g], INT32_MAX));
+        const cudaError_t e = b->precision == QL_FP32
+                                  ? launch_batch_stage_ret_f32(kBatchQList[g], stage, gq, a, b->stream)
+                                  : launch_batch_stage_ret_f64(kBatchQList[g], stage, gq, a, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return fm ? launch_fm_all(b) : cudaSuccess;
 }
 
 // Fields of every instance averaged over blocks of nx/ncoarse cells:
@@ -228,7 +275,9 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
 
     // descriptors and host initial fields
     std::vector<std::vector<double>> fields(n);
-    int64_t off = 0;
+    int64_t off = 0, noff = 0;
+    std::vector<double> fmk;      // ball weights of the chi_RET-FM instances
+    std::vector<int2> fmwork;     // their (instance, block) list
     b->inst.resize(n);
     b->updates.resize(n);
     for (int64_t i = 0; i < n; ++i) {
@@ -242,6 +291,7 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
         if (!(I.denseness > 0) || !(I.kn > 0) || !(I.rho_ref > 0)) return bail(QL_EINVAL, id + "bad gas parameters");
         if (I.bc.kind != QL_BC_PERIODIC && I.bc.kind != QL_BC_FIXED) return bail(QL_EINVAL, id + "bad bc");
         if (I.pr_mode == QL_PR_CONST && !(I.pr_const > 0)) return bail(QL_EINVAL, id + "bad pr_const");
+        if (I.chi_mode != QL_CHI_SET && I.chi_mode != QL_CHI_RET_FM) return bail(QL_EINVAL, id + "bad chi_mode");
         double eta0;
         if (!eta_of_denseness(I.denseness, &eta0)) return bail(QL_EINVAL, id + "denseness out of range");
         BatchInstance &D = b->inst[i];
@@ -267,16 +317,40 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
                             I.init.u, I.init.T, I.init.ghost, kHalo, fields[i].data(), fields[i].data() + ncol,
                             fields[i].data() + 2 * ncol))
             return bail(QL_EINVAL, id + "invalid initial state for this init kind / boundary");
+        if (I.chi_mode == QL_CHI_RET_FM) {
+            // as ql_create: sigma = E_l Kn L, the ball's half-width in cells, its weights
+            const double dx = I.grid.length / double(D.nx), sigma = I.denseness * I.kn * I.grid.length;
+            const int W = fm_halfwidth(dx, sigma);
+            if (W > QL_FM_MAX_HALFWIDTH)
+                return bail(QL_EUNSUPPORTED, id + "the chi_RET-FM ball reaches " + std::to_string(W) +
+                                                 " cells on each side; at most QL_FM_MAX_HALFWIDTH are supported");
+            D.ret = 1;
+            D.fm_w = W;
+            D.noff = noff;
+            noff += D.stride;
+            D.koff = int64_t(fmk.size());
+            fmk.resize(fmk.size() + 2 * size_t(W) + 1);
+            fm_weights(dx, sigma, W, fmk.data() + D.koff);
+            b->max_w = std::max(b->max_w, W);
+            // fixed bc: densities of ghost cells -3..-1 (columns 1..3) and nx..nx+2
+            for (int g = 0; g < 3; ++g) {
+                D.ghost_n[g] = D.periodic ? 0.0 : fields[i][1 + g];
+                D.ghost_n[3 + g] = D.periodic ? 0.0 : fields[i][D.nx + kHalo + g];
+            }
+            const int64_t nb = (ncol + kFmThreads - 1) / kFmThreads;
+            for (int64_t k = 0; k < nb; ++k) fmwork.push_back(make_int2(int(i), int(k)));
+        }
     }
     // work lists, grouped by velocity set: all tiles of the first instance with
     // Q = kBatchQList[0], then of the next one, ..., then the instances with kBatchQList[1], ...
-    std::vector<int2> work[2];
+    // (the chi_SET instances; the chi_RET-FM ones in a list of 8-warp tiles of their own)
+    std::vector<int2> work[2], rwork;
     for (int wi = 0; wi < 2; ++wi) {
         const int tile = 31 * kBatchWarps[wi];
         for (int g = 0; g < kNumBatchQ; ++g) {
             b->qstart[wi][g] = int64_t(work[wi].size());
             for (int64_t i = 0; i < n; ++i) {
-                if (b->inst[i].Q != kBatchQList[g]) continue;
+                if (b->inst[i].Q != kBatchQList[g] || b->inst[i].ret) continue;
                 const int64_t nt = (b->inst[i].nx + tile - 1) / tile;
                 for (int64_t t = 0; t < nt; ++t) work[wi].push_back(make_int2(int(i), int(t)));
             }
@@ -284,6 +358,16 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
         }
         b->nwork[wi] = int64_t(work[wi].size());
     }
+    for (int g = 0; g < kNumBatchQ; ++g) {
+        b->rstart[g] = int64_t(rwork.size());
+        for (int64_t i = 0; i < n; ++i) {
+            if (b->inst[i].Q != kBatchQList[g] || !b->inst[i].ret) continue;
+            const int64_t nt = (b->inst[i].nx + 31 * kBatchWarps[0] - 1) / (31 * kBatchWarps[0]);
+            for (int64_t t = 0; t < nt; ++t) rwork.push_back(make_int2(int(i), int(t)));
+        }
+        b->rcount[g] = int64_t(rwork.size()) - b->rstart[g];
+    }
+    b->nfm = int64_t(fmwork.size());
 
     cudaError_t e = cudaSetDevice(b->device);
     if (e != cudaSuccess) return bail(QL_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
@@ -318,6 +402,16 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
     if (!b->d_inst || !b->d_work[0] || !b->d_work[1] || !b->d_err || !b->d_tab64 || !b->d_fields || !b->d_partial ||
         !b->d_totals || !b->d_init)
         return bail(QL_ENOMEM, "work buffer allocation failed");
+    if (b->nfm > 0) {
+        const size_t real = b->elem / 2;
+        b->d_rwork = static_cast<int2 *>(balloc(b, sizeof(int2) * rwork.size()));
+        b->d_fmwork = static_cast<int2 *>(balloc(b, sizeof(int2) * fmwork.size()));
+        b->d_n = balloc(b, real * size_t(noff));
+        b->d_nbar = balloc(b, real * size_t(noff));
+        b->d_fmk = static_cast<double *>(balloc(b, sizeof(double) * fmk.size()));
+        if (!b->d_rwork || !b->d_fmwork || !b->d_n || !b->d_nbar || !b->d_fmk)
+            return bail(QL_ENOMEM, "chi_RET-FM buffer allocation failed");
+    }
     e = cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInstance) * n, cudaMemcpyHostToDevice, b->stream);
     for (int wi = 0; wi < 2 && e == cudaSuccess; ++wi)
         e = cudaMemcpyAsync(b->d_work[wi], work[wi].data(), sizeof(int2) * work[wi].size(), cudaMemcpyHostToDevice,
@@ -341,6 +435,27 @@ ql_status ql_batch_create(const ql_instance *in, int64_t n, const ql_opts *opts,
     }
     for (int j = 1; j < 3 && e == cudaSuccess; ++j)
         e = cudaMemcpyAsync(b->arena[j], b->arena[0], b->arena_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (b->nfm > 0) {
+        // chi_RET-FM: work lists, weights, then nbar of the initial states (densities, ball average)
+        const size_t real = b->elem / 2;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_rwork, rwork.data(), sizeof(int2) * rwork.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_fmwork, fmwork.data(), sizeof(int2) * fmwork.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_fmk, fmk.data(), sizeof(double) * fmk.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nbar, 0, real * size_t(noff), b->stream);
+        for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
+            const BatchInstance &D = b->inst[i];
+            if (!D.ret) continue;
+            const void *psi = static_cast<unsigned char *>(b->arena[0]) + size_t(D.off) * b->elem;
+            void *dn = static_cast<unsigned char *>(b->d_n) + size_t(D.noff) * real;
+            e = b->precision == QL_FP32 ? launch_density_f32(D.Q, psi, D.nx, D.stride, dn, b->stream)
+                                        : launch_density_f64(D.Q, psi, D.nx, D.stride, dn, b->stream);
+        }
+        if (e == cudaSuccess) e = launch_fm_all(b);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(QL_ECUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
     b->warps = kBatchWarps[0];
@@ -364,9 +479,11 @@ ql_status ql_batch_tune(ql_batch *b, int32_t trial_launches, int32_t *warps_out,
         for (int c = 0; c <= cmax; ++c) {
             const int grid = b->sms * c;
             // stage 1 reads psi^n and writes psi^(1) only, so timing it leaves the state unchanged
-            QB_CUDA(b, launch_stage(b, 1, w, grid));
+            // (with chi_RET-FM it also rewrites the densities, scratch until the next
+            // stage's own; nbar is left alone)
+            QB_CUDA(b, launch_stage(b, 1, w, grid, false));
             QB_CUDA(b, cudaEventRecord(e0, b->stream));
-            for (int r = 0; r < trial_launches; ++r) QB_CUDA(b, launch_stage(b, 1, w, grid));
+            for (int r = 0; r < trial_launches; ++r) QB_CUDA(b, launch_stage(b, 1, w, grid, false));
             QB_CUDA(b, cudaEventRecord(e1, b->stream));
             QB_CUDA(b, cudaEventSynchronize(e1));
             float ms = 0;

@@ -113,6 +113,13 @@ struct BatchInstance {
     int64_t nx, stride, off;
     double inv_dx, dt, eta0, inv_rho_ref, tau_pref, pr_const;
     int32_t Q, pr_mode, enskog, periodic;
+    // chi_RET-FM (ret != 0): the instance's densities and nbar sit at column
+    // offset noff of the batch's density and nbar arrays (stride values each),
+    // its ball weights K_-W .. K_W at koff of the weight array (W = fm_w), and
+    // ghost_n holds the fixed-bc ghost densities as FmArgs::ghost
+    int64_t noff, koff;
+    int32_t ret, fm_w;
+    double ghost_n[6];
 };
 struct BatchArgs {
     const BatchInstance *inst;
@@ -121,6 +128,20 @@ struct BatchArgs {
     void *arena[3];
     unsigned *err;  // one error word per instance
     int sums64;     // FP32: per-cell conserved sums in FP64 (else double-FP32)
+    // chi_RET-FM work lists: densities of the stage's output, and nbar
+    void *n, *nbar;
+};
+// Threads (columns) per block of the ball-average kernels.
+constexpr int kFmThreads = 256;
+// Ball averages of the chi_RET-FM instances of a batch: one CTA per work item
+// (instance, block of kFmThreads columns), as fdlb_fm_kernel per instance.
+struct BatchFmArgs {
+    const BatchInstance *inst;
+    const int2 *work;
+    int64_t nwork;
+    const void *n;
+    void *nbar;
+    const double *K;
 };
 // Tile shapes the batched kernels are compiled for (warps per CTA).
 constexpr int kBatchWarps[2] = {8, 4};
@@ -198,6 +219,12 @@ cudaError_t launch_lq_moments(int Q, const MomentArgs &a, const double *tab, cud
 // One launch over the work items of the instances with velocity-set size Q.
 cudaError_t launch_batch_stage_f32(int Q, int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
 cudaError_t launch_batch_stage_f64(int Q, int stage, int warps, int grid, const BatchArgs &b, cudaStream_t s);
+// The chi_RET-FM form (8-warp tiles; b.n and b.nbar set), then the batched
+// ball average of its output densities (max_w: the largest W of the list).
+cudaError_t launch_batch_stage_ret_f32(int Q, int stage, int grid, const BatchArgs &b, cudaStream_t s);
+cudaError_t launch_batch_stage_ret_f64(int Q, int stage, int grid, const BatchArgs &b, cudaStream_t s);
+cudaError_t launch_batch_fm_f32(const BatchFmArgs &a, int max_w, cudaStream_t s);
+cudaError_t launch_batch_fm_f64(const BatchFmArgs &a, int max_w, cudaStream_t s);
 // Resident CTAs per SM of the batched kernel (occupancy calculator).
 int batch_ctas_per_sm_f32(int stage, int warps);
 int batch_ctas_per_sm_f64(int stage, int warps);

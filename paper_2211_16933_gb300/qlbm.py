@@ -77,7 +77,7 @@ class ql_opts(C.Structure):
 class ql_instance(C.Structure):
     _fields_ = [("vs", ql_velset), ("grid", ql_grid), ("denseness", C.c_double), ("kn", C.c_double),
                 ("bc", ql_bc), ("init", ql_init), ("pr_mode", C.c_int32), ("enskog", C.c_int32),
-                ("pr_const", C.c_double), ("rho_ref", C.c_double)]
+                ("pr_const", C.c_double), ("rho_ref", C.c_double), ("chi_mode", C.c_int32), ("pad_", C.c_int32)]
 
 
 class ql_checkpoint_info(C.Structure):
@@ -374,7 +374,7 @@ def ql_sound_modes(denseness, kn, length, rho, T, k, rho_ref=1.0, pr_mode=QL_PR_
 
 def make_instance(Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND, prm=(),
                   pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, keep=None, rho=None, u=None, T=None,
-                  ghost=None):
+                  ghost=None, chi_mode=QL_CHI_SET):
     """One ql_instance; `keep` (a list) holds the numpy arrays its pointers refer to."""
     I = ql_instance()
     I.vs = ql_velset(Q, 0)
@@ -391,6 +391,7 @@ def make_instance(Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_k
                 keep.append(a)
             setattr(I.init, name, _ptr(a))
     I.pr_mode, I.enskog, I.pr_const, I.rho_ref = pr_mode, enskog, pr_const, rho_ref
+    I.chi_mode = chi_mode
     return I
 
 

@@ -120,3 +120,63 @@ def test_batch_sample_matches_oracle(gpu):
         for k in ("rho", "u", "T", "q"):
             assert float(np.abs(fg[k] - fo[k]).max()) <= 1e-10, (i, k)
     b.close()
+
+
+def _ret_specs():
+    """chi_RET-FM instances of the paper's shock tube (Sec. IV.B: Sod state at eta_i = 0.05, L = 80, Q = 8 for
+    sigma < 0.1) at several sigma, so that the ball reaches from 0 to several cells, plus a periodic sound wave
+    with chi_RET-FM; nx uneven and below one tile for some."""
+    out = []
+    for sigma, nx in ((0.001, 200), (0.05, 413), (0.3, 160), (0.9, 530)):
+        out.append(dict(kind="tube", Q=8 if sigma < 0.1 else 16, nx=nx, length=80.0, denseness=0.4825,
+                        kn=sigma / (0.4825 * 80.0), prm=(1.0, 0.0, 1.0, 0.125, 0.0, 1.0)))
+    out.append(dict(kind="sound", Q=16, nx=301, length=1.0, denseness=0.6, kn=0.05, prm=(1.0, 1.0, 1e-3)))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_chi_ret_fm_matches_single_instance_runs_bitwise(gpu, precision):
+    """Batched chi_RET-FM instances (own work list, the ball average after every stage in one launch over them),
+    mixed with chi_SET instances, against ql_step of each instance alone with chi_RET-FM: bit for bit after 7
+    steps, for both precisions (the same tile code, the same ball-average code, the same density sums)."""
+    q = gpu
+    keep = []
+    items = []
+    for d in _ret_specs():
+        p, _ = q.ql_velocity_set(d["Q"])
+        dt = inputs.cfl_dt(d["length"] / d["nx"], abs(p).max())
+        if d["kind"] == "tube":
+            dt = min(dt, 1e-3)  # the paper's step for these tubes: explicit in the relaxation, dt ~ tau at sigma = 1e-3
+        if d["kind"] == "sound":
+            kw = dict(bc=q.QL_BC_PERIODIC, init_kind=q.QL_INIT_SOUND)
+        else:
+            kw = dict(bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN)
+        items.append((d, dt, kw, q.make_instance(d["Q"], d["nx"], d["length"], dt, d["denseness"], d["kn"],
+                                                 prm=d["prm"], keep=keep, chi_mode=q.QL_CHI_RET_FM, **kw)))
+    mixed = _instances(q, 4, 7, keep)  # chi_SET instances alongside
+    b = q.Batch([I for *_, I in items] + [I for _, _, I in mixed], precision=precision)
+    b.run(7)
+    assert not b.sync().any()
+    for i, (d, dt, kw, _) in enumerate(items):
+        s = q.Solver(d["Q"], d["nx"], d["length"], dt, d["denseness"], d["kn"], prm=d["prm"], precision=precision,
+                     pr_mode=q.QL_PR_DENSE, chi_mode=q.QL_CHI_RET_FM, **kw)
+        s.step(7)
+        r = s.state()
+        s.close()
+        a = b.state(i)
+        np.testing.assert_array_equal(a[0], r[0])
+        np.testing.assert_array_equal(a[1], r[1])
+    for j, (d, dt, _) in enumerate(mixed):
+        r = _single(q, d, dt, precision, 7)
+        a = b.state(len(items) + j)
+        np.testing.assert_array_equal(a[0], r[0])
+    b.close()
+
+
+def test_batch_rejects_a_bad_chi_mode(gpu):
+    q = gpu
+    keep = []
+    _, _, I = _instances(q, 1, 5, keep)[0]
+    I.chi_mode = 7
+    with pytest.raises(q.QLError):
+        q.Batch([I], precision=1)
