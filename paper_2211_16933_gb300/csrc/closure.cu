@@ -1166,7 +1166,10 @@ struct ql_closure {
     std::vector<bf16 *> act;  // act[0] input (bf16), act[l] output of layer l (l < L)
     float *pred = nullptr;    // last layer output f32 [B][X][16]
     std::vector<bf16 *> dz;   // dz[l]: gradient wrt pre-activation of layer l (1-based), stored bf16
-    float *partial = nullptr;
+    float *partial = nullptr;  // two halves of 2 x sms weight-gradient partials each
+    // a second stream for the end terms and partial sums of the backward pass, and its events
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> events;
     float *loss_partial = nullptr;
     float *edge = nullptr;  // [max_batch][2][64] end-position gradient terms of replicate padding
     float *norm = nullptr;  // in_shift[8], in_inv_scale[8], out_scale[8], inv_out_scale[8]
@@ -1217,6 +1220,8 @@ static void closure_release(ql_closure *c)
         cfree_dev(c, p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->side) cudaStreamDestroy(c->side);
     for (bf16 *p : c->act) cfree_dev(c, p);
     for (bf16 *p : c->dz) cfree_dev(c, p);
 }
@@ -1295,27 +1300,48 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
     const float gscale = 2.f / float(npos * c->d.out_channels);
     QC_CUDA(c, launch(mse_kernel, dim3(nb), dim3(256), 0, c->stream, c->pred, y, yidx, ystep, X, npos,
                       c->d.out_channels, c->norm + 24, gscale, c->dz[nl - 1], c->loss_partial));
+    // The weight gradients and backward-data convolutions run on c->stream; the end terms of
+    // layer l (after dz[l] is written) and the sum of layer l's weight-gradient partials (after
+    // they are written) run on a second stream beside them, joined by events: the end terms
+    // before the backward-data convolution that adds them, every partial sum before the end of
+    // the pass.  Layer l's partials sit in half l % 2 of the partial buffer, so that the next
+    // layer's weight gradient does not wait for this layer's sum.
+    cudaEvent_t *ev = c->events.data();  // per layer l: [4 l] dz[l] ready, [4 l + 1] end terms, [4 l + 2] partials
+    const size_t half = size_t(2 * c->sms) * (64 * kTaps * 64 + 64);
     for (int l = nl - 1; l >= 0; --l) {
         const Layer &L = c->layers[l];
         const int len = L.cout * kTaps * L.cin + L.cout;  // a multiple of 4 (channels are padded to 16)
         if (len % 4 != 0) return cfail(c, QL_EUNSUPPORTED, "channel padding");
+        float *part = c->partial + (l % 2) * half;
+        if (l > 0) {
+            // end terms of replicate padding for dz[l-1], beside the weight gradient
+            static_assert(kEdgeSamples * kEdgeChannels == 256, "one output per thread");
+            QC_CUDA(c, cudaEventRecord(ev[4 * l], c->stream));
+            QC_CUDA(c, cudaStreamWaitEvent(c->side, ev[4 * l], 0));
+            QC_CUDA(c, launch(edge_grad_kernel,
+                              dim3((B + kEdgeSamples - 1) / kEdgeSamples, 2, (L.cin + kEdgeChannels - 1) / kEdgeChannels),
+                              dim3(256), 0, c->side, c->dz[l], c->w16 + L.woff, per, B, X, L.cout, L.cin, c->edge));
+            QC_CUDA(c, cudaEventRecord(ev[4 * l + 1], c->side));
+        }
         int parts = 0;
-        QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->sms, c->partial, c->bad, &parts,
+        QC_CUDA(c, wgrad_any(L.cin, L.cout, c->dz[l], c->act[l], per, B, X, c->sms, part, c->bad, &parts,
                              c->stream));
         // partial layout per CTA: [cout][5 cin] then [cout]; W and b are contiguous in the parameter vector
-        QC_CUDA(c, launch(reduce_partials_kernel, dim3((len + 127) / 128), dim3(32 * kReduceWarps), 0, c->stream,
-                          c->partial, parts, len, c->grad + L.woff));
+        QC_CUDA(c, cudaEventRecord(ev[4 * l + 2], c->stream));
+        QC_CUDA(c, cudaStreamWaitEvent(c->side, ev[4 * l + 2], 0));
+        QC_CUDA(c, launch(reduce_partials_kernel, dim3((len + 127) / 128), dim3(32 * kReduceWarps), 0, c->side,
+                          part, parts, len, c->grad + L.woff));
         if (l > 0) {
             // dz[l-1] = (W^T * dz[l] + end terms of replicate padding) masked by act[l] > 0
             // (act[l] is the output of layer l-1)
-            static_assert(kEdgeSamples * kEdgeChannels == 256, "one output per thread");
-            QC_CUDA(c, launch(edge_grad_kernel,
-                              dim3((B + kEdgeSamples - 1) / kEdgeSamples, 2, (L.cin + kEdgeChannels - 1) / kEdgeChannels),
-                              dim3(256), 0, c->stream, c->dz[l], c->w16 + L.woff, per, B, X, L.cout, L.cin, c->edge));
+            QC_CUDA(c, cudaStreamWaitEvent(c->stream, ev[4 * l + 1], 0));
             QC_CUDA(c, conv_any(L.cout, L.cin, EPI_MASK_BF16, c->dz[l], c->wt16 + L.woff, nullptr, per, B, X,
                                 c->dz[l - 1], c->act[l], c->edge, c->bad, c->stream));
         }
     }
+    // the side stream's last partial sum before anything that follows on c->stream
+    QC_CUDA(c, cudaEventRecord(ev[3], c->side));
+    QC_CUDA(c, cudaStreamWaitEvent(c->stream, ev[3], 0));
     if (loss) {
         std::vector<float> h(nb);
         QC_CUDA(c, cudaMemcpyAsync(h.data(), c->loss_partial, sizeof(float) * nb, cudaMemcpyDeviceToHost, c->stream));
@@ -1381,7 +1407,11 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     c->sms = sms > 0 ? sms : 128;
-    c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(2 * c->sms) * (64 * kTaps * 64 + 64)));
+    c->partial = static_cast<float *>(calloc_dev(c, sizeof(float) * 2 * size_t(2 * c->sms) * (64 * kTaps * 64 + 64)));
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) c->side = nullptr;
+    c->events.assign(size_t(4 * d->layers), nullptr);
+    for (cudaEvent_t &e : c->events)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
     c->loss_partial = static_cast<float *>(calloc_dev(c, sizeof(float) * mse_blocks(npos)));
     c->edge = static_cast<float *>(calloc_dev(c, sizeof(float) * size_t(B) * 2 * 64));
     c->perb = static_cast<int32_t *>(calloc_dev(c, sizeof(int32_t) * size_t(B)));
@@ -1390,6 +1420,9 @@ ql_status ql_closure_create(const ql_closure_desc *d, const ql_opts *opts, ql_cl
               c->loss_partial && c->edge && c->perb && c->bad;
     for (int l = 0; l < d->layers; ++l) ok = ok && c->act[l] && c->dz[l];
     if (!ok) return bail(QL_ENOMEM, "closure allocation failed");
+    bool evok = c->side != nullptr;
+    for (cudaEvent_t e : c->events) evok = evok && e != nullptr;
+    if (!evok) return bail(QL_ECUDA, "closure stream or event creation failed");
 
     // seeded He-uniform weights (real channels only), zero biases and padding
     std::vector<float> h(off, 0.f);
