@@ -1292,7 +1292,7 @@ static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *
 
 // Loss, gradients of all parameters into c->grad; loss (host) if not null.
 static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, const int *ystep, const int *per, int B,
-                          float *loss)
+                          float *loss, float *losses = nullptr)
 {
     const int X = c->d.positions, nl = int(c->layers.size());
     const int64_t npos = int64_t(B) * X;
@@ -1306,8 +1306,17 @@ static ql_status backward(ql_closure *c, const float *y, const int32_t *yidx, co
     // before the backward-data convolution that adds them, every partial sum before the end of
     // the pass.  Layer l's partials sit in half l % 2 of the partial buffer, so that the next
     // layer's weight gradient does not wait for this layer's sum.
-    cudaEvent_t *ev = c->events.data();  // per layer l: [4 l] dz[l] ready, [4 l + 1] end terms, [4 l + 2] partials
+    // per layer l: [4 l] dz[l] ready, [4 l + 1] end terms, [4 l + 2] partials; [3] the join at the
+    // end, [4 (nl - 1) + 3] the loss partials
+    cudaEvent_t *ev = c->events.data();
     const size_t half = size_t(2 * c->sms) * (64 * kTaps * 64 + 64);
+    if (losses) {
+        // a training run's per-step loss (device array, slot *ystep), on the second stream
+        QC_CUDA(c, cudaEventRecord(ev[4 * (nl - 1) + 3], c->stream));
+        QC_CUDA(c, cudaStreamWaitEvent(c->side, ev[4 * (nl - 1) + 3], 0));
+        QC_CUDA(c, launch(loss_sum_kernel, dim3(1), dim3(256), 0, c->side, c->loss_partial, int(nb),
+                          float(1.0 / double(npos * c->d.out_channels)), losses, ystep));
+    }
     for (int l = nl - 1; l >= 0; --l) {
         const Layer &L = c->layers[l];
         const int len = L.cout * kTaps * L.cin + L.cout;  // a multiple of 4 (channels are padded to 16)
@@ -1613,19 +1622,12 @@ static ql_status enqueue_train_step(ql_closure *c, const float *x, const float *
                                     int64_t n, const int32_t *perm, int64_t B, float *losses)
 {
     const int X = c->d.positions;
-    const int64_t npos = B * X;
-    const unsigned nb = mse_blocks(npos);
-    const float lscale = float(1.0 / double(npos * c->d.out_channels));
     QC_CUDA(c, launch(pack_gather_kernel, dim3(unsigned((B * X + 255) / 256)), dim3(256), 0, c->stream, x, periodic,
                       perm, c->d_step, n, int(B), X, c->d.in_channels, c->norm, c->norm + 8, c->act[0], c->perb,
                       c->bad));
     ql_status st = forward(c, c->perb, int(B));
-    if (st == QL_OK) st = backward(c, y, perm, c->d_step, c->perb, int(B), nullptr);
+    if (st == QL_OK) st = backward(c, y, perm, c->d_step, c->perb, int(B), nullptr, losses);
     if (st != QL_OK) return st;
-    if (losses) {
-        QC_CUDA(c, launch(loss_sum_kernel, dim3(1), dim3(256), 0, c->stream, c->loss_partial, int(nb), lscale, losses,
-                          c->d_step));
-    }
     AdamArgs a = adam_args(c);
     a.step = c->d_step;
     a.lr_arr = c->d_sched;
