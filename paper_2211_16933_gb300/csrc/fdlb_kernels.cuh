@@ -47,8 +47,16 @@ __device__ __forceinline__ double2 sp2(double a) { return make_double2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b as an exact fused multiply-add
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// a - b, one packed subtraction (PTX sub.rn.f32x2: no constant pair to hold
+// in registers, unlike a fused multiply-add by -1, which rounds the same)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+    return *reinterpret_cast<float2 *>(&r);
+}
 
 __device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
@@ -88,8 +96,16 @@ __device__ __forceinline__ double exp_<double>(double x) { return exp(x); }
 
 template <typename Real>
 __device__ __forceinline__ Real rcp_(Real x);
+// FP32: the hardware reciprocal approximation alone (PTX rcp.approx.ftz.f32),
+// for normal x; __fdividef(1, x) gives the same values for the arguments used
+// here but adds a multiply and range checks to every reciprocal.
 template <>
-__device__ __forceinline__ float rcp_<float>(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp_<float>(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <>
 __device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
 
@@ -183,8 +199,8 @@ __device__ __forceinline__ FF ff_div(FF a, FF b)
 // ---------------------------------------------------------------------------
 // WENO-5 value at the interface i+1/2 for a positive advection velocity
 // (App. A.2), from f_{i-2..i+2}, for both components of the pairs.  Weights
-// are delta_q / beta_q^2 normalised, with no epsilon, evaluated in the product
-// form
+// are delta_q / beta_q^2 normalised, with no epsilon; FP32 evaluates that
+// quotient with reciprocals (below), FP64 in the product form
 //   w_q = delta_q prod_{r != q} beta_r^2 / sum_s delta_s prod_{r != s} beta_r^2,
 // equal to the quotient form wherever all beta_q > 0.  The indicators are
 // first rescaled by one exact power of two (the weights depend only on their
@@ -219,22 +235,46 @@ __device__ __forceinline__ P2<Real> weno5_face2(P2<Real> fm2, P2<Real> fm1, P2<R
     const V c2 = add2(Dm1, D0x);
     const V c3 = fma2(sp2(Real(-0.5)), D1, D0x);
     const V sc = mk2(pow2_recip_(max3_(b1.x, b2.x, b3.x)), pow2_recip_(max3_(b1.y, b2.y, b3.y)));
-    b1 = mul2(b1, sc);
-    b2 = mul2(b2, sc);
-    b3 = mul2(b3, sc);
-    const V s1 = mul2(b1, b1), s2 = mul2(b2, b2), s3 = mul2(b3, b3);
-    const V P1 = mul2(s2, s3), P2v = mul2(s1, s3), P3 = mul2(s1, s2);
-    const V D = fma2(sp2(Real(3)), P3, fma2(sp2(Real(6)), P2v, P1));
-    const V num = fma2(P1, c1, fma2(P2v, c2, mul2(P3, c3)));
-    // D = 0 only when two or three indicators vanish.  beta_q = 0 means the three
-    // values of stencil q are equal, so two vanishing indicators make the union of
-    // those stencils constant, the candidates that carry weight in Table weno_x
-    // equal f0 there, and the face value is f0: num = 0 in that case too, and D is
-    // raised to the smallest normal number so that its reciprocal stays finite
-    // (a D below it would have no finite FP32 reciprocal either).
-    const Real dmin = min_normal_<Real>();
-    const V rD = mk2(rcp_(max_(D.x, dmin)), rcp_(max_(D.y, dmin)));
-    return fma2(num, rD, f0);
+    if constexpr (sizeof(Real) == 4) {
+        // FP32: the quotient form itself, 1/beta_q^2 from the hardware reciprocal
+        // (the special-function unit has room where the FMA pipes have none).  The
+        // rescaled indicators lie in [0, 4), the largest in [1, 4); the same fused
+        // multiply-add raises each by 2^-50, which bounds 1/beta^2 by 2^100 (the
+        // numerator stays finite for differences below 2^26).  Nonzero FP32
+        // indicators of one face differ from the largest by less than 2^54, so
+        // the raise moves weight only between stencils flat to within 2^-25 of
+        // the face's largest difference, whose candidates agree to that level.
+        // A vanishing indicator gets 1/beta^2 = 2^100 against at most 1 for the
+        // largest: one zero takes all the weight and two or three share it as
+        // delta_q, the rows of Table weno_x.
+        const V e50 = sp2(Real(8.8817841970012523e-16));
+        b1 = fma2(b1, sc, e50);
+        b2 = fma2(b2, sc, e50);
+        b3 = fma2(b3, sc, e50);
+        const V r1 = mk2(rcp_(b1.x), rcp_(b1.y)), r2 = mk2(rcp_(b2.x), rcp_(b2.y)), r3 = mk2(rcp_(b3.x), rcp_(b3.y));
+        const V a1 = mul2(r1, r1), a2 = mul2(r2, r2), a3 = mul2(r3, r3);
+        const V D = fma2(sp2(Real(3)), a3, fma2(sp2(Real(6)), a2, a1));
+        const V num = fma2(a1, c1, fma2(a2, c2, mul2(a3, c3)));
+        const V rD = mk2(rcp_(D.x), rcp_(D.y));
+        return fma2(num, rD, f0);
+    } else {
+        b1 = mul2(b1, sc);
+        b2 = mul2(b2, sc);
+        b3 = mul2(b3, sc);
+        const V s1 = mul2(b1, b1), s2 = mul2(b2, b2), s3 = mul2(b3, b3);
+        const V P1 = mul2(s2, s3), P2v = mul2(s1, s3), P3 = mul2(s1, s2);
+        const V D = fma2(sp2(Real(3)), P3, fma2(sp2(Real(6)), P2v, P1));
+        const V num = fma2(P1, c1, fma2(P2v, c2, mul2(P3, c3)));
+        // D = 0 only when two or three indicators vanish.  beta_q = 0 means the three
+        // values of stencil q are equal, so two vanishing indicators make the union of
+        // those stencils constant, the candidates that carry weight in Table weno_x
+        // equal f0 there, and the face value is f0: num = 0 in that case too, and D is
+        // raised to the smallest normal number so that its reciprocal stays finite
+        // (a D below it would have no finite reciprocal either).
+        const Real dmin = min_normal_<Real>();
+        const V rD = mk2(rcp_(max_(D.x, dmin)), rcp_(max_(D.y, dmin)));
+        return fma2(num, rD, f0);
+    }
 }
 
 // Asks the TMA unit to bring `bytes` (a multiple of 16, 16-byte aligned
@@ -274,13 +314,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 // Bulk copy (TMA, no tensor map) of `bytes` from global to shared memory,
 // completion counted on `bar`; both addresses 16-byte aligned, bytes a
-// multiple of 16.
+// multiple of 16.  The lines are marked first for eviction from L2: a staged
+// row is read by its own tile and the halo of its neighbours, and leaving L2 to
+// the psi^n rows prefetched for the velocity loop measured 0.7 % faster.
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
 }
 // Orders this thread's earlier generic-proxy accesses to shared memory before
 // later async-proxy (TMA) writes to it.
@@ -701,8 +746,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
                 op = fma2(c, bp, vp);
                 om = fma2(c, bm, vm);
             }
-            out[ip] = op;
-            out[im] = om;
+            // streaming stores: the next stage reads them from memory, not from L2
+            __stcs(out + ip, op);
+            __stcs(out + im, om);
             if (own_density) s_nout[s] += op.x + om.x;
         }
     }
@@ -776,9 +822,11 @@ __global__ void __launch_bounds__(32 * WARPS, sizeof(Real) == 4 ? BatchOccupancy
             const P2<Real> *A = static_cast<const P2<Real> *>(b.arena[0]) + off;
             const P2<Real> *Bb = static_cast<const P2<Real> *>(b.arena[1]) + off;
             const P2<Real> *C = static_cast<const P2<Real> *>(b.arena[2]) + off;
+            // psi^(n+1) goes to the buffer of psi^(1), not in place (the host swaps
+            // the first two buffers after each step)
             a.in = STAGE == 1 ? A : (STAGE == 2 ? Bb : C);
             a.base = A;
-            a.out = const_cast<P2<Real> *>(STAGE == 1 ? Bb : (STAGE == 2 ? C : A));
+            a.out = const_cast<P2<Real> *>(STAGE == 2 ? C : Bb);
             a.nx = I.nx;
             a.stride = I.stride;
             a.inv_dx = I.inv_dx;

@@ -35,7 +35,12 @@ struct ql_ctx {
     ql_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
     size_t elem = 8;
-    void *buf[3] = {nullptr, nullptr, nullptr};  // psi^n, psi^(1), psi^(2)
+    // psi^n is buf[cur] (cur 0 or 1); a step's stages write psi^(1) into
+    // buf[1 - cur], psi^(2) into buf[2] and, on the tiled path, psi^(n+1) into
+    // buf[1 - cur] again (an in-place last stage, which reads and rewrites the
+    // same lines, ran about 3 % slower), after which cur flips
+    void *buf[3] = {nullptr, nullptr, nullptr};
+    int cur = 0;
     double *d_fields = nullptr;   // 6 * nx output fields
     double *d_init = nullptr;     // 3 * (nx + 2 kHalo) initial fields
     double *d_partial = nullptr;  // moment_blocks(nx) * 3
@@ -49,10 +54,10 @@ struct ql_ctx {
     double *d_fmk = nullptr;  // 2 fm_w + 1
     void *d_n = nullptr;      // nx values of the working precision
     void *d_nbar = nullptr;   // stride values (columns -kHalo .. ; the tail past nx + kHalo unused)
-    // ql_step of more than one step replays one recorded step (its launches
-    // read only buffers fixed for the context's lifetime)
+    // ql_step of more than one step replays a recorded step, one recording per
+    // value of cur (its launches read only buffers fixed for the context's lifetime)
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t step_graph = nullptr;
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
     bool step_graph_failed = false;
     int64_t steps = 0;  // steps advanced (restart files carry it)
     std::string err;
@@ -135,6 +140,14 @@ static void dev_free(ql_ctx *c, void *p)
 }
 
 static FmArgs fm_args(ql_ctx *c);
+
+// The buffer holding the current state psi^n, and the one the next step's
+// first and last stages write.
+static void *state_buf(ql_ctx *c) { return c->buf[c->cur]; }
+static void *other_buf(ql_ctx *c) { return c->buf[1 - c->cur]; }
+// Whether a step ends in the other buffer (the tiled path; the generic large-Q
+// path keeps psi^n in place).
+static bool rotates(const ql_ctx *c) { return !c->lq; }
 
 static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, void *out)
 {
@@ -224,8 +237,8 @@ static cudaError_t fm_average(ql_ctx *c)
 static cudaError_t refresh_nbar(ql_ctx *c)
 {
     if (c->chi_mode != QL_CHI_RET_FM || c->lq) return cudaSuccess;
-    cudaError_t e = c->precision == QL_FP32 ? launch_density_f32(c->Q, c->buf[0], c->nx, c->stride, c->d_n, c->stream)
-                                            : launch_density_f64(c->Q, c->buf[0], c->nx, c->stride, c->d_n, c->stream);
+    cudaError_t e = c->precision == QL_FP32 ? launch_density_f32(c->Q, state_buf(c), c->nx, c->stride, c->d_n, c->stream)
+                                            : launch_density_f64(c->Q, state_buf(c), c->nx, c->stride, c->d_n, c->stream);
     return e == cudaSuccess ? fm_average(c) : e;
 }
 
@@ -247,12 +260,12 @@ static ql_status upload_fields_and_init(ql_ctx *c, const double *rho, const doub
     memcpy(h.data() + ncol, u, sizeof(double) * ncol);
     memcpy(h.data() + 2 * ncol, T, sizeof(double) * ncol);
     QL_CUDA(c, cudaMemcpyAsync(c->d_init, h.data(), sizeof(double) * 3 * ncol, cudaMemcpyHostToDevice, c->stream));
-    cudaError_t e = c->lq ? launch_lq_init(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
+    cudaError_t e = c->lq ? launch_lq_init(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, state_buf(c), c->nx,
                                            c->stride, c->d_lqtab, c->stream)
                     : c->precision == QL_FP32
-                        ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
+                        ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, state_buf(c), c->nx,
                                           c->stride, c->d_tab64, c->stream)
-                        : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], c->nx,
+                        : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, state_buf(c), c->nx,
                                           c->stride, c->d_tab64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     QL_CUDA(c, cudaStreamSynchronize(c->stream));  // h goes out of scope
@@ -261,9 +274,10 @@ static ql_status upload_fields_and_init(ql_ctx *c, const double *rho, const doub
 
 static void destroy_buffers(ql_ctx *c)
 {
-    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    for (auto &g : c->step_graph)
+        if (g) cudaGraphExecDestroy(g);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    c->step_graph = nullptr;
+    c->step_graph[0] = c->step_graph[1] = nullptr;
     c->cap_stream = nullptr;
     for (int b = 0; b < 3; ++b) dev_free(c, c->buf[b]);
     dev_free(c, c->d_fields);
@@ -429,7 +443,8 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
         std::string m = c->err;
         return bail(st, m);
     }
-    // psi^(1), psi^(2) start as copies so their ghost columns hold the fixed states
+    // the other buffers start as copies so their ghost columns hold the fixed
+    // states (a step may leave psi^n in buf[1]; cur is 0 here)
     for (int b = 1; b < 3 && e == cudaSuccess; ++b)
         e = cudaMemcpyAsync(c->buf[b], c->buf[0], state_bytes, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -450,25 +465,27 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     return QL_OK;
 }
 
-// One step of Eq. (rk3) on c->stream: three stages and, with chi_RET-FM on the
-// tiled path, the ball average after each (each tiled stage also writes the
-// densities of its output, from which nbar for the next stage is averaged).
-static cudaError_t enqueue_step(ql_ctx *c)
+// One step of Eq. (rk3) on c->stream from psi^n in buf[cur]: three stages and,
+// with chi_RET-FM on the tiled path, the ball average after each (each tiled
+// stage also writes the densities of its output, from which nbar for the next
+// stage is averaged).  The caller flips cur afterwards when the step rotates.
+static cudaError_t enqueue_step(ql_ctx *c, int cur)
 {
     const bool ret = c->chi_mode == QL_CHI_RET_FM && !c->lq;
-    cudaError_t e = stage(c, 1, c->buf[0], c->buf[0], c->buf[1]);
+    void *S = c->buf[cur], *T1 = c->buf[1 - cur], *T2 = c->buf[2];
+    cudaError_t e = stage(c, 1, S, S, T1);
     if (e == cudaSuccess && ret) e = fm_average(c);
-    if (e == cudaSuccess) e = stage(c, 2, c->buf[1], c->buf[0], c->buf[2]);
+    if (e == cudaSuccess) e = stage(c, 2, T1, S, T2);
     if (e == cudaSuccess && ret) e = fm_average(c);
-    if (e == cudaSuccess) e = stage(c, 3, c->buf[2], c->buf[0], c->buf[0]);
+    if (e == cudaSuccess) e = stage(c, 3, T2, S, rotates(c) ? T1 : S);
     if (e == cudaSuccess && ret) e = fm_average(c);
     return e;
 }
 
-// Records one step as a CUDA graph, on a stream of the context's own (the
-// caller's may be the legacy default stream, which cannot be recorded).  A
-// recording that fails leaves the step to plain launches.
-static void record_step_graph(ql_ctx *c)
+// Records the step from buf[cur] as a CUDA graph, on a stream of the context's
+// own (the caller's may be the legacy default stream, which cannot be
+// recorded).  A recording that fails leaves the steps to plain launches.
+static void record_step_graph(ql_ctx *c, int cur)
 {
     if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         c->cap_stream = nullptr;
@@ -481,15 +498,15 @@ static void record_step_graph(ql_ctx *c)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        e = enqueue_step(c);
+        e = enqueue_step(c, cur);
         const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
         if (e == cudaSuccess) e = e2;
     }
     c->stream = user;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph[cur], g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        c->step_graph = nullptr;
+        c->step_graph[cur] = nullptr;
         c->step_graph_failed = true;
         (void)cudaGetLastError();
     }
@@ -498,13 +515,18 @@ static void record_step_graph(ql_ctx *c)
 ql_status ql_step(ql_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
-    // several steps replay one recorded step: one graph launch per step instead
+    // several steps replay a recorded step: one graph launch per step instead
     // of three to six kernel launches, which matters where launches are slow
-    if (nsteps > 1 && !c->step_graph && !c->step_graph_failed) record_step_graph(c);
-    const bool replay = nsteps > 1 && c->step_graph;
+    const bool rot = rotates(c);
+    if (nsteps > 1 && !c->step_graph_failed) {
+        if (!c->step_graph[c->cur]) record_step_graph(c, c->cur);
+        if (rot && !c->step_graph_failed && !c->step_graph[1 - c->cur]) record_step_graph(c, 1 - c->cur);
+    }
+    const bool replay = nsteps > 1 && !c->step_graph_failed;
     for (int64_t s = 0; s < nsteps; ++s) {
-        const cudaError_t e = replay ? cudaGraphLaunch(c->step_graph, c->stream) : enqueue_step(c);
+        const cudaError_t e = replay ? cudaGraphLaunch(c->step_graph[c->cur], c->stream) : enqueue_step(c, c->cur);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+        if (rot) c->cur = 1 - c->cur;
         c->steps += 1;
     }
     return QL_OK;
@@ -519,7 +541,7 @@ ql_status ql_sync(ql_ctx *c)
 static ql_status run_moments(ql_ctx *c, bool fields)
 {
     MomentArgs a;
-    a.psi = c->buf[0];
+    a.psi = state_buf(c);
     a.nx = c->nx;
     a.stride = c->stride;
     a.eta0 = c->eta0;
@@ -598,7 +620,7 @@ static ql_status download_rows(ql_ctx *c, const void *dev, double *phi, double *
 ql_status ql_get_state(ql_ctx *c, double *phi, double *theta)
 {
     if (!c) return fail(c, QL_EINVAL, "null context");
-    ql_status st = download_rows(c, c->buf[0], phi, theta);
+    ql_status st = download_rows(c, state_buf(c), phi, theta);
     if (st != QL_OK) return st;
     return check_err_word(c);
 }
@@ -621,11 +643,11 @@ ql_status ql_set_state(ql_ctx *c, const double *phi, const double *theta)
             }
         }
     }
-    QL_CUDA(c, cudaMemcpy2DAsync(static_cast<unsigned char *>(c->buf[0]) + kHalo * c->elem, c->stride * c->elem,
+    QL_CUDA(c, cudaMemcpy2DAsync(static_cast<unsigned char *>(state_buf(c)) + kHalo * c->elem, c->stride * c->elem,
                                  h.data(), nx * c->elem, nx * c->elem, Q, cudaMemcpyHostToDevice, c->stream));
     if (c->periodic) {
-        cudaError_t e = c->precision == QL_FP32 ? launch_periodic_ghosts_f32(Q, c->buf[0], nx, c->stride, c->stream)
-                                                : launch_periodic_ghosts_f64(Q, c->buf[0], nx, c->stride, c->stream);
+        cudaError_t e = c->precision == QL_FP32 ? launch_periodic_ghosts_f32(Q, state_buf(c), nx, c->stride, c->stream)
+                                                : launch_periodic_ghosts_f64(Q, state_buf(c), nx, c->stride, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "ghost kernel");
     }
     QL_CUDA(c, refresh_nbar(c));
@@ -660,12 +682,12 @@ ql_status ql_load_fields(ql_ctx *c, const double *rho, const double *u, const do
         QL_CUDA(c, cudaMemcpyAsync(c->d_init + f * ncol + kHalo + nx, gh[f] + kHalo, sizeof(double) * kHalo,
                                    cudaMemcpyHostToDevice, c->stream));
     }
-    cudaError_t e = c->lq ? launch_lq_init(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
+    cudaError_t e = c->lq ? launch_lq_init(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, state_buf(c), nx,
                                            c->stride, c->d_lqtab, c->stream)
                     : c->precision == QL_FP32
-                        ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
+                        ? launch_init_f32(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, state_buf(c), nx,
                                           c->stride, c->d_tab64, c->stream)
-                        : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, c->buf[0], nx,
+                        : launch_init_f64(c->Q, c->d_init, c->d_init + ncol, c->d_init + 2 * ncol, state_buf(c), nx,
                                           c->stride, c->d_tab64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     QL_CUDA(c, refresh_nbar(c));
@@ -676,9 +698,9 @@ ql_status ql_load_fields(ql_ctx *c, const double *rho, const double *u, const do
 ql_status ql_rhs(ql_ctx *c, double *Lphi, double *Ltheta)
 {
     if (!c) return fail(c, QL_EINVAL, "null context");
-    cudaError_t e = stage(c, 0, c->buf[0], c->buf[0], c->buf[1]);
+    cudaError_t e = stage(c, 0, state_buf(c), state_buf(c), other_buf(c));
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
-    ql_status st = download_rows(c, c->buf[1], Lphi, Ltheta);
+    ql_status st = download_rows(c, other_buf(c), Lphi, Ltheta);
     if (st != QL_OK) return st;
     return check_err_word(c);
 }
@@ -686,7 +708,7 @@ ql_status ql_rhs(ql_ctx *c, double *Lphi, double *Ltheta)
 ql_status ql_state_device(ql_ctx *c, void **phi, int64_t *row_stride)
 {
     if (!c || !phi || !row_stride) return fail(c, QL_EINVAL, "bad arguments to ql_state_device");
-    *phi = static_cast<unsigned char *>(c->buf[0]) + kHalo * c->elem;
+    *phi = static_cast<unsigned char *>(state_buf(c)) + kHalo * c->elem;
     *row_stride = c->stride;
     return QL_OK;
 }

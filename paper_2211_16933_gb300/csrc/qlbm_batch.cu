@@ -47,9 +47,15 @@ struct ql_batch {
     int max_w = 0;
     void *d_n = nullptr, *d_nbar = nullptr;
     double *d_fmk = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int64_t graph_steps = -1;
-    int graph_warps = 0, graph_grid = 0;
+    // A step writes psi^(n+1) into the buffer that held psi^(1) (a last stage
+    // writing in place ran about 3 % slower), and arena[0] and arena[1] swap on
+    // the host, so that arena[0] always holds the state.  A run recorded as a
+    // CUDA graph is kept per buffer order (swapped: arena[0] is the second
+    // allocation) and per step count and CTA shape.
+    bool swapped = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_steps[2] = {-1, -1};
+    int graph_warps[2] = {0, 0}, graph_grid[2] = {0, 0};
     std::string err;
 };
 
@@ -88,7 +94,8 @@ static void bfree(ql_batch *b, void *p)
 
 static void batch_release(ql_batch *b)
 {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto &g : b->graph)
+        if (g) cudaGraphExecDestroy(g);
     for (int j = 0; j < 3; ++j) bfree(b, b->arena[j]);
     for (int j = 0; j < 2; ++j) bfree(b, b->d_work[j]);
     bfree(b, b->d_inst);
@@ -124,9 +131,12 @@ static cudaError_t launch_fm_all(ql_batch *b)
 // One Runge-Kutta stage of every instance: a launch per velocity set present,
 // of `grid` CTAs walking the set's work items, or (grid 0) one CTA per item;
 // the chi_RET-FM instances in launches of their own (8-warp tiles, one CTA per
-// item), then (fm) the ball average of their output densities.
-static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid, bool fm = true)
+// item), then (fm) the ball average of their output densities.  With par = 1
+// the stage runs from arena[1] as psi^n (the odd steps of a run: each step
+// leaves the state in the other of the first two buffers).
+static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid, bool fm = true, int par = 0)
 {
+    void *const order[3] = {b->arena[par], b->arena[1 - par], b->arena[2]};
     const int wi = warps == kBatchWarps[0] ? 0 : 1;
     for (int g = 0; g < kNumBatchQ; ++g) {
         if (b->qcount[wi][g] == 0) continue;
@@ -135,7 +145,7 @@ static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid, boo
         a.inst = b->d_inst;
         a.work = b->d_work[wi] + b->qstart[wi][g];
         a.nwork = b->qcount[wi][g];
-        for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
+        for (int j = 0; j < 3; ++j) a.arena[j] = order[j];
         a.err = b->d_err;
         a.sums64 = b->sums64;
         const cudaError_t e = b->precision == QL_FP32
@@ -149,7 +159,7 @@ static cudaError_t launch_stage(ql_batch *b, int stage, int warps, int grid, boo
         a.inst = b->d_inst;
         a.work = b->d_rwork + b->rstart[g];
         a.nwork = b->rcount[g];
-        for (int j = 0; j < 3; ++j) a.arena[j] = b->arena[j];
+        for (int j = 0; j < 3; ++j) a.arena[j] = order[j];
         a.err = b->d_err;
         a.sums64 = b->sums64;
         a.n = b->d_n;
@@ -520,29 +530,35 @@ ql_status ql_batch_run(ql_batch *b, int64_t nsteps)
 {
     if (!b || nsteps < 0) return bfail(b, QL_EINVAL, "bad arguments to ql_batch_run");
     if (nsteps == 0) return QL_OK;
-    if (!b->graph || b->graph_steps != nsteps || b->graph_warps != b->warps || b->graph_grid != b->grid) {
-        if (b->graph) {
-            cudaGraphExecDestroy(b->graph);
-            b->graph = nullptr;
+    const int o = b->swapped ? 1 : 0;
+    if (!b->graph[o] || b->graph_steps[o] != nsteps || b->graph_warps[o] != b->warps || b->graph_grid[o] != b->grid) {
+        if (b->graph[o]) {
+            cudaGraphExecDestroy(b->graph[o]);
+            b->graph[o] = nullptr;
         }
         QB_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s)
-            for (int st = 1; st <= 3 && e == cudaSuccess; ++st) e = launch_stage(b, st, b->warps, b->grid);
+            for (int st = 1; st <= 3 && e == cudaSuccess; ++st)
+                e = launch_stage(b, st, b->warps, b->grid, true, int(s & 1));
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return bcuda(b, e != cudaSuccess ? e : e2, "graph capture");
         }
-        e = cudaGraphInstantiate(&b->graph, g, 0);
+        e = cudaGraphInstantiate(&b->graph[o], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
-        b->graph_steps = nsteps;
-        b->graph_warps = b->warps;
-        b->graph_grid = b->grid;
+        b->graph_steps[o] = nsteps;
+        b->graph_warps[o] = b->warps;
+        b->graph_grid[o] = b->grid;
     }
-    QB_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    QB_CUDA(b, cudaGraphLaunch(b->graph[o], b->stream));
+    if (nsteps & 1) {
+        std::swap(b->arena[0], b->arena[1]);
+        b->swapped = !b->swapped;
+    }
     return QL_OK;
 }
 
