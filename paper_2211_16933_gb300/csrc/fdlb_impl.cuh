@@ -11,10 +11,25 @@
 
 namespace qlbm {
 
+// The stage kernels' copy of the tables: as built, except that the
+// equilibrium rows are G[k][l] / sqrt(l!) = w_k He_l(p_k) / l! and cb[l] holds
+// l - 1, for the coefficients d_l = l! c_l of Eq. (g_alpha), whose recurrence
+// d_l = u d_{l-1} + (l - 1)(T - 1) d_{l-2} takes one operation less per
+// coefficient than that of the normalised c^_l.
 cudaError_t QL_FN(upload_tables_)(const double *all)
 {
     static QL_REAL host[kTabTotal];
     for (int e = 0; e < kTabTotal; ++e) host[e] = QL_REAL(all[e]);
+    for (int j = 0; j < kNumQ; ++j) {
+        const int Q = kQList[j];
+        const TabView tv = tab_view(Q);
+        double isf = 1.0;  // 1 / sqrt(l!)
+        for (int l = 0; l < Q; ++l) {
+            if (l > 0) isf /= sqrt(double(l));
+            for (int k = 0; k < Q; ++k) host[tv.G + k * Q + l] = QL_REAL(all[tv.G + k * Q + l] * isf);
+            host[tv.cb + l] = QL_REAL(l >= 2 ? l - 1 : 0);
+        }
+    }
     return cudaMemcpyToSymbol(QL_TAB, host, sizeof(host));
 }
 
@@ -45,8 +60,20 @@ static cudaError_t stage_q(const StageArgs &a, cudaStream_t s)
         const int64_t v = resident[dev & 63] / nt;
         b.vsplit = int(v < Q / 2 ? v : Q / 2);
     }
-    kern<<<dim3(unsigned(nt * b.vsplit)), dim3(kThreads), smem, s>>>(b);
-    cudaError_t e = cudaGetLastError();
+    // programmatic stream serialisation: the launch may overlap the tail of the
+    // previous kernel in the stream, which the kernel waits for before its
+    // first access to memory
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(nt * b.vsplit));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, b);
     if (e == cudaSuccess && RET && STAGE != 0 && b.vsplit > 1)
         e = QL_FN(launch_density_)(Q, b.out, b.nx, b.stride, b.nout, s);
     return e;

@@ -648,9 +648,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
         D2 = fma2(mu, D3, D2);
     }
 
-    // Normalised Hermite coefficients of the equilibrium, Eq. (g_alpha):
-    // c^_0 = 1, c^_1 = u, c^_l = u c^_{l-1}/sqrt(l) + (T-1) c^_{l-2} sqrt((l-1)/l),
-    // held as pairs (c^_{2m}, c^_{2m+1}).
+    // Hermite coefficients of the equilibrium, Eq. (g_alpha), scaled as
+    // d_l = l! c_l: d_0 = 1, d_1 = u, d_l = u d_{l-1} + (l-1)(T-1) d_{l-2} (the
+    // factor l - 1 from the table; its equilibrium rows carry the 1/l!), held as
+    // pairs (d_{2m}, d_{2m+1}).
     V ch[H];
     {
         Real cm2 = Real(1), cm1 = u;
@@ -658,8 +659,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &a, const int64_t i0,
         const Real Tm1 = T - Real(1);
 #pragma unroll
         for (int m = 1; m < H; ++m) {
-            const Real ce = fma_(QL_TAB[TV.ca + 2 * m] * u, cm1, QL_TAB[TV.cb + 2 * m] * Tm1 * cm2);
-            const Real co = fma_(QL_TAB[TV.ca + 2 * m + 1] * u, ce, QL_TAB[TV.cb + 2 * m + 1] * Tm1 * cm1);
+            const Real ce = fma_(u, cm1, (QL_TAB[TV.cb + 2 * m] * Tm1) * cm2);
+            const Real co = fma_(u, ce, (QL_TAB[TV.cb + 2 * m + 1] * Tm1) * cm1);
             ch[m] = mk2(ce, co);
             cm2 = ce;
             cm1 = co;
@@ -783,6 +784,13 @@ __global__ void __launch_bounds__(kThreads, StageOccupancy<Real, Q>::value) fdlb
         if (threadIdx.x == 0) mbar_init(&mbar);
         __syncthreads();
     }
+    // Programmatic dependent launch (the solver launches its stages that way):
+    // the next stage may be scheduled once every CTA of this one has started,
+    // and this one reads or writes no state before the previous kernel in the
+    // stream has completed (a no-op for plain launches).  Each stage waits for
+    // its predecessor, so a stage's start implies that all earlier ones ended.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int vs = sizeof(Real) == 8 ? a.vsplit : 1;
     const int64_t tile = int64_t(blockIdx.x) / vs;
     const int part = int(int64_t(blockIdx.x) - tile * vs);

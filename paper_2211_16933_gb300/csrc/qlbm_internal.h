@@ -56,6 +56,8 @@ inline int64_t row_stride(int64_t nx) { return (nx + 256 + 2 * kHalo + 31) / 32 
 //   ca[l] = 1/sqrt(l), cb[l] = sqrt((l-1)/l)  (l >= 2), for the recurrence of
 //   the normalised equilibrium coefficients c^_l = c_l sqrt(l!):
 //   c^_0 = 1, c^_1 = u, c^_l = ca[l] u c^_{l-1} + cb[l] (T-1) c^_{l-2}.
+// The stage kernels' constant-bank copy rescales G[k][l] by 1/sqrt(l!) and
+// holds l - 1 in cb[l] (upload_tables_f32/f64).
 QL_HD constexpr int tab_size(int Q) { return Q * Q + 5 * Q; }
 QL_HD constexpr int tab_offset(int Q)
 {
