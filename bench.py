@@ -87,7 +87,7 @@ def _flops_per_update(precision_name, Q=32):
         t = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_flops.json")))
         e = t.get(precision_name)
         if e and e.get("kernel_hash") == _kernel_hash(precision_name) and e.get("Q") == Q:
-            return float(sum(e["flop_per_update_per_stage"]))
+            return float(e["flop_per_update"])
     except Exception:
         pass
     return None
@@ -98,7 +98,7 @@ def _flops_per_update(precision_name, Q=32):
 ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12}
 
 
-def _alu_roofline(precision_name, updates_per_s, Q=32):
+def _alu_roofline(precision_name, updates_per_s, Q=32, kernel="fdlb_stage_kernel"):
     f = _flops_per_update(precision_name, Q)
     if f is None:
         return None
@@ -106,18 +106,18 @@ def _alu_roofline(precision_name, updates_per_s, Q=32):
     peak = ALU_PEAK_TFLOPS[precision_name]
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "peak_source": "derived from unit counts and the maximum SM clock",
-            "flop_per_update": f, "kernel": "fdlb_stage_kernel"}
+            "flop_per_update": f, "kernel": kernel}
 
 
-def _traffic(precision_name, Q=32, nx=1 << 22):
-    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on this kernel source and
-    scaled to this workload's size."""
+def _traffic_per_step(precision_name, Q=32, nx=1 << 22):
+    """DRAM bytes per step from the committed ncu summary, if it was taken on this kernel source and scaled
+    to this workload's size."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
         e = t.get(precision_name)
         if (e and e.get("kernel_hash") == _kernel_hash(precision_name) and e.get("Q") == Q
                 and e.get("scaled_to_nx") == nx):
-            return e["dram_bytes_per_launch"]
+            return e["dram_bytes_per_step"]
     except Exception:
         pass
     return None
@@ -274,34 +274,48 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def _hbm_roofline(elem, nx, Q, step_s, precision_name):
-    """Stage kernel against the measured copy bandwidth: 16 words of phi and theta per update per step
-    (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2), per launch = a third of the step."""
+def _hbm_roofline(elem, nx, Q, step_s, precision_name, steps_per_launch, kernel):
+    """The stepping kernel against the measured copy bandwidth: 16 words of phi and theta per update per step
+    (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2).  fdlb_run_kernel: one launch runs
+    steps_per_launch steps; fdlb_stage_kernel: one launch is one stage, a third of a step."""
     bytes_per_step = 16 * elem * nx * Q
-    achieved = bytes_per_step / 3 / (step_s / 3) / 1e9
+    launches_per_step = 1.0 / steps_per_launch if kernel == "fdlb_run_kernel" else 3.0
+    achieved = bytes_per_step / step_s / 1e9
     peaks = _peaks()
     if peaks and "hbm_gbs" in peaks:
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
+    tr = _traffic_per_step(precision_name, Q, nx)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(precision_name, Q, nx), "peak_source": peak_src,
-            "algorithmic_bytes_per_launch": bytes_per_step / 3, "launches_per_step": 3, "kernel": "fdlb_stage_kernel"}
+            "traffic": None if tr is None else tr / launches_per_step, "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": bytes_per_step / launches_per_step,
+            "launches_per_step": launches_per_step, "kernel": kernel}
 
 
-def _timed_steps(s, steps, warmup, stream):
-    """Per-step times (ms) of `steps` single steps after `warmup`, CUDA events on the solver's stream."""
+def _stepping(q, s, steps):
+    """The kernel a solver's step calls launch, and how many launches `steps` steps in one call take."""
+    per = s.steps_per_launch()
+    if per > 0:
+        return "fdlb_run_kernel", -(-steps // per)
+    return "fdlb_stage_kernel", 3 * steps
+
+
+_LAUNCH = {"auto": lambda q: q.QL_LAUNCH_AUTO, "run": lambda q: q.QL_LAUNCH_RUN,
+           "stages": lambda q: q.QL_LAUNCH_STAGES}
+
+
+def _timed_run(s, steps, warmup, stream):
+    """Time (ms) of `steps` steps in one call after `warmup` steps, CUDA events on the solver's stream."""
     import torch
-    for _ in range(warmup):
-        s.step(1)
+    s.step(warmup)
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    ev[0].record(stream)
-    for k in range(steps):
-        s.step(1)
-        ev[k + 1].record(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
     torch.cuda.synchronize()
-    return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return e0.elapsed_time(e1)
 
 
 def _forms(args, w, window, q, inputs, dev, stream):
@@ -316,19 +330,21 @@ def _forms(args, w, window, q, inputs, dev, stream):
                                     ("fp64", q.QL_FP64, q.QL_SUMS_DFP32, min(args.steps, args.fp64_steps))):
         s = q.Solver(Q, nx, w["length"], dt, w["denseness"], w["kn"], bc=q.QL_BC_FIXED,
                      init_kind=q.QL_INIT_RIEMANN, prm=w["prm"], precision=prec, pr_mode=q.QL_PR_DENSE, device=dev,
-                     sums=sums)
-        ms = _timed_steps(s, steps, min(args.warmup, 3), stream)
+                     sums=sums, launch=_LAUNCH[args.launch](q))
+        ms = _timed_run(s, steps, max(3, min(args.warmup, 3)), stream)
+        kern, launches = _stepping(q, s, steps)
         s.close()
         del s
         torch.cuda.empty_cache()
-        step_s = sum(ms) * 1e-3 / steps
+        step_s = ms * 1e-3 / steps
         elem = 4 if prec == q.QL_FP32 else 8
         pname = "fp32" if prec == q.QL_FP32 else "fp64"
         rec = {"value": nx * Q / step_s, "unit": "updates/s", "steps": steps, "ms_per_step": step_s * 1e3,
                "dtype": "f32" if prec == q.QL_FP32 else "f64",
                "sums": "f64 per-cell conserved sums" if sums == q.QL_SUMS_FP64 or prec == q.QL_FP64 else "double-f32",
-               "roofline_hbm": _hbm_roofline(elem, nx, Q, step_s, pname),
-               "roofline_alu": _alu_roofline(pname, nx * Q / step_s, Q)}
+               "roofline_hbm": _hbm_roofline(elem, nx, Q, step_s, pname, steps / launches, kern),
+               "roofline_alu": _alu_roofline(pname, nx * Q / step_s, Q, kern), "kernel": kern,
+               "gpu_launches": launches}
         if window is not None:
             rec["errors_vs_oracle"] = _errors_vs_oracle(window, prec, sums)
         out[name] = rec
@@ -380,7 +396,7 @@ def run_ours(args, w):
     pmax = float(np.abs(q.ql_velocity_set(Q)[0]).max())
     dt = inputs.cfl_dt(w["length"] / nx, pmax)
     s = q.Solver(Q, nx, w["length"], dt, w["denseness"], w["kn"], bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_RIEMANN,
-                 prm=w["prm"], precision=prec, pr_mode=q.QL_PR_DENSE, device=dev)
+                 prm=w["prm"], precision=prec, pr_mode=q.QL_PR_DENSE, device=dev, launch=_LAUNCH[args.launch](q))
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -388,29 +404,28 @@ def run_ours(args, w):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # --- device-resident throughput: K timed steps, each 3 stage launches
-    for _ in range(args.warmup):
-        s.step(1)
+    # --- device-resident throughput: K timed steps in one call (one launch of the whole-run kernel, or three
+    # stage launches per step)
+    s.step(args.warmup)
     barrier()
     clk = ClockSampler(dev)
     clk.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    for k in range(args.steps):
-        s.step(1)
-        ev[k + 1].record(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
     barrier()
     clocks = clk.stop()
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
+    total_ms = e0.elapsed_time(e1)
     s.sync()
     max_ms = max_over_ranks(total_ms, ws)
     value = whole_job_rate(nx * Q * args.steps, ws, max_ms * 1e-3)
+    kern, launches = _stepping(q, s, args.steps)
 
-    # roofline of the stage kernel: algorithmic bytes = 16 words per update per step
-    hbm_roofline = _hbm_roofline(elem, nx, Q, total_ms * 1e-3 / args.steps, args.precision)
-    # the per-launch update rate is the step's (three launches of the same cells)
-    alu_roofline = _alu_roofline(args.precision, nx * Q * args.steps / (total_ms * 1e-3), Q)
+    # roofline of the stepping kernel: algorithmic bytes = 16 words per update per step
+    hbm_roofline = _hbm_roofline(elem, nx, Q, total_ms * 1e-3 / args.steps, args.precision,
+                                 args.steps / launches, kern)
+    alu_roofline = _alu_roofline(args.precision, nx * Q * args.steps / (total_ms * 1e-3), Q, kern)
     # FP32: the metric's HBM roofline, the FP32-pipe view beside it; FP64: bound by GB300's FP64 rate
     if args.precision == "fp64" and alu_roofline is not None:
         roofline, other_roofline = alu_roofline, hbm_roofline
@@ -470,8 +485,7 @@ def run_ours(args, w):
                                2 * Q * nx * elem / 2 ** 30)},
                 "roofline": roofline, "roofline_other": other_roofline, "cpu_baseline": cpu,
                 "errors_vs_oracle": errors, "e2e": e2e, "forms": forms,
-                "gpu_launches": 3 * args.steps,
-                "clocks": clocks, "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+                "gpu_launches": launches, "kernel": kern, "launch": args.launch, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -671,6 +685,44 @@ def run_learned(args):
                                  "err_vs_fp64_fine": {"coarse_plus_net": L.field_errors(learned, ref),
                                                       "fine_fp32_batch": L.field_errors(fine32, ref)}}}
     print(json.dumps(line), flush=True)
+
+
+def run_launch_sizes(args):
+    """Step time of the whole-run launch against per-stage launches across domain sizes (FP32 Sod tube): per row,
+    5 warm-up steps, then K steps in one ql_step(K) call between two CUDA events, best of 3, each launch mode on
+    a solver of its own.  One JSON line per row, then a summary line."""
+    import torch
+    from paper_2211_16933_gb300 import build as B
+    from paper_2211_16933_gb300 import inputs
+    from paper_2211_16933_gb300 import qlbm as q
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for Q, nx in ((8, 1600), (32, 1600), (32, 8192), (32, 32768), (32, 131072), (32, 524288), (32, 2097152),
+                  (32, 4194304)):
+        K = min(5000, max(20, int(3e8 / (nx * Q))))
+        p, _ = q.ql_velocity_set(Q)
+        dt = inputs.cfl_dt(1.0 / nx, float(np.abs(p).max()))
+        w = inputs.sod_tube(nx=nx, Q=Q)
+        row = {"Q": Q, "nx": nx, "K": K}
+        for name, lm in (("stages", q.QL_LAUNCH_STAGES), ("run", q.QL_LAUNCH_RUN), ("auto", q.QL_LAUNCH_AUTO)):
+            s = q.Solver(Q, nx, w["length"], dt, w["denseness"], w["kn"], bc=q.QL_BC_FIXED,
+                         init_kind=q.QL_INIT_RIEMANN, prm=w["prm"], precision=q.QL_FP32, pr_mode=q.QL_PR_DENSE,
+                         launch=lm)
+            best = float("inf")
+            for _ in range(3):
+                best = min(best, _timed_run(s, K, 5, stream) / K)
+            if name == "auto":
+                row["auto_picks"] = "run" if s.steps_per_launch() > 0 else "stages"
+            s.sync()
+            s.close()
+            row[name + "_ms_per_step"] = best
+        row["run_over_stages"] = row["run_ms_per_step"] / row["stages_ms_per_step"]
+        print(json.dumps(row), flush=True)
+        rows.append(row)
+    print(json.dumps({"metric": "ms per step by launch mode", "workload": "launch_sizes", "rows": len(rows),
+                      "data": "synthetic"}), flush=True)
 
 
 def run_dispersion(args):
@@ -909,6 +961,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--launch", choices=["auto", "run", "stages"], default="auto",
+                    help="ql_opts.launch: auto (the library picks by domain size), run (one launch per step call), "
+                         "stages (one launch per Runge-Kutta stage)")
     ap.add_argument("--nx", type=int, default=1 << 22)
     ap.add_argument("--q", type=int, default=32)
     ap.add_argument("--cpu-steps", type=int, default=6)
@@ -917,7 +972,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-with-FP64-sums, FP64 and batch sub-records")
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--workload", choices=["sod", "batch", "learned", "dispersion", "paper_table", "standing_shock",
-                                           "inviscid"], default="sod")
+                                           "inviscid", "launch_sizes"], default="sod")
     ap.add_argument("--inviscid-t", type=float, default=0.05)
     ap.add_argument("--shock-steps", type=int, default=1_200_000)
     ap.add_argument("--table-steps", type=int, default=9000)
@@ -952,6 +1007,9 @@ def main():
         return
     if args.workload == "inviscid" and args.impl == "ours":
         run_inviscid(args)
+        return
+    if args.workload == "launch_sizes" and args.impl == "ours":
+        run_launch_sizes(args)
         return
     if args.impl == "reference":
         run_reference(args, w)

@@ -51,6 +51,7 @@ typedef enum {
 
 enum { QL_FP64 = 0, QL_FP32 = 1 };              /* arithmetic of the state and its update */
 enum { QL_SUMS_DFP32 = 0, QL_SUMS_FP64 = 1 };   /* FP32 mode: per-cell conserved sums */
+enum { QL_LAUNCH_AUTO = 0, QL_LAUNCH_STAGES = 1, QL_LAUNCH_RUN = 2 }; /* how ql_step launches (ql_opts.launch) */
 enum { QL_BC_PERIODIC = 0, QL_BC_FIXED = 1 };   /* boundary of the 1D domain */
 enum { QL_INIT_SOUND = 0, QL_INIT_RIEMANN = 1, QL_INIT_SHOCK = 2, QL_INIT_FIELDS = 3 };
 enum { QL_PR_CONST = 0, QL_PR_DENSE = 1 };
@@ -150,6 +151,18 @@ typedef void (*ql_free_fn)(void *ptr, void *user);
  *              CTA's bounded wait gives up (no copy is in flight, nothing
  *              faults) and the next synchronising call returns QL_ECUDA
  *              ("gave up waiting"); the state is left as it was.
+ *   launch     How ql_step launches the stages of FP32 chi_SET solvers of the
+ *              tiled velocity sets (Q = 8, 16, 20, 24, 32, 40); other solvers
+ *              always launch per stage.  QL_LAUNCH_STAGES: one launch per
+ *              Runge-Kutta stage (ql_step of several steps replays a recorded
+ *              step).  QL_LAUNCH_RUN: each ql_step call is one launch of
+ *              (stage, tile) work items, a tile's stage starting once the
+ *              previous stage of it and of its neighbours has completed, so
+ *              that consecutive stages and steps overlap.  QL_LAUNCH_AUTO (0,
+ *              default): QL_LAUNCH_RUN for domains of one to eight times as
+ *              many tiles (248 cells each) as the GPU holds CTAs at once, where
+ *              a stage's last wave of CTAs leaves much of the GPU idle, and
+ *              QL_LAUNCH_STAGES otherwise.  Results are the same bit for bit.
  *   stream     cudaStream_t for all work, NULL for the legacy default stream. */
 typedef struct {
     int32_t precision;
@@ -159,7 +172,7 @@ typedef struct {
     int32_t chi_mode;
     int32_t fault;
     int32_t sums;
-    int32_t pad_;
+    int32_t launch;
     double pr_const;
     double rho_ref;
     void *stream;
@@ -233,6 +246,12 @@ ql_status ql_state_device(ql_ctx *ctx, void **psi, int64_t *row_stride);
  * out[2] = sigma, out[3] = dx, out[4] = dt, out[5] = max |p_k|,
  * out[6..6+Q) = p_k, out[6+Q..6+2Q) = w_k.  out holds 6 + 2Q doubles. */
 ql_status ql_info(const ql_ctx *ctx, double *out);
+
+/* How ql_step launches (no counterpart in the paper; for timing tools):
+ * *steps_per_launch = the most steps one launch of the whole-run kernel covers
+ * (ql_opts.launch), or 0 when the solver launches one kernel per Runge-Kutta
+ * stage.  QL_EINVAL for a null argument. */
+ql_status ql_launch_info(const ql_ctx *ctx, int64_t *steps_per_launch);
 
 /* ---- Batched form -------------------------------------------------------- */
 

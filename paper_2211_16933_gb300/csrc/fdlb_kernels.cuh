@@ -797,6 +797,132 @@ __global__ void __launch_bounds__(kThreads, StageOccupancy<Real, Q>::value) fdlb
     stage_tile<Real, Q, STAGE, kWarps, RET>(a, tile * kTile, smem_raw, &mbar, 0u, part, vs);
 }
 
+// ---------------------------------------------------------------------------
+// A run of steps in one launch (FP32, chi_SET).  With one launch per stage,
+// each stage waits for the slowest CTA of the one before, and its first wave
+// of CTAs stages its tiles all at once.  Here CTA b of the launch takes ticket
+// b, tile b mod N of stage b / N of the run (N tiles), and starts as soon as
+// the previous stage of the tiles it reads has completed, so consecutive
+// stages overlap.
+//
+// Dependencies of stage g of tile i: stage g - 1 of tiles i - 1, i and i + 1
+// (modulo N with a periodic boundary; there tiles 0 and N - 2 also depend on
+// each other, because when the last tile holds fewer cells than the halo, tile
+// N - 2 stages ghost images that tile 0 writes and writes some that tile 0
+// stages).  Overwrites are ordered by the same chain: whoever read a buffer's
+// cells at stage g - 1 is a tile that the writer at stage g waits for, and
+// readers at earlier stages completed before those.
+//
+// Ordering: a tile's stores (all threads, then a CTA barrier) are published by
+// thread 0 as the tile's count of completed stages (counted from the solver's
+// first run), a release store at GPU scope.  A consumer's thread 0 reads the counts with acquire loads, then
+// orders its staging copies (async proxy) after them; its other threads read
+// after CTA barriers.
+//
+// Progress: a ticket's dependencies hold smaller tickets, that is CTAs of
+// smaller index, which the hardware starts first (one-dimensional grids are
+// dispatched in index order, the assumption single-pass scans with
+// look-back also make), so the smallest unfinished ticket always has what it
+// needs.  Waits are bounded all the same: a CTA that gives up sets bit 2 of
+// the error word and returns, and every CTA that finds the bit while waiting
+// returns too (the state is then invalid and the host reports the error).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Orders this thread's earlier generic-proxy view of global memory before its
+// later async-proxy (TMA) reads.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// True once stage g - 1 of every tile that stage g of `tile` reads has
+// completed (always for the run's first stage).
+// Counts are kept modulo 2^32: count c has reached stage s when the signed
+// difference c - s is not negative.
+__device__ __forceinline__ bool reached_(unsigned c, unsigned s) { return int(c - s) >= 0; }
+__device__ __forceinline__ bool run_ready(const unsigned *d, unsigned N, bool per, unsigned tile, unsigned g,
+                                          unsigned g0)
+{
+    if (g == 0) return true;  // every tile completed the previous run
+    const unsigned s = g0 + g;
+    bool ok = reached_(ld_acquire_gpu(d + tile), s);
+    if (tile > 0)
+        ok &= reached_(ld_acquire_gpu(d + tile - 1), s);
+    else if (per)
+        ok &= reached_(ld_acquire_gpu(d + N - 1), s);
+    if (tile + 1 < N)
+        ok &= reached_(ld_acquire_gpu(d + tile + 1), s);
+    else if (per)
+        ok &= reached_(ld_acquire_gpu(d), s);
+    if (per && N > 2) {
+        if (tile == 0) ok &= reached_(ld_acquire_gpu(d + N - 2), s);
+        if (tile == N - 2) ok &= reached_(ld_acquire_gpu(d), s);
+    }
+    return ok;
+}
+
+// Polls of a tile's dependencies before a CTA gives up (each poll is a round
+// trip to L2 and a short sleep: about a second in all, against microseconds
+// for a tile's stage).
+constexpr uint32_t kRunPolls = 1u << 20;
+
+template <int Q>
+__global__ void __launch_bounds__(kThreads, StageOccupancy<float, Q>::value) fdlb_run_kernel(RunArgs r)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int s_stop;
+    __shared__ unsigned s_tile, s_count;  // read back by thread 0 after the tile
+    // Programmatic dependent launch, as for the stage kernels: the next kernel
+    // may be scheduled once every CTA of this one has started, and no CTA
+    // touches the state before the previous kernel in the stream has completed.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int t = threadIdx.x;
+    // fewer than 2^31 tickets per launch
+    const unsigned N = unsigned(r.ntiles);
+    const unsigned g = blockIdx.x / N;
+    const unsigned tile = blockIdx.x - g * N;
+    if (t == 0) {
+        s_tile = tile;
+        s_count = r.g0 + g + 1u;
+        bool ok = run_ready(r.done, N, r.st[0][0].periodic != 0, tile, g, r.g0);
+        for (uint32_t polls = 0; !ok;) {
+            if (++polls >= kRunPolls || (*reinterpret_cast<volatile unsigned *>(r.st[0][0].err) & 4u)) {
+                atomicOr(r.st[0][0].err, 4u);
+                break;
+            }
+            __nanosleep(64);
+            ok = run_ready(r.done, N, r.st[0][0].periodic != 0, tile, g, r.g0);
+        }
+        s_stop = !ok;
+        if (ok) fence_proxy_async_global();
+        if (QL_STAGE_TMA) mbar_init(&mbar);
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const int64_t i0 = int64_t(tile) * kTile;
+    // step g / 3 reads psi^n from buf0 (even steps) or buf1 (odd steps)
+    const int k = int(g % 3u), odd = int((g / 3u) & 1u);
+    if (k == 0) {
+        stage_tile<float, Q, 1, kWarps, false>(r.st[odd][0], i0, smem_raw, &mbar, 0u);
+    } else if (k == 1) {
+        stage_tile<float, Q, 2, kWarps, false>(r.st[odd][1], i0, smem_raw, &mbar, 0u);
+    } else {
+        stage_tile<float, Q, 3, kWarps, false>(r.st[odd][2], i0, smem_raw, &mbar, 0u);
+    }
+    __syncthreads();  // every store of the tile is issued
+    if (t == 0) st_release_gpu(r.done + s_tile, s_count);  // cumulative: orders the CTA's stores before it
+}
+
 // Batched form: per Runge-Kutta stage, one persistent launch per velocity set
 // over the work list of (instance, tile) items of the instances with that Q
 // (independent domains with their own size and gas parameters).  Each CTA

@@ -7,6 +7,7 @@
 #include <string.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <mutex>
 #include <memory>
 #include <string>
@@ -60,6 +61,12 @@ struct ql_ctx {
     cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
     bool step_graph_failed = false;
     int64_t steps = 0;  // steps advanced (restart files carry it)
+    // FP32 chi_SET on the tiled path: ql_step may launch whole runs of steps
+    // (ql_opts.launch) with per-tile counts of completed stages in d_done,
+    // run_stages stages counted modulo 2^32 so far
+    int launch = QL_LAUNCH_AUTO;
+    unsigned *d_done = nullptr;
+    unsigned run_stages = 0;
     std::string err;
 };
 
@@ -149,6 +156,33 @@ static void *other_buf(ql_ctx *c) { return c->buf[1 - c->cur]; }
 // path keeps psi^n in place).
 static bool rotates(const ql_ctx *c) { return !c->lq; }
 
+// Arguments of one stage on the tiled path (chi_SET; stage() adds the chi_RET-FM buffers).
+static StageArgs stage_args(const ql_ctx *c, const void *in, const void *base, void *out)
+{
+    StageArgs a;
+    a.in = in;
+    a.base = base;
+    a.out = out;
+    a.nx = c->nx;
+    a.stride = c->stride;
+    a.inv_dx = 1.0 / c->dx;
+    a.dt = c->dt;
+    a.eta0 = c->eta0;
+    a.inv_rho_ref = 1.0 / c->rho_ref;
+    a.tau_pref = c->tau_pref;
+    a.pr_const = c->pr_const;
+    a.pr_mode = c->pr_mode;
+    a.enskog = c->enskog;
+    a.periodic = c->periodic;
+    a.fault = c->fault;
+    a.sums64 = c->sums64;
+    a.vsplit = 1;
+    a.err = c->d_err;
+    a.nbar = nullptr;
+    a.nout = nullptr;
+    return a;
+}
+
 static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, void *out)
 {
     if (c->lq) {
@@ -180,25 +214,7 @@ static cudaError_t stage(ql_ctx *c, int s, const void *in, const void *base, voi
         }
         return launch_lq_stage(s, l, c->stream);
     }
-    StageArgs a;
-    a.in = in;
-    a.base = base;
-    a.out = out;
-    a.nx = c->nx;
-    a.stride = c->stride;
-    a.inv_dx = 1.0 / c->dx;
-    a.dt = c->dt;
-    a.eta0 = c->eta0;
-    a.inv_rho_ref = 1.0 / c->rho_ref;
-    a.tau_pref = c->tau_pref;
-    a.pr_const = c->pr_const;
-    a.pr_mode = c->pr_mode;
-    a.enskog = c->enskog;
-    a.periodic = c->periodic;
-    a.fault = c->fault;
-    a.sums64 = c->sums64;
-    a.vsplit = 1;  // the launcher picks the FP64 split
-    a.err = c->d_err;
+    StageArgs a = stage_args(c, in, base, out);  // the launcher picks the FP64 split
     const bool ret = c->chi_mode == QL_CHI_RET_FM;
     a.nbar = ret ? c->d_nbar : nullptr;
     a.nout = ret && s != 0 ? c->d_n : nullptr;
@@ -248,6 +264,7 @@ static ql_status check_err_word(ql_ctx *c)
     QL_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     QL_CUDA(c, cudaStreamSynchronize(c->stream));
     if (h & 2u) return fail(c, QL_ECUDA, "a stage kernel gave up waiting for its tile's TMA copies");
+    if (h & 4u) return fail(c, QL_ECUDA, "a run gave up waiting for a neighbouring tile's previous stage");
     if (h & 1u) return fail(c, QL_ENONPHYSICAL, "non-physical state: n <= 0, T <= 0 or non-finite moments");
     return QL_OK;
 }
@@ -286,6 +303,7 @@ static void destroy_buffers(ql_ctx *c)
     dev_free(c, c->d_totals);
     dev_free(c, c->d_tab64);
     dev_free(c, c->d_err);
+    dev_free(c, c->d_done);
     dev_free(c, c->d_fmk);
     dev_free(c, c->d_n);
     dev_free(c, c->d_nbar);
@@ -318,10 +336,13 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     if (opts->chi_mode != QL_CHI_SET && opts->chi_mode != QL_CHI_RET_FM) return fail(nullptr, QL_EINVAL, "bad chi_mode");
     if (opts->fault != 0 && opts->fault != 1) return fail(nullptr, QL_EINVAL, "bad fault (0 or 1)");
     if (opts->sums != QL_SUMS_DFP32 && opts->sums != QL_SUMS_FP64) return fail(nullptr, QL_EINVAL, "bad sums");
+    if (opts->launch != QL_LAUNCH_AUTO && opts->launch != QL_LAUNCH_STAGES && opts->launch != QL_LAUNCH_RUN)
+        return fail(nullptr, QL_EINVAL, "bad launch (QL_LAUNCH_AUTO, QL_LAUNCH_STAGES or QL_LAUNCH_RUN)");
 
     ql_ctx *c = new ql_ctx();
     c->chi_mode = opts->chi_mode;
     c->fault = opts->fault;
+    c->launch = opts->launch;
     c->sums64 = opts->precision == QL_FP32 && opts->sums == QL_SUMS_FP64;
     c->lq = lq;
     c->Q = vs->Q;
@@ -412,6 +433,13 @@ ql_status ql_create(const ql_velset *vs, const ql_grid *grid, double denseness, 
     c->d_err = static_cast<unsigned *>(dev_alloc(c, 256));
     if (!c->d_fields || !c->d_init || !c->d_partial || !c->d_totals || !c->d_tab64 || !c->d_err)
         return bail(QL_ENOMEM, "work buffer allocation failed");
+    if (!c->lq && c->precision == QL_FP32 && run_supported_f32(c->Q)) {
+        const size_t bytes = sizeof(unsigned) * size_t(num_tiles(c->nx));
+        c->d_done = static_cast<unsigned *>(dev_alloc(c, bytes));
+        if (!c->d_done) return bail(QL_ENOMEM, "run counter allocation failed");
+        e = cudaMemsetAsync(c->d_done, 0, bytes, c->stream);
+        if (e != cudaSuccess) return bail(QL_ECUDA, std::string("run counters: ") + cudaGetErrorString(e));
+    }
     if (c->lq) {
         c->d_lqtab = static_cast<double *>(dev_alloc(c, sizeof(double) * lqtab.size()));
         c->d_lqmom = static_cast<double *>(dev_alloc(c, sizeof(double) * 6 * ncol));
@@ -512,9 +540,60 @@ static void record_step_graph(ql_ctx *c, int cur)
     }
 }
 
+// FP32 chi_SET solvers on the tiled path may run whole runs of steps as single
+// launches (fdlb_run_kernel): always with QL_LAUNCH_RUN, and with
+// QL_LAUNCH_AUTO for domains of 1 to kRunAutoWaves times as many tiles as the
+// GPU holds CTAs.  Measured on the Sod tube, Q = 32, against per-stage
+// launches: 0.70x the step time at 2^17 cells (1.2 waves of CTAs per stage),
+// 0.92x at 2^19 (4.6 waves), 1.02x at 2^21 (18.5 waves), 1.04x at 2^22; 1.10x
+// at 2^13 and 2^15 (fewer tiles than CTA slots).  Never with fault.
+constexpr int64_t kRunAutoWaves = 8;
+static bool runs_whole(const ql_ctx *c)
+{
+    if (!c->d_done || c->chi_mode != QL_CHI_SET || c->fault || c->launch == QL_LAUNCH_STAGES) return false;
+    if (c->launch == QL_LAUNCH_RUN) return true;
+    const int64_t n = num_tiles(c->nx), resident = run_resident_f32(c->Q);
+    return resident > 0 && n >= resident && n <= kRunAutoWaves * resident;
+}
+
+// nsteps steps as launches of fdlb_run_kernel (each at most kRunMaxTickets
+// (stage, tile) tickets), rotating the buffers as the step-by-step path does.
+static int64_t run_steps_per_launch(const ql_ctx *c)
+{
+    return std::max<int64_t>(1, kRunMaxTickets / (3 * num_tiles(c->nx)));
+}
+
+static ql_status run_steps(ql_ctx *c, int64_t nsteps)
+{
+    const int64_t N = num_tiles(c->nx);
+    const int64_t per_launch = run_steps_per_launch(c);
+    while (nsteps > 0) {
+        const int64_t k = std::min(nsteps, per_launch);
+        RunArgs r;
+        for (int p = 0; p < 2; ++p) {
+            const int cur = c->cur ^ p;
+            void *S = c->buf[cur], *T1 = c->buf[1 - cur], *T2 = c->buf[2];
+            r.st[p][0] = stage_args(c, S, S, T1);
+            r.st[p][1] = stage_args(c, T1, S, T2);
+            r.st[p][2] = stage_args(c, T2, S, T1);
+        }
+        r.ntiles = N;
+        r.done = c->d_done;
+        r.g0 = c->run_stages;
+        const cudaError_t e = launch_run_f32(c->Q, r, k, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "run kernel launch");
+        c->run_stages += unsigned(3 * k);
+        if (k & 1) c->cur = 1 - c->cur;
+        c->steps += k;
+        nsteps -= k;
+    }
+    return QL_OK;
+}
+
 ql_status ql_step(ql_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return fail(c, QL_EINVAL, "bad arguments to ql_step");
+    if (runs_whole(c)) return run_steps(c, nsteps);
     // several steps replay a recorded step: one graph launch per step instead
     // of three to six kernel launches, which matters where launches are slow
     const bool rot = rotates(c);
@@ -728,6 +807,13 @@ ql_status ql_info(const ql_ctx *c, double *out)
         out[6 + k] = c->p[k];
         out[6 + c->Q + k] = c->w[k];
     }
+    return QL_OK;
+}
+
+ql_status ql_launch_info(const ql_ctx *c, int64_t *steps_per_launch)
+{
+    if (!c || !steps_per_launch) return QL_EINVAL;
+    *steps_per_launch = runs_whole(c) ? run_steps_per_launch(c) : 0;
     return QL_OK;
 }
 

@@ -87,12 +87,26 @@ struct StageArgs {
     int fault;      // 1: arm the staging barrier without issuing the copies (failure-detection tests)
     int sums64;     // FP32: 1 combines the per-cell conserved sums in FP64, 0 in double-FP32
     int vsplit;     // FP64: CTAs per tile, each updating a contiguous range of the velocity pairs (>= 1)
-    unsigned *err;  // device error word; bit 0: non-physical cell, bit 1: a TMA staging wait gave up
+    unsigned *err;  // device error word; bit 0: non-physical cell, bit 1: a TMA staging wait gave up,
+                    // bit 2: a persistent run gave up waiting for a neighbouring tile
     // chi_RET-FM only (else null): nbar of every column of the stage input
     // (nx + 2 kHalo values of the working precision), and the density of
     // every interior cell of the stage output, written by the kernel.
     const void *nbar;
     void *nout;
+};
+
+// A run of steps in one launch (FP32, chi_SET, tiled velocity sets): CTA b
+// takes tile b mod ntiles of stage b / ntiles of the run (stage g is
+// Runge-Kutta stage g mod 3 + 1 of step g / 3).  st[p][s] are the arguments of
+// stage s + 1 of the steps whose psi^n sits in the buffer of parity p (0: the
+// run's first step).  done[i] counts the stages tile i has completed, modulo
+// 2^32, over all runs of the solver; each is g0 at launch.
+struct RunArgs {
+    StageArgs st[2][3];
+    int64_t ntiles;
+    unsigned *done;
+    unsigned g0;
 };
 
 // chi_RET-FM: nbar of every column (cells -kHalo .. nx+kHalo-1) from the
@@ -164,6 +178,13 @@ const double *host_tables();
 // stage: 0 writes L[psi] into out, 1..3 are the stages of Eq. (rk3).
 cudaError_t launch_stage_f32(int Q, int stage, const StageArgs &a, cudaStream_t s);
 cudaError_t launch_stage_f64(int Q, int stage, const StageArgs &a, cudaStream_t s);
+// A run of `steps` steps as one launch (RunArgs) of at most kRunMaxTickets
+// CTAs; false from run_supported_f32 for velocity sets without it.
+constexpr int64_t kRunMaxTickets = (int64_t(1) << 31) - 1;
+cudaError_t launch_run_f32(int Q, const RunArgs &r, int64_t steps, cudaStream_t s);
+bool run_supported_f32(int Q);
+// CTAs of the run kernel the current device holds at once (0 if the query fails).
+int64_t run_resident_f32(int Q);
 
 // psi = discrete equilibrium of (rho, u, T) given for cells -kHalo .. nx+kHalo-1
 // (device arrays of nx + 2 kHalo doubles); interior and ghost columns.

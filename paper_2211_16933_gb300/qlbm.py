@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libqlbm.so")
 QL_OK, QL_EINVAL, QL_ENOMEM, QL_ECUDA, QL_ENONPHYSICAL, QL_ETIMEOUT, QL_EUNSUPPORTED = range(7)
 QL_FP64, QL_FP32 = 0, 1
 QL_SUMS_DFP32, QL_SUMS_FP64 = 0, 1
+QL_LAUNCH_AUTO, QL_LAUNCH_STAGES, QL_LAUNCH_RUN = 0, 1, 2
 QL_BC_PERIODIC, QL_BC_FIXED = 0, 1
 QL_INIT_SOUND, QL_INIT_RIEMANN, QL_INIT_SHOCK, QL_INIT_FIELDS = 0, 1, 2, 3
 QL_PR_CONST, QL_PR_DENSE = 0, 1
@@ -34,7 +35,8 @@ EXPORTED = ("ql_create", "ql_step", "ql_sync", "ql_moments", "ql_totals", "ql_ge
             "ql_batch_set_shape",
             "ql_batch_fields", "ql_batch_project", "ql_sound_modes", "ql_closure_create", "ql_closure_forward", "ql_closure_gradients",
             "ql_closure_train_step", "ql_closure_train_steps", "ql_closure_params", "ql_closure_destroy",
-            "ql_closure_last_error", "ql_step_count", "ql_save", "ql_checkpoint_read_info", "ql_load")
+            "ql_closure_last_error", "ql_step_count", "ql_save", "ql_checkpoint_read_info", "ql_load",
+            "ql_launch_info")
 
 
 class QLError(RuntimeError):
@@ -69,7 +71,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class ql_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("pr_mode", C.c_int32), ("enskog", C.c_int32), ("device", C.c_int32),
-                ("chi_mode", C.c_int32), ("fault", C.c_int32), ("sums", C.c_int32), ("pad_", C.c_int32),
+                ("chi_mode", C.c_int32), ("fault", C.c_int32), ("sums", C.c_int32), ("launch", C.c_int32),
                 ("pr_const", C.c_double), ("rho_ref", C.c_double), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
@@ -117,6 +119,7 @@ def lib():
         L.ql_rhs.argtypes = [V, _DP, _DP]
         L.ql_state_device.argtypes = [V, C.POINTER(V), C.POINTER(C.c_int64)]
         L.ql_info.argtypes = [V, _DP]
+        L.ql_launch_info.argtypes = [V, C.POINTER(C.c_int64)]
         L.ql_destroy.argtypes = [V]
         L.ql_last_error.argtypes = [V]
         L.ql_last_error.restype = C.c_char_p
@@ -271,6 +274,13 @@ def ql_info(ctx, Q):
     out = np.zeros(6 + 2 * Q)
     _check(lib().ql_info(ctx, _ptr(out)), ctx)
     return out
+
+
+def ql_launch_info(ctx):
+    """Steps one launch of the whole-run kernel covers, 0 if the solver launches per stage."""
+    n = C.c_int64(0)
+    _check(lib().ql_launch_info(ctx, C.byref(n)), ctx)
+    return n.value
 
 
 def ql_destroy(ctx):
@@ -565,10 +575,12 @@ class Solver:
     def __init__(self, Q, nx, length, dt, denseness, kn, *, bc=QL_BC_PERIODIC, init_kind=QL_INIT_SOUND,
                  prm=(1.0, 1.0, 1e-3), rho=None, u=None, T=None, ghost=None, precision=QL_FP64,
                  pr_mode=QL_PR_DENSE, pr_const=2.0 / 3.0, enskog=1, rho_ref=1.0, device=0, use_torch=True,
-                 chi_mode=None, fault=0, sums=QL_SUMS_DFP32):
+                 chi_mode=None, fault=0, sums=QL_SUMS_DFP32, launch=QL_LAUNCH_AUTO):
         """fault = 1 is for failure-detection tests (ql_opts.fault): the stage kernels give up waiting for
         copies that are never issued and the next synchronising call raises QLError(QL_ECUDA).  sums
-        (FP32 only): QL_SUMS_DFP32 or QL_SUMS_FP64, the arithmetic of the per-cell conserved sums."""
+        (FP32 only): QL_SUMS_DFP32 or QL_SUMS_FP64, the arithmetic of the per-cell conserved sums.
+        launch (ql_opts.launch): QL_LAUNCH_AUTO, QL_LAUNCH_STAGES (one launch per stage) or QL_LAUNCH_RUN (one
+        launch per step call where the solver supports it)."""
         self.Q, self.nx, self.precision = Q, nx, precision
         vs = ql_velset(Q, 0)
         grid = ql_grid(nx, length, dt)
@@ -589,6 +601,7 @@ class Solver:
         o.chi_mode = QL_CHI_SET if chi_mode is None else chi_mode
         o.fault = fault
         o.sums = sums
+        o.launch = launch
         self._attach_torch(o, device, use_torch)
         self.ctx = ql_create(vs, grid, denseness, kn, b, ini, o)
         self._read_info()
@@ -646,6 +659,10 @@ class Solver:
 
     def step(self, n=1):
         ql_step(self.ctx, n)
+
+    def steps_per_launch(self):
+        """Steps one launch covers on the whole-run path, 0 when each stage is a launch (ql_launch_info)."""
+        return ql_launch_info(self.ctx)
 
     def sync(self):
         ql_sync(self.ctx)

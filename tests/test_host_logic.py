@@ -128,6 +128,9 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(qlbm_lib):
     with pytest.raises(q.QLError) as e:
         q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, precision=q.QL_FP32, sums=2, **kw)
     assert e.value.status == q.QL_EINVAL and "sums" in str(e.value)
+    with pytest.raises(q.QLError) as e:
+        q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, precision=q.QL_FP32, launch=3, **kw)
+    assert e.value.status == q.QL_EINVAL and "launch" in str(e.value)
     # a sound wave needs a periodic domain
     with pytest.raises(q.QLError) as e:
         q.Solver(16, 64, 1.0, 1e-3, 0.1, 0.1, bc=q.QL_BC_FIXED, init_kind=q.QL_INIT_SOUND,
@@ -249,8 +252,8 @@ def test_bench_records_apply_only_to_their_workload():
     """The committed DRAM-traffic and operation-count records are for Q = 32 at 2^22 cells: other velocity sets or
     sizes report null rather than a borrowed figure; the ALU peaks follow from the unit counts and clocks."""
     import bench
-    assert bench._traffic("fp32", 16, 1 << 22) is None
-    assert bench._traffic("fp32", 32, 1 << 20) is None
+    assert bench._traffic_per_step("fp32", 16, 1 << 22) is None
+    assert bench._traffic_per_step("fp32", 32, 1 << 20) is None
     assert bench._flops_per_update("fp32", 24) is None
     assert bench._alu_roofline("fp64", 1e9, 40) is None
     assert abs(bench.ALU_PEAK_TFLOPS["fp32"] - 80.54784) < 1e-9
