@@ -274,6 +274,9 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e datasheet bandwidth (context beside the measured copy)
+
+
 def _hbm_roofline(elem, nx, Q, step_s, precision_name, steps_per_launch, kernel):
     """The stepping kernel against the measured copy bandwidth: 16 words of phi and theta per update per step
     (stage 1 reads 2 / writes 2, stages 2-3 read 4 / write 2).  fdlb_run_kernel: one launch runs
@@ -287,10 +290,15 @@ def _hbm_roofline(elem, nx, Q, step_s, precision_name, steps_per_launch, kernel)
     else:
         peak, peak_src = 6800.0, "fallback"
     tr = _traffic_per_step(precision_name, Q, nx)
+    # the DRAM view: ncu's DRAM bytes (scaled to this size) over the same time, and both against the nominal
+    # HBM3e bandwidth beside the measured copy
+    dram = None if tr is None else tr / step_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None if tr is None else tr / launches_per_step, "peak_source": peak_src,
             "algorithmic_bytes_per_launch": bytes_per_step / launches_per_step,
-            "launches_per_step": launches_per_step, "kernel": kernel}
+            "launches_per_step": launches_per_step, "kernel": kernel,
+            "dram_achieved": dram, "dram_frac": None if dram is None else dram / peak,
+            "peak_nominal": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS}
 
 
 def _stepping(q, s, steps):
