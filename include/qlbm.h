@@ -156,9 +156,10 @@ typedef void (*ql_free_fn)(void *ptr, void *user);
  *              always launch per stage.  QL_LAUNCH_STAGES: one launch per
  *              Runge-Kutta stage (ql_step of several steps replays a recorded
  *              step).  QL_LAUNCH_RUN: each ql_step call is one launch of
- *              (stage, tile) work items, a tile's stage starting once the
- *              previous stage of it and of its neighbours has completed, so
- *              that consecutive stages and steps overlap.  QL_LAUNCH_AUTO (0,
+ *              (stage, tile) work items (several for runs of more than
+ *              2^31 - 1 of them), a tile's stage starting once the previous
+ *              stage of it and of its neighbours has completed, so that
+ *              consecutive stages and steps overlap.  QL_LAUNCH_AUTO (0,
  *              default): QL_LAUNCH_RUN for domains of one to eight times as
  *              many tiles (248 cells each) as the GPU holds CTAs at once, where
  *              a stage's last wave of CTAs leaves much of the GPU idle, and

@@ -551,8 +551,10 @@ constexpr int64_t kRunAutoWaves = 8;
 static bool runs_whole(const ql_ctx *c)
 {
     if (!c->d_done || c->chi_mode != QL_CHI_SET || c->fault || c->launch == QL_LAUNCH_STAGES) return false;
+    const int64_t n = num_tiles(c->nx);
+    if (3 * n > kRunMaxTickets) return false;  // not even one step fits one launch
     if (c->launch == QL_LAUNCH_RUN) return true;
-    const int64_t n = num_tiles(c->nx), resident = run_resident_f32(c->Q);
+    const int64_t resident = run_resident_f32(c->Q);
     return resident > 0 && n >= resident && n <= kRunAutoWaves * resident;
 }
 
