@@ -260,6 +260,23 @@ def test_bench_records_apply_only_to_their_workload():
     assert abs(bench.ALU_PEAK_TFLOPS["fp64"] - 1.25856) < 1e-12
 
 
+def test_bench_roofline_per_launch_for_both_launch_forms():
+    """The HBM roofline record counts bytes per launch: a third of a step for a stage launch, K steps for one
+    launch of the whole-run kernel; the achieved bandwidth (bytes per step over the step time) is the same."""
+    import bench
+    nx, Q, step_s = 1 << 22, 32, 1.8e-3
+    a = bench._hbm_roofline(4, nx, Q, step_s, "fp32", 1.0 / 3.0, "fdlb_stage_kernel")
+    b = bench._hbm_roofline(4, nx, Q, step_s, "fp32", 20, "fdlb_run_kernel")
+    step_bytes = 64 * nx * Q
+    assert a["launches_per_step"] == 3 and a["algorithmic_bytes_per_launch"] == step_bytes / 3
+    assert b["launches_per_step"] == 1 / 20 and b["algorithmic_bytes_per_launch"] == step_bytes * 20
+    assert a["achieved"] == b["achieved"] == step_bytes / step_s / 1e9
+    assert a["frac_of_nominal"] == a["achieved"] / bench.HBM_NOMINAL_GBS
+    if a["traffic"] is not None:
+        assert abs(b["traffic"] - 60 * a["traffic"]) <= 1e-6 * b["traffic"]
+        assert a["dram_achieved"] == b["dram_achieved"]
+
+
 def test_kernel_fingerprint_follows_code_not_comments():
     """The fingerprint that scopes the ncu records ignores comments and blank lines and changes with any code
     token."""
